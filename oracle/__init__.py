@@ -1,0 +1,169 @@
+"""Python access to the plain CPU oracle (``oracle/oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it.  The CUDA library never imports it.
+
+The C source is compiled on first use with ``gcc -O2 -ffp-contract=off
+-fno-fast-math`` so that every binary64 operation is rounded exactly as
+written (no fused multiply-add, no reassociation).
+
+Functions follow the paper's definitions (Section 1, Eq. 1; Section 3):
+``count_auto`` (DD or RR, unordered pairs i < j), ``count_cross`` (DR, all
+ordered pairs) and ``estimate`` (Landy-Szalay w(theta)).  Histograms have
+``len(edges) + 1`` entries: [underflow, bin 0 .. bin B-1, overflow].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fno-builtin", "-fPIC", "-shared"]
+
+LS_EXACT = 0
+LS_PAPER = 1
+
+
+def build(src: str = _SRC, out: str = _LIB, force: bool = False) -> str:
+    """Compile ``src`` into the shared library ``out`` (if stale) and return its path."""
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        tmp = f"{out}.{os.getpid()}.tmp"
+        subprocess.run(["gcc", *CFLAGS, src, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, out)
+    return out
+
+
+def _bind(lib):
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    u64 = ctypes.c_uint64
+    lib.oracle_count_auto_rows.argtypes = [dp, u64, dp, ctypes.c_int, u64, u64, u64p]
+    lib.oracle_count_cross_rows.argtypes = [dp, u64, dp, u64, dp, ctypes.c_int, u64, u64, u64p]
+    lib.oracle_estimate.argtypes = [u64p, u64p, u64p, ctypes.c_int, u64, u64, ctypes.c_int, dp]
+    for f in (lib.oracle_count_auto_rows, lib.oracle_count_cross_rows, lib.oracle_estimate):
+        f.restype = ctypes.c_int
+    return lib
+
+
+def load(path: str | None = None):
+    """Load (building if needed) the oracle library; ``path`` loads another build."""
+    global _lib
+    if path is not None:
+        return _bind(ctypes.CDLL(path))
+    with _lock:
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _uptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def _as_xyz(x) -> np.ndarray:
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    if a.ndim != 2 or a.shape[1] != 3:
+        raise ValueError("catalog must be an (n, 3) array of unit vectors")
+    return a
+
+
+def _row_splits(n_rows: int, weights, parts: int) -> list[tuple[int, int]]:
+    """Cut [0, n_rows) into ``parts`` contiguous ranges of about equal work."""
+    if parts <= 1 or n_rows == 0:
+        return [(0, n_rows)]
+    cum = np.concatenate([[0.0], np.cumsum(weights)])
+    cuts = np.searchsorted(cum, np.linspace(0.0, cum[-1], parts + 1))
+    cuts[0], cuts[-1] = 0, n_rows
+    cuts = np.maximum.accumulate(cuts)
+    return [(int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+
+
+def count_auto(xyz, edges, threads: int = 1, lib=None) -> np.ndarray:
+    """DD or RR histogram over unordered pairs i < j (B + 2 uint64 entries).
+
+    ``threads > 1`` splits the rows of the triangle across host threads (the
+    C call releases the GIL) and sums the per-range histograms.
+    """
+    lib = lib or load()
+    a = _as_xyz(xyz)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    n = a.shape[0]
+
+    def run(r):
+        h = np.zeros(len(e) + 1, dtype=np.uint64)
+        rc = lib.oracle_count_auto_rows(_dptr(a), n, _dptr(e), len(e), r[0], r[1], _uptr(h))
+        if rc != 0:
+            raise ValueError("oracle_count_auto: invalid arguments")
+        return h
+
+    ranges = _row_splits(n, n - 1 - np.arange(n, dtype=np.float64), threads)
+    if len(ranges) == 1:
+        return run(ranges[0])
+    with ThreadPoolExecutor(len(ranges)) as ex:
+        return np.sum(list(ex.map(run, ranges)), axis=0, dtype=np.uint64)
+
+
+def count_cross(xyz_d, xyz_r, edges, threads: int = 1, lib=None) -> np.ndarray:
+    """DR histogram over all ordered pairs (i in D, j in R) (B + 2 uint64 entries)."""
+    lib = lib or load()
+    d = _as_xyz(xyz_d)
+    r_ = _as_xyz(xyz_r)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    nd, nr = d.shape[0], r_.shape[0]
+
+    def run(rg):
+        h = np.zeros(len(e) + 1, dtype=np.uint64)
+        rc = lib.oracle_count_cross_rows(_dptr(d), nd, _dptr(r_), nr, _dptr(e), len(e),
+                                         rg[0], rg[1], _uptr(h))
+        if rc != 0:
+            raise ValueError("oracle_count_cross: invalid arguments")
+        return h
+
+    ranges = _row_splits(nd, np.ones(nd), threads)
+    if len(ranges) == 1:
+        return run(ranges[0])
+    with ThreadPoolExecutor(len(ranges)) as ex:
+        return np.sum(list(ex.map(run, ranges)), axis=0, dtype=np.uint64)
+
+
+def estimate(dd, dr, rr, nd: int, nr: int, estimator: int = LS_EXACT, lib=None) -> np.ndarray:
+    """Landy-Szalay w(theta) per bin (Eq. 1; see ``oracle_estimate`` for the two readings).
+
+    ``dd``, ``dr``, ``rr`` are the per-bin counts without underflow/overflow.
+    """
+    lib = lib or load()
+    dd = np.ascontiguousarray(dd, dtype=np.uint64)
+    dr = np.ascontiguousarray(dr, dtype=np.uint64)
+    rr = np.ascontiguousarray(rr, dtype=np.uint64)
+    nb = len(dd)
+    if len(dr) != nb or len(rr) != nb:
+        raise ValueError("dd, dr and rr must have the same length")
+    w = np.empty(nb, dtype=np.float64)
+    rc = lib.oracle_estimate(_uptr(dd), _uptr(dr), _uptr(rr), nb, nd, nr, estimator, _dptr(w))
+    if rc != 0:
+        raise ValueError("oracle_estimate: invalid arguments")
+    return w
+
+
+def correlation(data, rand, edges, estimator: int = LS_EXACT, threads: int = 1):
+    """DD, DR, RR histograms and w(theta) for one data/random catalog pair."""
+    dd = count_auto(data, edges, threads)
+    rr = count_auto(rand, edges, threads)
+    dr = count_cross(data, rand, edges, threads)
+    w = estimate(dd[1:-1], dr[1:-1], rr[1:-1], len(data), len(rand), estimator)
+    return dd, dr, rr, w
