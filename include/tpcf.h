@@ -1,0 +1,246 @@
+/*
+ * tpcf.h - C ABI of the GB300 angular two-point correlation library.
+ *
+ * The library counts pairs of points on the sphere by angular separation
+ * into the three histograms of the Landy-Szalay estimator and evaluates the
+ * estimator (Ponce et al., "Application of GPUs for the calculation of two
+ * point correlation functions in cosmology"):
+ *   - Section 1, Eq. 1 and the definitions after it: DD (pairs within the
+ *     data catalog), RR (pairs within the random catalog) and DR (pairs
+ *     between the two), as functions of the separation angle theta.
+ *   - Section 3: the angle of a pair follows from the dot product of the two
+ *     unit vectors; per-block partial histograms in shared memory are combined
+ *     into one histogram in global memory; the three histograms are computed
+ *     concurrently (the paper uses one GPU per histogram, this library one
+ *     CUDA stream or one fused launch per histogram set).
+ *   - Section 2 / Section 5: brute force, every pair is visited.
+ *
+ * Counting conventions (the paper leaves them open; these are this library's):
+ *   - Auto counts (DD, RR) count unordered pairs i < j; self pairs are not
+ *     counted.  Cross counts (DR) count every pair (i in D, j in R).
+ *   - The separation of unit vectors a, b is theta = acos(d) with
+ *     d = (ax*bx + ay*by) + az*bz evaluated in binary64 in that order without
+ *     fused multiply-add, clamped to [-1, 1], and acos the host C library's.
+ *     The GPU never evaluates acos: for each edge t_k the host derives the
+ *     binary64 threshold C_k = the largest double d with acos(d) >= t_k, so
+ *     that theta >= t_k exactly when d <= C_k.
+ *   - Bins are half-open [t_k, t_{k+1}).  A histogram has B + 2 uint64
+ *     entries for B + 1 edges: [0] underflow (theta < t_0), [k + 1] bin k,
+ *     [B + 1] overflow (theta >= t_B).  The entries sum to the number of pairs.
+ *   - Counts are exact integers.  In TPCF_SCREEN_RECHECK mode an FP32 dot
+ *     product classifies every pair whose FP32 cosine is farther than a proven
+ *     error bound from every threshold; the remaining pairs (the guard band)
+ *     are recomputed in binary64 exactly as above.  Both modes give identical
+ *     histograms.
+ *
+ * Errors: every function returns a status code (TPCF_OK = 0).  No exception or
+ * signal crosses the ABI.  tpcf_strerror() names a code; tpcf_last_error()
+ * gives the context's last message.  After TPCF_ECUDA the context should be
+ * destroyed.  TPCF_ETIMEOUT means a bounded device wait gave up; the kernel
+ * returned early, the outputs of that call are invalid and the context stays
+ * usable.
+ *
+ * Ownership: handles (tpcf_ctx, tpcf_catalog, tpcf_bins) are created and owned
+ * by the library and freed by the matching *_destroy.  Input arrays stay owned
+ * by the caller and are copied (host) or read during the call's stream order
+ * (device).  Output arrays are allocated by the caller.
+ *
+ * Threads and streams: a context may be used from several host threads; calls
+ * on different streams run concurrently on the device.  `stream` arguments are
+ * cudaStream_t values passed as void* (NULL = the legacy default stream).
+ */
+#ifndef TPCF_H
+#define TPCF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define TPCF_OK 0
+#define TPCF_EINVAL 1    /* bad argument: NULL, size, NaN/Inf, non-unit vector, unsorted edges */
+#define TPCF_ENOMEM 2    /* device or host allocation failed */
+#define TPCF_EBUDGET 3   /* a job alone exceeds the context's device-memory budget */
+#define TPCF_ECUDA 4     /* a CUDA runtime call failed */
+#define TPCF_EAGAIN 5    /* tpcf_poll: job not finished yet */
+#define TPCF_ETIMEOUT 6  /* a bounded device wait gave up (outputs invalid, context usable) */
+#define TPCF_EOVERFLOW 7 /* a size exceeds a documented limit */
+#define TPCF_ECANCELED 8 /* job was cancelled */
+#define TPCF_ENOTFOUND 9 /* unknown job id */
+#define TPCF_ESTATE 10   /* call not valid in the current state (e.g. shut down) */
+
+/* where an array lives */
+#define TPCF_HOST 0
+#define TPCF_DEVICE 1
+
+/* counting precision */
+#define TPCF_SCREEN_RECHECK 0 /* FP32 screen + binary64 guard-band recheck (default) */
+#define TPCF_PLAIN_FP64 1     /* every pair in binary64 (comparator, slower) */
+
+/* estimator readings of Eq. 1 (see tpcf_estimate) */
+#define TPCF_LS_EXACT 0
+#define TPCF_LS_PAPER 1
+
+/* configuration flags */
+#define TPCF_F_NO_SORT 0x1u          /* keep catalog order (no spatial sort on the device) */
+#define TPCF_F_DYNAMIC_SCHED 0x2u    /* persistent blocks take work from an atomic counter */
+#define TPCF_F_TEST_WAIT_TIMEOUT 0x100u /* test hook: the first j-tile copy of each counting
+                                           launch is never issued, so its bounded wait expires
+                                           and the call returns TPCF_ETIMEOUT */
+
+/* limits */
+#define TPCF_MAX_EDGES 321           /* B + 1 <= 321, i.e. at most 320 bins (per-thread
+                                        shared-memory histograms must fit one block) */
+#define TPCF_MAX_POINTS 0x7fffffffull /* points per catalog */
+
+typedef struct tpcf_ctx tpcf_ctx;
+typedef struct tpcf_catalog tpcf_catalog;
+typedef struct tpcf_bins tpcf_bins;
+
+typedef struct tpcf_config {
+    int device;                /* CUDA device ordinal */
+    int precision;             /* TPCF_SCREEN_RECHECK or TPCF_PLAIN_FP64 */
+    double guard_band;         /* half-width g of the recheck band in cos(theta); 0 -> 2^-20.
+                                  Must exceed the FP32 screen's error bound (about 9 * 2^-24). */
+    uint64_t hbm_budget_bytes; /* device memory the job server may hold for catalogs; 0 -> 120 GB
+                                  capped at 80% of free memory */
+    uint32_t flags;            /* TPCF_F_* */
+    int threads;               /* kernel shape override: threads per block (0 = tuned default) */
+    int ipt;                   /* kernel shape override: i-points per thread (0 = default) */
+    int jtile;                 /* kernel shape override: j-points per shared-memory tile (0 = default) */
+    uint32_t shard_index;      /* multi-process split of the pair tiles: this process's index */
+    uint32_t shard_count;      /* number of shards (0 or 1 = no split); histograms of all
+                                  shards sum to the unsplit result exactly */
+    uint32_t wait_timeout_us;  /* limit of every device-side wait; 0 -> 2,000,000 us */
+} tpcf_config;
+
+typedef struct tpcf_stats {
+    uint64_t pairs;         /* pairs visited by the call (all histograms of the call) */
+    uint64_t band_pairs;    /* pairs whose FP32 cosine fell in a guard band (rechecked in FP64) */
+    uint64_t band_mismatch; /* band pairs whose bin by FP32 comparison against the FP32-rounded
+                               thresholds differs from the binary64 bin */
+    uint32_t device_error;  /* device error word of the call (0 = none) */
+    uint32_t launches;      /* kernels launched by the call */
+    double kernel_ms;       /* device time of the counting launch (CUDA events) */
+} tpcf_stats;
+
+/* ------------------------------------------------------------------ misc */
+const char *tpcf_strerror(int status);
+/* Last error message recorded on ctx (empty string if none).  Not thread-safe
+ * with respect to concurrent failing calls on the same context. */
+const char *tpcf_last_error(const tpcf_ctx *ctx);
+/* Fills *cfg with the defaults (device 0, screen + recheck, g = 2^-20). */
+void tpcf_config_default(tpcf_config *cfg);
+/* Library version as major * 10000 + minor * 100 + patch. */
+int tpcf_version(void);
+
+/* ------------------------------------------------------------------ context */
+/* Creates a context on cfg->device (NULL cfg = defaults).  Allocates the
+ * per-call device scratch slots.  *out is NULL on failure. */
+int tpcf_create(tpcf_ctx **out, const tpcf_config *cfg);
+/* Waits for the context's work, stops the job server, frees everything. */
+int tpcf_destroy(tpcf_ctx *ctx);
+
+/* ------------------------------------------------------------------ catalogs
+ * A catalog is n unit vectors, xyz row-major (n x 3 binary64), from the host
+ * (where = TPCF_HOST, copied synchronously) or the device (TPCF_DEVICE, read
+ * in `stream` order; the call synchronizes the stream before returning so the
+ * input may be freed afterwards).  The library validates every point (finite,
+ * | |v| - 1 | <= 1e-6), keeps a binary64 copy and an FP32 copy, and (unless
+ * TPCF_F_NO_SORT) reorders points along a space-filling curve on the cube
+ * faces; counts do not depend on the order (they are sums over all pairs).
+ * n may be 0.  Errors: TPCF_EINVAL (bad point), TPCF_EOVERFLOW (n too large).
+ *
+ * tpcf_catalog_create_segmented: the same, for a catalog made of nseg
+ * consecutive segments (offsets[0] = 0, offsets[nseg] = n, non-decreasing);
+ * points are reordered only within their segment, so segment s keeps the
+ * points offsets[s] .. offsets[s+1]-1 of the input.  Used for jackknife
+ * patches (tpcf_count_patches). */
+int tpcf_catalog_create(tpcf_ctx *ctx, const double *xyz, uint64_t n, int where, void *stream,
+                        tpcf_catalog **out);
+int tpcf_catalog_create_segmented(tpcf_ctx *ctx, const double *xyz, uint64_t n, int where,
+                                  const uint64_t *offsets, int nseg, void *stream,
+                                  tpcf_catalog **out);
+int tpcf_catalog_destroy(tpcf_catalog *cat);
+uint64_t tpcf_catalog_size(const tpcf_catalog *cat);
+
+/* ------------------------------------------------------------------ bins
+ * nedges = B + 1 edges in radians, strictly increasing, in [0, pi].
+ * Derives the binary64 cos-space thresholds C_k on the host (bisection on the
+ * ordered doubles against the host acos, then a scan of neighbouring doubles
+ * that checks the predicate acos(d) >= t_k flips exactly once), the FP32
+ * screen bounds lo_k = RD(C_k - g), hi_k = RU(C_k + g), and a lookup table
+ * from FP32 cosine to candidate bins; uploads them to the device. */
+int tpcf_bins_create(tpcf_ctx *ctx, const double *edges_rad, int nedges, tpcf_bins **out);
+int tpcf_bins_destroy(tpcf_bins *bins);
+/* Host-only: the thresholds for edges_rad (no context or GPU needed).
+ * cos_thr[k] = C_k (+inf for t_k = 0); lo[k], hi[k] the FP32 screen bounds for
+ * guard band g (0 -> 2^-20); verified[k] = 1 when the neighbour scan around
+ * C_k covered at least 4 ulps of t_k on each side and found the predicate
+ * monotone, 0 otherwise.  Any output pointer may be NULL. */
+int tpcf_bins_thresholds(const double *edges_rad, int nedges, double guard_band, double *cos_thr,
+                         float *lo, float *hi, int *verified);
+
+/* ------------------------------------------------------------------ counting
+ * hist: B + 2 uint64 (layout above).  where = TPCF_HOST: the call is
+ * synchronous, hist is host memory, st (optional) receives the statistics.
+ * where = TPCF_DEVICE: the call is asynchronous in `stream`, hist is device
+ * memory written when the stream reaches the end of the call; st must be NULL.
+ * Catalogs and bins must belong to ctx. */
+int tpcf_count_auto(tpcf_ctx *ctx, const tpcf_catalog *cat, const tpcf_bins *bins, void *stream,
+                    uint64_t *hist, int where, tpcf_stats *st);
+int tpcf_count_cross(tpcf_ctx *ctx, const tpcf_catalog *d, const tpcf_catalog *r,
+                     const tpcf_bins *bins, void *stream, uint64_t *hist, int where,
+                     tpcf_stats *st);
+/* DD, DR and RR in one persistent launch whose blocks take tiles of all three
+ * (the single-GPU counterpart of the paper's three GPUs, Section 3).  Same
+ * conventions as above for each of dd, dr, rr. */
+int tpcf_count_all(tpcf_ctx *ctx, const tpcf_catalog *d, const tpcf_catalog *r,
+                   const tpcf_bins *bins, void *stream, uint64_t *dd, uint64_t *dr, uint64_t *rr,
+                   int where, tpcf_stats *st);
+
+/* ------------------------------------------------------------------ estimator
+ * Landy-Szalay w(theta) (Eq. 1) for nbins bins.  dd, dr, rr: the per-bin
+ * counts WITHOUT underflow/overflow (host arrays of nbins); nd, nr >= 2 the
+ * catalog sizes; w: nbins host doubles.  Eq. 1 is garbled in print; two
+ * readings:
+ *   TPCF_LS_EXACT: nDD = DD/(nd(nd-1)/2), nRR = RR/(nr(nr-1)/2), nDR = DR/(nd nr),
+ *                  w = ((nDD - 2 nDR) + nRR) / nRR;
+ *   TPCF_LS_PAPER: q = nr/nd, DD' = 2 DD, RR' = 2 RR (ordered pairs),
+ *                  w = (1 + (q q)(DD'/RR')) - ((2 q)(DR/RR')).
+ * Each in binary64 in exactly that order; RR = 0 gives NaN. */
+int tpcf_estimate(const uint64_t *dd, const uint64_t *dr, const uint64_t *rr, int nbins,
+                  uint64_t nd, uint64_t nr, int estimator, double *w);
+
+/* One call from host arrays to w(theta): uploads both catalogs, derives the
+ * bins, counts DD, DR, RR in one launch, copies the histograms back and
+ * evaluates the estimator.  dd, dr, rr: B + 2 host uint64 each (may be NULL);
+ * w: B host doubles (may be NULL).  Synchronous in `stream`. */
+int tpcf_correlate(tpcf_ctx *ctx, const double *d_xyz, uint64_t nd, const double *r_xyz,
+                   uint64_t nr, const double *edges_rad, int nedges, int estimator, void *stream,
+                   uint64_t *dd, uint64_t *dr, uint64_t *rr, double *w, tpcf_stats *st);
+
+/* ------------------------------------------------------------------ self-check hooks
+ * Host-only helpers used by the test-suite (no GPU needed).
+ *
+ * tpcf_plan_coverage: enumerates the work items and tiles the counting kernel
+ * uses for one histogram (na x nb points, i-block I, j-chunk Jc, j-tile J;
+ * auto_mode = 1 for an auto count, na == nb) and adds 1 to counts[i * nb + j]
+ * (host array of na * nb, may be NULL) for every pair the kernel would count.
+ * Returns the number of items (-1 on bad sizes); *pairs (may be NULL) gets the
+ * sum of the per-item pair counts the kernel reports.
+ *
+ * tpcf_debug_fail_alloc_after: the n-th following device allocation made by
+ * the library fails with TPCF_ENOMEM (n = -1 switches this off). */
+int64_t tpcf_plan_coverage(uint32_t na, uint32_t nb, int auto_mode, uint32_t I, uint32_t Jc,
+                           uint32_t J, uint32_t *counts, uint64_t *pairs);
+void tpcf_debug_fail_alloc_after(int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPCF_H */

@@ -1,0 +1,99 @@
+// Work decomposition of one pair-count histogram into items and tiles.
+// Shared by the counting kernel (device) and the host runtime (shards,
+// expected pair counts, coverage self-test), so both enumerate exactly the
+// same pairs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tpcf {
+
+struct ItemGeom {
+    uint32_t i0;       // first i of the i-block
+    uint32_t j0;       // first j of the j-chunk
+    uint32_t t_first;  // first j-tile of the chunk holding a countable pair
+    uint32_t t_end;    // one past the last j-tile
+};
+
+__host__ __device__ inline uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__host__ __device__ inline uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+// Number of chunks of i-block b's row that precede the first useful chunk:
+// floor(b * I / Jc).  Either Jc divides I or I divides Jc.
+__host__ __device__ inline uint64_t first_chunk(uint64_t b, uint32_t I, uint32_t Jc) {
+    return (b * I) / Jc;
+}
+
+// F(ib) = sum_{b < ib} floor(b I / Jc) in closed form.
+__host__ __device__ inline uint64_t first_chunk_prefix(uint64_t ib, uint32_t I, uint32_t Jc) {
+    if (ib == 0) return 0;
+    if (I >= Jc) {
+        uint64_t k = I / Jc;
+        return k * (ib * (ib - 1) / 2);
+    }
+    uint64_t m = Jc / I;
+    uint64_t Q = ib / m, Rm = ib % m;
+    return m * (Q * (Q - 1) / 2) + Q * Rm;
+}
+
+// Items in the upper triangle (auto) or the rectangle (cross).
+__host__ __device__ inline uint64_t items_of(uint32_t n_iblk, uint32_t n_jchunk, bool auto_mode,
+                                             uint32_t I, uint32_t Jc) {
+    if (!auto_mode) return (uint64_t)n_iblk * n_jchunk;
+    return (uint64_t)n_iblk * n_jchunk - first_chunk_prefix(n_iblk, I, Jc);
+}
+
+// Local item index -> geometry.  Auto mode: row ib has n_jchunk - floor(ib I / Jc)
+// items, starting at chunk floor(ib I / Jc), the chunk holding j = ib * I.
+__host__ __device__ inline ItemGeom item_geom(uint64_t local, uint32_t na, uint32_t nb,
+                                              uint32_t n_iblk, uint32_t n_jchunk, bool auto_mode,
+                                              uint32_t I, uint32_t Jc, uint32_t J) {
+    uint64_t ib, jc;
+    if (!auto_mode) {
+        ib = local / n_jchunk;
+        jc = local % n_jchunk;
+    } else {
+        // largest ib with S(ib) <= local, S(ib) = ib * n_jchunk - F(ib)
+        uint64_t lo = 0, hi = n_iblk;  // S(lo) <= local < S(hi)
+        while (hi - lo > 1) {
+            uint64_t mid = (lo + hi) / 2;
+            uint64_t s = mid * (uint64_t)n_jchunk - first_chunk_prefix(mid, I, Jc);
+            if (s <= local) lo = mid; else hi = mid;
+        }
+        ib = lo;
+        uint64_t s = ib * (uint64_t)n_jchunk - first_chunk_prefix(ib, I, Jc);
+        jc = first_chunk(ib, I, Jc) + (local - s);
+    }
+    ItemGeom g;
+    g.i0 = (uint32_t)(ib * I);
+    g.j0 = (uint32_t)(jc * Jc);
+    uint64_t nj = (g.j0 < nb) ? umin64(Jc, nb - g.j0) : 0;
+    g.t_end = (uint32_t)((nj + J - 1) / J);
+    g.t_first = 0;
+    if (auto_mode && (uint64_t)g.i0 + 1 > g.j0) {
+        g.t_first = (uint32_t)(((uint64_t)g.i0 + 1 - g.j0) / J);
+        if (g.t_first > g.t_end) g.t_first = g.t_end;
+    }
+    (void)na;
+    return g;
+}
+
+// Pairs an item counts: i in [i0, i0 + I) and j in [j0, j0 + Jc), clipped to
+// the catalogs, with j > i in auto mode.
+__host__ __device__ inline uint64_t item_pairs(const ItemGeom& g, uint32_t na, uint32_t nb,
+                                               bool auto_mode, uint32_t I, uint32_t Jc) {
+    if (g.i0 >= na || g.j0 >= nb) return 0;
+    uint64_t i0 = g.i0, j0 = g.j0;
+    uint64_t iend = umin64(i0 + I, na), jend = umin64(j0 + Jc, nb);
+    uint64_t nj = jend - j0;
+    if (!auto_mode) return (iend - i0) * nj;
+    uint64_t total = 0;
+    uint64_t a_end = umin64(iend, j0);  // i < j0: every j of the chunk is above i
+    if (a_end > i0) total += (a_end - i0) * nj;
+    uint64_t a = umax64(i0, j0), b = umin64(iend, jend - 1);  // i inside the chunk
+    if (b > a) total += (b - a) * (jend - 1) - ((a + b - 1) * (b - a)) / 2;
+    return total;
+}
+
+}  // namespace tpcf

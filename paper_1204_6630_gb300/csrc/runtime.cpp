@@ -1,0 +1,825 @@
+// Host runtime of the pair-counting library: contexts, device scratch slots,
+// catalogs, bin thresholds, kernel shapes, launches and the estimator.
+//
+// Paper: Ponce et al., "Application of GPUs for the calculation of two point
+// correlation functions in cosmology" (Section 1, Eq. 1: DD, DR, RR and the
+// Landy-Szalay estimator; Section 3: dot product + arc-cosine per pair,
+// partial histograms merged into one, one histogram per GPU).
+//
+// Compiled with -ffp-contract=off: every binary64 operation here is rounded
+// exactly as written (threshold derivation and the estimator depend on it).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+#include "tpcf.h"
+#include "tpcf_internal.h"
+
+using namespace tpcf;
+
+namespace {
+
+constexpr int kSlots = 16;
+constexpr size_t kHistStride = TPCF_MAX_EDGES + 1;          // words per histogram in a slot
+constexpr size_t kStatOff = 3 * kHistStride;                 // stats words after 3 histograms
+constexpr size_t kSlotWords = ((kStatOff + kStatWords) + 31) / 32 * 32;
+constexpr double kDefaultGuard = 1.0 / 1048576.0;            // 2^-20
+constexpr uint32_t kDefaultWaitUs = 2000000;
+
+std::atomic<int> g_alloc_fail_countdown{-1};
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    int c = g_alloc_fail_countdown.load();
+    if (c >= 0) {
+        if (c == 0) { *p = nullptr; return cudaErrorMemoryAllocation; }
+        g_alloc_fail_countdown.fetch_sub(1);
+    }
+    return cudaMalloc(p, bytes);
+}
+
+}  // namespace
+
+// ====================================================================== handles
+struct tpcf_ctx {
+    tpcf_config cfg;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    std::mutex err_mu;
+    std::string last_error;
+    struct Slot {
+        unsigned long long* dev = nullptr;
+        cudaEvent_t ev = nullptr;
+        std::mutex mu;
+    };
+    Slot slots[kSlots];
+    std::atomic<uint32_t> slot_rr{0};
+
+    int fail(int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+};
+
+int tpcf_ctx::fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::lock_guard<std::mutex> g(err_mu);
+    last_error = buf;
+    return code;
+}
+
+struct tpcf_catalog {
+    tpcf_ctx* ctx = nullptr;
+    uint64_t n = 0;
+    uint32_t n_pad = 0;
+    Point64* d64 = nullptr;
+    float4* d32 = nullptr;
+    std::vector<uint64_t> offsets;  // segments (empty = one segment)
+};
+
+struct tpcf_bins {
+    tpcf_ctx* ctx = nullptr;
+    int nedges = 0;
+    std::vector<double> edges, cos_thr;
+    std::vector<float> lo, hi, c32;
+    std::vector<uint32_t> lut;
+    std::vector<int> verified;
+    BinsDev host;                  // device pointers, host copy
+    void* dev_buf = nullptr;       // arrays
+    BinsDev* dev_desc = nullptr;   // device copy of `host`
+};
+
+#define CUDA_TRY(ctx, call)                                                                    \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return (ctx)->fail(e_ == cudaErrorMemoryAllocation ? TPCF_ENOMEM : TPCF_ECUDA,     \
+                               "%s failed: %s", #call, cudaGetErrorString(e_));                \
+    } while (0)
+
+// ====================================================================== misc
+extern "C" const char* tpcf_strerror(int s) {
+    switch (s) {
+        case TPCF_OK: return "ok";
+        case TPCF_EINVAL: return "invalid argument";
+        case TPCF_ENOMEM: return "out of memory";
+        case TPCF_EBUDGET: return "job exceeds the device-memory budget";
+        case TPCF_ECUDA: return "CUDA error";
+        case TPCF_EAGAIN: return "not finished";
+        case TPCF_ETIMEOUT: return "bounded device wait timed out";
+        case TPCF_EOVERFLOW: return "size limit exceeded";
+        case TPCF_ECANCELED: return "cancelled";
+        case TPCF_ENOTFOUND: return "unknown job";
+        case TPCF_ESTATE: return "invalid state";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* tpcf_last_error(const tpcf_ctx* ctx) {
+    return ctx ? ctx->last_error.c_str() : "";
+}
+
+extern "C" void tpcf_config_default(tpcf_config* cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->precision = TPCF_SCREEN_RECHECK;
+    cfg->guard_band = kDefaultGuard;
+    cfg->wait_timeout_us = kDefaultWaitUs;
+}
+
+extern "C" int tpcf_version(void) { return 100; }
+
+// Test hook: make the n-th following device allocation fail (n = -1: never).
+extern "C" void tpcf_debug_fail_alloc_after(int n) { g_alloc_fail_countdown.store(n); }
+
+// ====================================================================== context
+extern "C" int tpcf_create(tpcf_ctx** out, const tpcf_config* cfg_in) {
+    if (!out) return TPCF_EINVAL;
+    *out = nullptr;
+    tpcf_config cfg;
+    tpcf_config_default(&cfg);
+    if (cfg_in) cfg = *cfg_in;
+    if (cfg.guard_band == 0.0) cfg.guard_band = kDefaultGuard;
+    if (cfg.wait_timeout_us == 0) cfg.wait_timeout_us = kDefaultWaitUs;
+    if (!(cfg.guard_band > 0.0 && cfg.guard_band < 0.25)) return TPCF_EINVAL;
+    if (cfg.precision != TPCF_SCREEN_RECHECK && cfg.precision != TPCF_PLAIN_FP64) return TPCF_EINVAL;
+    if (cfg.shard_count > 1 && cfg.shard_index >= cfg.shard_count) return TPCF_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev)
+        return TPCF_ECUDA;
+    if (cudaSetDevice(cfg.device) != cudaSuccess) return TPCF_ECUDA;
+    tpcf_ctx* ctx = new tpcf_ctx();
+    ctx->cfg = cfg;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, cfg.device) != cudaSuccess) { delete ctx; return TPCF_ECUDA; }
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    for (auto& s : ctx->slots) {
+        if (dev_malloc((void**)&s.dev, kSlotWords * 8) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) {
+            tpcf_destroy(ctx);
+            return TPCF_ENOMEM;
+        }
+    }
+    *out = ctx;
+    return TPCF_OK;
+}
+
+extern "C" int tpcf_destroy(tpcf_ctx* ctx) {
+    if (!ctx) return TPCF_EINVAL;
+    cudaSetDevice(ctx->cfg.device);
+    for (auto& s : ctx->slots) {
+        if (s.ev) cudaEventSynchronize(s.ev);
+        if (s.dev) cudaFree(s.dev);
+        if (s.ev) cudaEventDestroy(s.ev);
+    }
+    delete ctx;
+    return TPCF_OK;
+}
+
+// ====================================================================== thresholds
+namespace {
+
+int64_t dkey(double d) {
+    int64_t b;
+    memcpy(&b, &d, 8);
+    return b >= 0 ? b : -(b & INT64_MAX);
+}
+
+double dfromkey(int64_t k) {
+    uint64_t b = k >= 0 ? (uint64_t)k : ((uint64_t)(-k) | 0x8000000000000000ull);
+    double d;
+    memcpy(&d, &b, 8);
+    return d;
+}
+
+int32_t fkey(float v) {
+    int32_t b;
+    memcpy(&b, &v, 4);
+    return b >= 0 ? b : -(b & 0x7fffffff);
+}
+
+float ffromkey(int64_t k) {
+    uint32_t b = k >= 0 ? (uint32_t)k : ((uint32_t)(-k) | 0x80000000u);
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+}
+
+// The oracle's predicate for one pair and one edge: theta >= t with
+// theta = acos(clamp(d, -1, 1)) from the host C library.
+bool angle_at_least(double d, double t) {
+    double c = d > 1.0 ? 1.0 : (d < -1.0 ? -1.0 : d);
+    return acos(c) >= t;
+}
+
+float round_down_f32(double x) {
+    float f = (float)x;
+    if ((double)f > x) f = nextafterf(f, -INFINITY);
+    return f;
+}
+
+float round_up_f32(double x) {
+    float f = (float)x;
+    if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+// C = the largest double d with acos(clamp(d)) >= t, found by bisection over
+// the ordered doubles of [-1, 1]; then the predicate is checked on a window of
+// neighbouring doubles wide enough to cover 4 ulps of t on each side.
+double derive_threshold(double t, int* verified) {
+    if (t <= 0.0) { *verified = 1; return INFINITY; }
+    int64_t lo = dkey(-1.0), hi = dkey(1.0);  // pred(lo) true (t <= pi), pred(hi) false (t > 0)
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (angle_at_least(dfromkey(mid), t)) lo = mid; else hi = mid;
+    }
+    const double C = dfromkey(lo);
+    const double ulp_t = nextafter(t, INFINITY) - t;
+    const double ac = fabs(C);
+    const double ulp_c = ac > 0 ? nextafter(ac, INFINITY) - ac : 4.9406564584124654e-324;
+    const double need = 4.0 * ulp_t * fmax(sin(t), 4.0 * ulp_t) / ulp_c;
+    const int64_t kMaxWin = (int64_t)1 << 22;
+    int64_t win = (int64_t)fmin(2.0 * ceil(need) + 64.0, (double)kMaxWin);
+    bool ok = need * 2.0 + 64.0 <= (double)kMaxWin;
+    const int64_t kmin = dkey(-1.0), kmax = dkey(1.0);
+    for (int64_t k = std::max(kmin, lo - win); k <= lo && ok; ++k)
+        if (!angle_at_least(dfromkey(k), t)) ok = false;
+    for (int64_t k = lo + 1; k <= std::min(kmax, lo + win) && ok; ++k)
+        if (angle_at_least(dfromkey(k), t)) ok = false;
+    *verified = ok ? 1 : 0;
+    return C;
+}
+
+bool edges_valid(const double* e, int ne) {
+    if (!e || ne < 2 || ne > TPCF_MAX_EDGES) return false;
+    for (int k = 0; k < ne; ++k)
+        if (!(e[k] >= 0.0 && e[k] <= 3.141592653589793)) return false;
+    for (int k = 1; k < ne; ++k)
+        if (!(e[k] > e[k - 1])) return false;
+    return true;
+}
+
+void derive_all(const double* edges, int ne, double g, std::vector<double>& C,
+                std::vector<float>& lo, std::vector<float>& hi, std::vector<float>& c32,
+                std::vector<int>& ver) {
+    C.resize(ne); lo.resize(ne); hi.resize(ne); c32.resize(ne); ver.resize(ne);
+    for (int k = 0; k < ne; ++k) {
+        C[k] = derive_threshold(edges[k], &ver[k]);
+        if (isinf(C[k])) {
+            lo[k] = hi[k] = c32[k] = INFINITY;
+        } else {
+            lo[k] = round_down_f32(C[k] - g);
+            hi[k] = round_up_f32(C[k] + g);
+            c32[k] = (float)C[k];
+        }
+    }
+}
+
+// LUT over the ordered keys of FP32 cosines from T = lo[B] to a little above
+// 1: entry e covers keys [key0 + (e << shift), key0 + ((e + 1) << shift) - 1]
+// and stores P = #{m : v_max < lo_m}, Q = #{m : v_min <= hi_m}.  The last
+// entry also covers everything above and stores P = 0 (always resolved by
+// explicit comparisons).
+void build_lut(const std::vector<float>& lo, const std::vector<float>& hi, std::vector<uint32_t>& lut,
+               int32_t* key0_out, int* shift_out) {
+    const int ne = (int)lo.size();
+    const float T = lo[ne - 1];
+    const int64_t key0 = fkey(T);
+    const int64_t key_hi = (int64_t)fkey(1.0f) + 64;
+    const int64_t span = key_hi - key0 + 1;
+    int shift = 0;
+    while (((span - 1) >> shift) + 1 > kLutMax) ++shift;
+    const int nlut = (int)(((span - 1) >> shift) + 1);
+    lut.assign(nlut, 0);
+    for (int e = 0; e < nlut; ++e) {
+        const int64_t ka = key0 + ((int64_t)e << shift);
+        const int64_t kb = std::min(key0 + (((int64_t)e + 1) << shift) - 1, key_hi);
+        const float va = ffromkey(ka), vb = ffromkey(kb);
+        uint32_t P = 0, Q = 0;
+        for (int m = 0; m < ne; ++m) {
+            P += (vb < lo[m]);
+            Q += (va <= hi[m]);
+        }
+        if (e == nlut - 1) P = 0;
+        lut[e] = P | (Q << 16);
+    }
+    *key0_out = (int32_t)key0;
+    *shift_out = shift;
+}
+
+}  // namespace
+
+extern "C" int tpcf_bins_thresholds(const double* edges, int nedges, double guard, double* cos_thr,
+                                    float* lo, float* hi, int* verified) {
+    if (!edges_valid(edges, nedges)) return TPCF_EINVAL;
+    if (guard == 0.0) guard = kDefaultGuard;
+    if (!(guard > 0.0 && guard < 0.25)) return TPCF_EINVAL;
+    std::vector<double> C;
+    std::vector<float> l, h, c;
+    std::vector<int> v;
+    derive_all(edges, nedges, guard, C, l, h, c, v);
+    for (int k = 0; k < nedges; ++k) {
+        if (cos_thr) cos_thr[k] = C[k];
+        if (lo) lo[k] = l[k];
+        if (hi) hi[k] = h[k];
+        if (verified) verified[k] = v[k];
+    }
+    return TPCF_OK;
+}
+
+extern "C" int tpcf_bins_create(tpcf_ctx* ctx, const double* edges, int nedges, tpcf_bins** out) {
+    if (!ctx || !out) return TPCF_EINVAL;
+    *out = nullptr;
+    if (!edges_valid(edges, nedges))
+        return ctx->fail(TPCF_EINVAL, "edges: need 2..%d strictly increasing values in [0, pi]",
+                         TPCF_MAX_EDGES);
+    cudaSetDevice(ctx->cfg.device);
+    tpcf_bins* b = new tpcf_bins();
+    b->ctx = ctx;
+    b->nedges = nedges;
+    b->edges.assign(edges, edges + nedges);
+    derive_all(edges, nedges, ctx->cfg.guard_band, b->cos_thr, b->lo, b->hi, b->c32, b->verified);
+    int32_t key0;
+    int shift;
+    build_lut(b->lo, b->hi, b->lut, &key0, &shift);
+    // one device buffer: C (double), lo, hi, c32 (float), lut (uint32)
+    const size_t nd = (size_t)nedges * 8, nf = (size_t)nedges * 4, nl = b->lut.size() * 4;
+    const size_t off_lo = (nd + 15) / 16 * 16, off_hi = off_lo + (nf + 15) / 16 * 16,
+                 off_c32 = off_hi + (nf + 15) / 16 * 16, off_lut = off_c32 + (nf + 15) / 16 * 16,
+                 total = off_lut + nl;
+    std::vector<unsigned char> host(total, 0);
+    memcpy(host.data(), b->cos_thr.data(), nd);
+    memcpy(host.data() + off_lo, b->lo.data(), nf);
+    memcpy(host.data() + off_hi, b->hi.data(), nf);
+    memcpy(host.data() + off_c32, b->c32.data(), nf);
+    memcpy(host.data() + off_lut, b->lut.data(), nl);
+    auto cleanup = [&](int code) {
+        if (b->dev_buf) cudaFree(b->dev_buf);
+        if (b->dev_desc) cudaFree(b->dev_desc);
+        delete b;
+        return ctx->fail(code, "bins: device allocation or copy failed");
+    };
+    if (dev_malloc(&b->dev_buf, total) != cudaSuccess) return cleanup(TPCF_ENOMEM);
+    if (cudaMemcpy(b->dev_buf, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
+        return cleanup(TPCF_ECUDA);
+    unsigned char* base = (unsigned char*)b->dev_buf;
+    b->host.cos_thr = (const double*)base;
+    b->host.lo = (const float*)(base + off_lo);
+    b->host.hi = (const float*)(base + off_hi);
+    b->host.cos32 = (const float*)(base + off_c32);
+    b->host.lut = (const uint32_t*)(base + off_lut);
+    b->host.nedges = nedges;
+    b->host.nlut = (int)b->lut.size();
+    b->host.lut_shift = shift;
+    b->host.lut_key0 = key0;
+    b->host.range_t = b->lo[nedges - 1];
+    b->host.cos_last = b->cos_thr[nedges - 1];
+    if (dev_malloc((void**)&b->dev_desc, sizeof(BinsDev)) != cudaSuccess) return cleanup(TPCF_ENOMEM);
+    if (cudaMemcpy(b->dev_desc, &b->host, sizeof(BinsDev), cudaMemcpyHostToDevice) != cudaSuccess)
+        return cleanup(TPCF_ECUDA);
+    *out = b;
+    return TPCF_OK;
+}
+
+extern "C" int tpcf_bins_destroy(tpcf_bins* b) {
+    if (!b) return TPCF_EINVAL;
+    cudaSetDevice(b->ctx->cfg.device);
+    cudaDeviceSynchronize();
+    if (b->dev_buf) cudaFree(b->dev_buf);
+    if (b->dev_desc) cudaFree(b->dev_desc);
+    delete b;
+    return TPCF_OK;
+}
+
+// ====================================================================== catalogs
+extern "C" int tpcf_catalog_create_segmented(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where,
+                                             const uint64_t* offsets, int nseg, void* stream_v,
+                                             tpcf_catalog** out) {
+    if (!ctx || !out) return TPCF_EINVAL;
+    *out = nullptr;
+    if (n > TPCF_MAX_POINTS) return ctx->fail(TPCF_EOVERFLOW, "catalog: %llu points > limit",
+                                              (unsigned long long)n);
+    if (n > 0 && !xyz) return ctx->fail(TPCF_EINVAL, "catalog: NULL coordinates");
+    if (where != TPCF_HOST && where != TPCF_DEVICE) return ctx->fail(TPCF_EINVAL, "catalog: bad where");
+    if (nseg < 0 || (nseg > 0 && !offsets)) return ctx->fail(TPCF_EINVAL, "catalog: bad segments");
+    if (nseg > 0) {
+        if (offsets[0] != 0 || offsets[nseg] != n)
+            return ctx->fail(TPCF_EINVAL, "catalog: offsets must start at 0 and end at n");
+        for (int s = 0; s < nseg; ++s)
+            if (offsets[s + 1] < offsets[s]) return ctx->fail(TPCF_EINVAL, "catalog: offsets decrease");
+        if (nseg > 65535) return ctx->fail(TPCF_EOVERFLOW, "catalog: too many segments");
+    }
+    cudaSetDevice(ctx->cfg.device);
+    cudaStream_t st = (cudaStream_t)stream_v;
+    tpcf_catalog* c = new tpcf_catalog();
+    c->ctx = ctx;
+    c->n = n;
+    c->n_pad = (uint32_t)(((n + kPad - 1) / kPad) * kPad);
+    if (c->n_pad == 0) c->n_pad = kPad;
+    if (nseg > 0) c->offsets.assign(offsets, offsets + nseg + 1);
+    const bool sort = !(ctx->cfg.flags & TPCF_F_NO_SORT);
+    uint32_t n_pow2 = 2048;
+    while (n_pow2 < n) n_pow2 <<= 1;
+
+    void* tmp_in = nullptr;
+    unsigned long long* keys = nullptr;
+    uint32_t* vals = nullptr;
+    uint32_t* seg = nullptr;
+    unsigned long long* err = nullptr;
+    int rc = TPCF_OK;
+    auto release = [&]() {
+        if (tmp_in) cudaFreeAsync(tmp_in, st);
+        if (keys) cudaFreeAsync(keys, st);
+        if (vals) cudaFreeAsync(vals, st);
+        if (seg) cudaFreeAsync(seg, st);
+        if (err) cudaFreeAsync(err, st);
+        cudaStreamSynchronize(st);
+    };
+    auto fail_with = [&](int code, const char* what) {
+        release();
+        if (c->d64) cudaFree(c->d64);
+        if (c->d32) cudaFree(c->d32);
+        delete c;
+        return ctx->fail(code, "catalog: %s", what);
+    };
+    if (dev_malloc((void**)&c->d64, (size_t)c->n_pad * sizeof(Point64)) != cudaSuccess ||
+        dev_malloc((void**)&c->d32, (size_t)c->n_pad * sizeof(float4)) != cudaSuccess)
+        return fail_with(TPCF_ENOMEM, "device allocation failed");
+    const double* in = xyz;
+    if (n > 0 && where == TPCF_HOST) {
+        if (cudaMallocAsync(&tmp_in, n * 24, st) != cudaSuccess)
+            return fail_with(TPCF_ENOMEM, "staging allocation failed");
+        if (cudaMemcpyAsync(tmp_in, xyz, n * 24, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return fail_with(TPCF_ECUDA, "host-to-device copy failed");
+        in = (const double*)tmp_in;
+    }
+    if (cudaMallocAsync((void**)&err, 8, st) != cudaSuccess ||
+        cudaMallocAsync((void**)&keys, (size_t)n_pow2 * 8, st) != cudaSuccess ||
+        cudaMallocAsync((void**)&vals, (size_t)n_pow2 * 4, st) != cudaSuccess)
+        return fail_with(TPCF_ENOMEM, "scratch allocation failed");
+    if (cudaMemsetAsync(err, 0, 8, st) != cudaSuccess) return fail_with(TPCF_ECUDA, "memset failed");
+    if (nseg > 0 && n > 0) {
+        std::vector<uint32_t> hs(n);
+        for (int s = 0; s < nseg; ++s)
+            for (uint64_t i = offsets[s]; i < offsets[s + 1]; ++i) hs[i] = (uint32_t)s;
+        if (cudaMallocAsync((void**)&seg, n * 4, st) != cudaSuccess)
+            return fail_with(TPCF_ENOMEM, "segment allocation failed");
+        if (cudaMemcpyAsync(seg, hs.data(), n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return fail_with(TPCF_ECUDA, "segment copy failed");
+    }
+    cudaError_t e = launch_prepare(in, (uint32_t)n, seg, sort ? 1 : 0, c->d64, c->d32, c->n_pad, keys,
+                                   vals, n_pow2, err, st);
+    if (e != cudaSuccess) return fail_with(TPCF_ECUDA, cudaGetErrorString(e));
+    unsigned long long herr = 0;
+    if (cudaMemcpyAsync(&herr, err, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail_with(TPCF_ECUDA, "preparation failed");
+    if (herr & kErrBadPoint) {
+        rc = TPCF_EINVAL;
+        return fail_with(rc, "a point is not finite or not a unit vector (| |v| - 1 | > 1e-6)");
+    }
+    release();
+    *out = c;
+    return TPCF_OK;
+}
+
+extern "C" int tpcf_catalog_create(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where,
+                                   void* stream, tpcf_catalog** out) {
+    return tpcf_catalog_create_segmented(ctx, xyz, n, where, nullptr, 0, stream, out);
+}
+
+extern "C" int tpcf_catalog_destroy(tpcf_catalog* c) {
+    if (!c) return TPCF_EINVAL;
+    cudaSetDevice(c->ctx->cfg.device);
+    cudaDeviceSynchronize();
+    if (c->d64) cudaFree(c->d64);
+    if (c->d32) cudaFree(c->d32);
+    delete c;
+    return TPCF_OK;
+}
+
+extern "C" uint64_t tpcf_catalog_size(const tpcf_catalog* c) { return c ? c->n : 0; }
+
+// ====================================================================== shapes
+namespace {
+
+struct SubSpec {
+    const tpcf_catalog* a;
+    const tpcf_catalog* b;
+    bool auto_mode;
+    uint32_t na, nb;        // counts (segments: sub-ranges)
+    uint32_t a_off, b_off;  // first point of the range in the catalog
+};
+
+bool choose_shape(tpcf_ctx* ctx, int precision, int nedges, uint64_t total_pairs, Shape* sh) {
+    const bool plain = precision == TPCF_PLAIN_FP64;
+    const tpcf_config& cfg = ctx->cfg;
+    // candidate (T, R): the override, or by problem size, then smaller blocks
+    // when the per-thread histograms do not fit in shared memory
+    int cand[3][2];
+    int nc = 0;
+    if (cfg.threads != 0 && cfg.ipt != 0) {
+        cand[nc][0] = cfg.threads; cand[nc][1] = cfg.ipt; ++nc;
+    } else {
+        const double per_sm = (double)total_pairs / std::max(1, ctx->num_sms);
+        if (per_sm >= 4e7) { cand[nc][0] = 256; cand[nc][1] = 8; ++nc; }
+        cand[nc][0] = 128; cand[nc][1] = 8; ++nc;
+    }
+    for (int c = 0; c < nc; ++c) {
+        const int T = cand[c][0], R = cand[c][1];
+        if (!count_shape_supported(T, R)) continue;
+        const int I = T * R;
+        int J = cfg.jtile ? cfg.jtile : (plain ? 1024 : 2048);
+        if (J > I) J = I;
+        if ((int)kPad % J != 0 || (int)kPad % I != 0 || J % 32 != 0 || I % J != 0) continue;
+        size_t smem = count_smem_bytes(precision, T, R, J, 2, nedges);
+        while (smem > ctx->smem_optin && J > 256 && cfg.jtile == 0) {
+            J /= 2;
+            smem = count_smem_bytes(precision, T, R, J, 2, nedges);
+        }
+        if (smem > ctx->smem_optin) continue;
+        sh->threads = T;
+        sh->ipt = R;
+        sh->jtile = J;
+        sh->stages = 2;
+        sh->smem = smem;
+        sh->blocks = ctx->num_sms;  // one persistent block per SM
+        sh->jchunk = I;
+        return true;
+    }
+    return false;
+}
+
+uint64_t full_pairs(const SubSpec& s) {
+    return s.auto_mode ? (uint64_t)s.na * (s.na ? s.na - 1 : 0) / 2 : (uint64_t)s.na * s.nb;
+}
+
+// Pairs of sub-problem `sp` inside the global item range [lo, hi).
+uint64_t range_pairs(const SubProblem& sp, uint64_t lo, uint64_t hi, uint32_t I, uint32_t Jc,
+                     uint32_t J) {
+    uint64_t a = std::max(lo, sp.item_begin), b = std::min(hi, sp.item_begin + sp.n_items);
+    uint64_t total = 0;
+    for (uint64_t q = a; q < b; ++q) {
+        ItemGeom g = item_geom(q - sp.item_begin, sp.na, sp.nb, sp.n_iblk, sp.n_jchunk,
+                               sp.auto_mode != 0, I, Jc, J);
+        if (g.t_first < g.t_end) total += item_pairs(g, sp.na, sp.nb, sp.auto_mode != 0, I, Jc);
+    }
+    return total;
+}
+
+int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* bins,
+               cudaStream_t st, unsigned long long* const* outs, int where, tpcf_stats* stats) {
+    if (where != TPCF_HOST && where != TPCF_DEVICE) return ctx->fail(TPCF_EINVAL, "bad where");
+    if (where == TPCF_DEVICE && stats) return ctx->fail(TPCF_EINVAL, "stats need where = TPCF_HOST");
+    if (!bins || bins->ctx != ctx) return ctx->fail(TPCF_EINVAL, "bins missing or from another context");
+    for (int s = 0; s < nsub; ++s) {
+        if (!outs[s]) return ctx->fail(TPCF_EINVAL, "NULL histogram");
+        if (!specs[s].a || !specs[s].b || specs[s].a->ctx != ctx || specs[s].b->ctx != ctx)
+            return ctx->fail(TPCF_EINVAL, "catalog missing or from another context");
+    }
+    cudaSetDevice(ctx->cfg.device);
+    const int ne = bins->nedges;
+    const int prec = ctx->cfg.precision;
+    uint64_t all_pairs = 0;
+    for (int s = 0; s < nsub; ++s) all_pairs += full_pairs(specs[s]);
+    Shape sh;
+    if (!choose_shape(ctx, prec, ne, all_pairs, &sh))
+        return ctx->fail(TPCF_EINVAL, "no kernel shape fits (threads=%d ipt=%d jtile=%d)",
+                         ctx->cfg.threads, ctx->cfg.ipt, ctx->cfg.jtile);
+    const uint32_t I = (uint32_t)(sh.threads * sh.ipt), J = (uint32_t)sh.jtile;
+    uint32_t Jc = (uint32_t)sh.jchunk;
+
+    // ---- slot
+    const uint32_t si = ctx->slot_rr.fetch_add(1) % kSlots;
+    tpcf_ctx::Slot& slot = ctx->slots[si];
+    std::lock_guard<std::mutex> slot_lock(slot.mu);
+    CUDA_TRY(ctx, cudaStreamWaitEvent(st, slot.ev, 0));
+    CUDA_TRY(ctx, cudaMemsetAsync(slot.dev, 0, kSlotWords * 8, st));
+
+    WorkDesc wd;
+    memset(&wd, 0, sizeof wd);
+    uint64_t items = 0;
+    for (int s = 0; s < nsub; ++s) {
+        const SubSpec& p = specs[s];
+        SubProblem& sp = wd.sub[s];
+        sp.a32 = p.a->d32 + p.a_off;
+        sp.b32 = p.b->d32 + p.b_off;
+        sp.a64 = p.a->d64 + p.a_off;
+        sp.b64 = p.b->d64 + p.b_off;
+        sp.na = p.na;
+        sp.nb = p.nb;
+        sp.n_iblk = (p.na + I - 1) / I;
+        sp.n_jchunk = (p.nb + Jc - 1) / Jc;
+        sp.auto_mode = p.auto_mode ? 1u : 0u;
+        sp.kratio = I / Jc;
+        sp.item_begin = items;
+        sp.n_items = (p.na == 0 || p.nb == 0) ? 0 : items_of(sp.n_iblk, sp.n_jchunk, p.auto_mode, I, Jc);
+        sp.hist = slot.dev + (size_t)s * kHistStride;
+        sp.bins = bins->dev_desc;
+        items += sp.n_items;
+    }
+    wd.sub_dev = nullptr;
+    wd.nsub = nsub;
+    wd.item_lo = 0;
+    wd.item_hi = items;
+    if (ctx->cfg.shard_count > 1) {
+        wd.item_lo = items * ctx->cfg.shard_index / ctx->cfg.shard_count;
+        wd.item_hi = items * (ctx->cfg.shard_index + 1) / ctx->cfg.shard_count;
+    }
+    wd.stats = slot.dev + kStatOff;
+    wd.I = I;
+    wd.J = J;
+    wd.Jc = Jc;
+    wd.flags = ctx->cfg.flags;
+    wd.nedges_max = ne;
+    wd.wait_limit_ns = (uint64_t)ctx->cfg.wait_timeout_us * 1000ull;
+
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (stats) {
+        CUDA_TRY(ctx, cudaEventCreate(&t0));
+        CUDA_TRY(ctx, cudaEventCreate(&t1));
+        CUDA_TRY(ctx, cudaEventRecord(t0, st));
+    }
+    uint32_t launches = 1;  // memset is not a kernel of ours
+    if (wd.item_hi > wd.item_lo) {
+        const uint64_t n_launch_items = wd.item_hi - wd.item_lo;
+        Shape sl = sh;
+        if ((uint64_t)sl.blocks > n_launch_items) sl.blocks = (int)n_launch_items;
+        CUDA_TRY(ctx, count_set_smem_limit(prec, sh.threads, sh.ipt, sh.smem));
+        CUDA_TRY(ctx, launch_count(wd, sl, prec, ne, st));
+        ++launches;
+    }
+    if (stats) CUDA_TRY(ctx, cudaEventRecord(t1, st));
+    // ---- finalize each histogram
+    for (int s = 0; s < nsub; ++s) {
+        uint64_t total = full_pairs(specs[s]);
+        if (ctx->cfg.shard_count > 1)
+            total = range_pairs(wd.sub[s], wd.item_lo, wd.item_hi, I, Jc, J);
+        unsigned long long* acc = wd.sub[s].hist;
+        unsigned long long* dst = where == TPCF_DEVICE ? outs[s] : acc;
+        CUDA_TRY(ctx, launch_finalize(acc, ne, dst, total, wd.stats + kStatError, st));
+        ++launches;
+    }
+    int rc = TPCF_OK;
+    if (where == TPCF_HOST) {
+        std::vector<unsigned long long> h(kSlotWords);
+        CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), slot.dev, kSlotWords * 8, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        for (int s = 0; s < nsub; ++s)
+            memcpy(outs[s], h.data() + (size_t)s * kHistStride, (size_t)(ne + 1) * 8);
+        const unsigned long long errw = h[kStatOff + kStatError];
+        if (stats) {
+            memset(stats, 0, sizeof *stats);
+            stats->pairs = h[kStatOff + kStatPairs];
+            stats->band_pairs = h[kStatOff + kStatBand];
+            stats->band_mismatch = h[kStatOff + kStatMismatch];
+            stats->device_error = (uint32_t)errw;
+            stats->launches = launches;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            stats->kernel_ms = ms;
+        }
+        if (errw & kErrWaitTimeout) rc = ctx->fail(TPCF_ETIMEOUT, "a bounded device wait timed out");
+        else if (errw) rc = ctx->fail(TPCF_ECUDA, "device error word 0x%llx", errw);
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    CUDA_TRY(ctx, cudaEventRecord(slot.ev, st));
+    return rc;
+}
+
+}  // namespace
+
+// ====================================================================== counting ABI
+extern "C" int tpcf_count_auto(tpcf_ctx* ctx, const tpcf_catalog* cat, const tpcf_bins* bins,
+                               void* stream, uint64_t* hist, int where, tpcf_stats* st) {
+    if (!ctx || !cat) return ctx ? ctx->fail(TPCF_EINVAL, "NULL catalog") : TPCF_EINVAL;
+    SubSpec s{cat, cat, true, (uint32_t)cat->n, (uint32_t)cat->n, 0, 0};
+    unsigned long long* outs[1] = {(unsigned long long*)hist};
+    return run_counts(ctx, &s, 1, bins, (cudaStream_t)stream, outs, where, st);
+}
+
+extern "C" int tpcf_count_cross(tpcf_ctx* ctx, const tpcf_catalog* d, const tpcf_catalog* r,
+                                const tpcf_bins* bins, void* stream, uint64_t* hist, int where,
+                                tpcf_stats* st) {
+    if (!ctx || !d || !r) return ctx ? ctx->fail(TPCF_EINVAL, "NULL catalog") : TPCF_EINVAL;
+    SubSpec s{d, r, false, (uint32_t)d->n, (uint32_t)r->n, 0, 0};
+    unsigned long long* outs[1] = {(unsigned long long*)hist};
+    return run_counts(ctx, &s, 1, bins, (cudaStream_t)stream, outs, where, st);
+}
+
+extern "C" int tpcf_count_all(tpcf_ctx* ctx, const tpcf_catalog* d, const tpcf_catalog* r,
+                              const tpcf_bins* bins, void* stream, uint64_t* dd, uint64_t* dr,
+                              uint64_t* rr, int where, tpcf_stats* st) {
+    if (!ctx || !d || !r) return ctx ? ctx->fail(TPCF_EINVAL, "NULL catalog") : TPCF_EINVAL;
+    // Largest first (RR, DR, DD when nr >= nd) so the tail of the launch is the cheapest work.
+    SubSpec s[3] = {{r, r, true, (uint32_t)r->n, (uint32_t)r->n, 0, 0},
+                    {d, r, false, (uint32_t)d->n, (uint32_t)r->n, 0, 0},
+                    {d, d, true, (uint32_t)d->n, (uint32_t)d->n, 0, 0}};
+    unsigned long long* outs[3] = {(unsigned long long*)rr, (unsigned long long*)dr,
+                                   (unsigned long long*)dd};
+    return run_counts(ctx, s, 3, bins, (cudaStream_t)stream, outs, where, st);
+}
+
+// ====================================================================== estimator
+extern "C" int tpcf_estimate(const uint64_t* dd, const uint64_t* dr, const uint64_t* rr, int nbins,
+                             uint64_t nd, uint64_t nr, int estimator, double* w) {
+    if (!dd || !dr || !rr || !w || nbins < 1 || nd < 2 || nr < 2 || nd > 0xffffffffull ||
+        nr > 0xffffffffull)
+        return TPCF_EINVAL;
+    if (estimator != TPCF_LS_EXACT && estimator != TPCF_LS_PAPER) return TPCF_EINVAL;
+    // Denominators from exact integer pair counts (nd, nr < 2^32 keeps them exact in uint64).
+    const double p_dd = (double)(nd * (nd - 1) / 2);
+    const double p_rr = (double)(nr * (nr - 1) / 2);
+    const double p_dr = (double)nd * (double)nr;
+    const double q = (double)nr / (double)nd;
+    for (int k = 0; k < nbins; ++k) {
+        if (rr[k] == 0) { w[k] = NAN; continue; }
+        if (estimator == TPCF_LS_EXACT) {
+            const double n_dd = (double)dd[k] / p_dd;
+            const double n_rr = (double)rr[k] / p_rr;
+            const double n_dr = (double)dr[k] / p_dr;
+            w[k] = ((n_dd - 2.0 * n_dr) + n_rr) / n_rr;
+        } else {
+            const double dd2 = 2.0 * (double)dd[k];
+            const double rr2 = 2.0 * (double)rr[k];
+            w[k] = (1.0 + (q * q) * (dd2 / rr2)) - ((2.0 * q) * ((double)dr[k] / rr2));
+        }
+    }
+    return TPCF_OK;
+}
+
+extern "C" int tpcf_correlate(tpcf_ctx* ctx, const double* d_xyz, uint64_t nd, const double* r_xyz,
+                              uint64_t nr, const double* edges, int nedges, int estimator,
+                              void* stream, uint64_t* dd, uint64_t* dr, uint64_t* rr, double* w,
+                              tpcf_stats* st) {
+    if (!ctx) return TPCF_EINVAL;
+    if (!edges_valid(edges, nedges)) return ctx->fail(TPCF_EINVAL, "bad edges");
+    tpcf_catalog *cd = nullptr, *cr = nullptr;
+    tpcf_bins* b = nullptr;
+    std::vector<uint64_t> hdd(nedges + 1), hdr(nedges + 1), hrr(nedges + 1);
+    int rc = tpcf_catalog_create(ctx, d_xyz, nd, TPCF_HOST, stream, &cd);
+    if (rc == TPCF_OK) rc = tpcf_catalog_create(ctx, r_xyz, nr, TPCF_HOST, stream, &cr);
+    if (rc == TPCF_OK) rc = tpcf_bins_create(ctx, edges, nedges, &b);
+    if (rc == TPCF_OK)
+        rc = tpcf_count_all(ctx, cd, cr, b, stream, hdd.data(), hdr.data(), hrr.data(), TPCF_HOST, st);
+    if (rc == TPCF_OK && w)
+        rc = tpcf_estimate(hdd.data() + 1, hdr.data() + 1, hrr.data() + 1, nedges - 1, nd, nr,
+                           estimator, w);
+    if (rc == TPCF_OK) {
+        if (dd) memcpy(dd, hdd.data(), hdd.size() * 8);
+        if (dr) memcpy(dr, hdr.data(), hdr.size() * 8);
+        if (rr) memcpy(rr, hrr.data(), hrr.size() * 8);
+    }
+    if (b) tpcf_bins_destroy(b);
+    if (cd) tpcf_catalog_destroy(cd);
+    if (cr) tpcf_catalog_destroy(cr);
+    return rc;
+}
+
+// ====================================================================== host-side self checks
+// Enumerates the items and tiles of one histogram exactly as the kernel does
+// and adds 1 to counts[i * nb + j] for every pair (i, j) an item counts.
+// Returns the number of items; *pairs receives the item_pairs total.
+extern "C" int64_t tpcf_plan_coverage(uint32_t na, uint32_t nb, int auto_mode, uint32_t I,
+                                      uint32_t Jc, uint32_t J, uint32_t* counts, uint64_t* pairs) {
+    if (I == 0 || J == 0 || Jc == 0 || Jc % J != 0 || (I % Jc != 0 && Jc % I != 0)) return -1;
+    if (auto_mode && na != nb) return -1;
+    if (na == 0 || nb == 0) { if (pairs) *pairs = 0; return 0; }
+    const uint32_t n_iblk = (na + I - 1) / I, n_jchunk = (nb + Jc - 1) / Jc;
+    const uint64_t items = items_of(n_iblk, n_jchunk, auto_mode != 0, I, Jc);
+    uint64_t total = 0;
+    for (uint64_t q = 0; q < items; ++q) {
+        ItemGeom g = item_geom(q, na, nb, n_iblk, n_jchunk, auto_mode != 0, I, Jc, J);
+        if (g.t_first >= g.t_end) continue;
+        total += item_pairs(g, na, nb, auto_mode != 0, I, Jc);
+        if (!counts) continue;
+        for (uint32_t t = g.t_first; t < g.t_end; ++t) {
+            const uint32_t jbase = g.j0 + t * J;
+            const bool masked = auto_mode && (jbase < g.i0 + I);  // as in the kernel
+            for (uint32_t ii = 0; ii < I; ++ii) {
+                const uint32_t i = g.i0 + ii;
+                if (i >= na) break;
+                for (uint32_t jj = 0; jj < J; ++jj) {
+                    const uint32_t j = jbase + jj;
+                    if (j >= nb) break;
+                    if (masked && !(j > i)) continue;
+                    counts[(uint64_t)i * nb + j] += 1;
+                }
+            }
+        }
+    }
+    if (pairs) *pairs = total;
+    return (int64_t)items;
+}

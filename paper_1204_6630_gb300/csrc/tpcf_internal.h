@@ -1,0 +1,104 @@
+// Internal types shared by the host runtime (runtime.cpp) and the kernels
+// (kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tpcf {
+
+// Catalog padding: every device catalog holds a multiple of this many
+// points; points past n are zero vectors (never counted, see kernels.cu).
+constexpr uint32_t kPad = 4096;
+
+// Lookup table from FP32 cosine to the candidate histogram index range.
+constexpr int kLutMax = 4096;
+
+// Binary64 point (x, y, z, 0), 32-byte aligned for two 16-byte loads.
+struct __align__(32) Point64 {
+    double x, y, z, w;
+};
+
+// Device-resident description of one bin set (Section 3: angle -> bin).
+// All arrays live in one device allocation owned by tpcf_bins.
+struct BinsDev {
+    const double* cos_thr;  // [nedges] C_k, decreasing (C_0 may be +inf)
+    const float* lo;        // [nedges] RD(C_k - g)
+    const float* hi;        // [nedges] RU(C_k + g)
+    const float* cos32;     // [nedges] RN(C_k): FP32-only classification (statistics)
+    const uint32_t* lut;    // [nlut] (P | Q << 16): see kernels.cu
+    int nedges;             // B + 1
+    int nlut;
+    int lut_shift;
+    int32_t lut_key0;       // ordered key of lo[B] (the range limit T)
+    float range_t;          // T = lo[B]: an FP32 cosine below T is certainly overflow
+    double cos_last;        // C_B (binary64 range limit, plain kernel)
+};
+
+// One histogram to fill: auto count over catalog A (B == A, pairs j > i) or
+// cross count A x B (all pairs).  Work is cut into items: (i-block of I points)
+// x (j-chunk of Jc points); an item is processed in j-tiles of J points.
+struct SubProblem {
+    const float4* a32;    // FP32 screen copy of A (padded to kPad)
+    const float4* b32;
+    const Point64* a64;   // binary64 copy of A (padded)
+    const Point64* b64;
+    uint32_t na, nb;      // real point counts
+    uint32_t n_iblk;      // ceil(na / I)
+    uint32_t n_jchunk;    // ceil(nb / Jc)
+    uint32_t auto_mode;   // 1: A == B, count j > i only
+    uint32_t kratio;      // I / Jc (auto mode: first chunk of i-block ib is ib * kratio)
+    uint64_t item_begin;  // global index of this sub-problem's first item
+    uint64_t n_items;
+    unsigned long long* hist;   // B + 2 accumulators (device)
+    const BinsDev* bins;        // device pointer to this sub-problem's bins
+};
+
+constexpr int kMaxInlineSub = 3;
+
+// Device statistics words (per call, in the scratch slot after the histograms).
+enum StatWord { kStatPairs = 0, kStatBand = 1, kStatMismatch = 2, kStatError = 3,
+                kStatWork = 4, kStatWords = 8 };
+
+// Device error word bits.
+enum : uint32_t { kErrWaitTimeout = 1u, kErrBadHist = 2u, kErrBadPoint = 4u, kErrSortOverflow = 8u };
+
+struct WorkDesc {
+    SubProblem sub[kMaxInlineSub];   // used when sub_dev == nullptr
+    const SubProblem* sub_dev;       // device array of nsub sub-problems (batched launches)
+    int nsub;
+    uint64_t item_lo, item_hi;       // item range of this launch (shards, serving quanta)
+    unsigned long long* stats;       // kStatWords words
+    uint32_t I, J, Jc;               // i-block, j-tile, j-chunk sizes (points)
+    uint32_t flags;                  // TPCF_F_* subset used on the device
+    int nedges_max;                  // largest B + 1 over the sub-problems (shared-memory sizing)
+    uint64_t wait_limit_ns;          // bounded waits
+};
+
+// Kernel shape selected on the host.
+struct Shape {
+    int threads;   // T
+    int ipt;       // R
+    int jtile;     // J
+    int jchunk;    // Jc
+    int stages;    // S
+    int blocks;    // grid size
+    size_t smem;   // dynamic shared memory bytes
+};
+
+// Launchers (kernels.cu).  All are asynchronous in `stream` and return a
+// cudaError_t from the launch.
+cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int precision, int nedges,
+                         cudaStream_t stream);
+cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long long* out,
+                            unsigned long long total, unsigned long long* err_word,
+                            cudaStream_t stream);
+cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
+                           int sort, Point64* out64, float4* out32, uint32_t n_pad,
+                           unsigned long long* key_scratch, uint32_t* val_scratch,
+                           uint32_t n_pow2, unsigned long long* err_word, cudaStream_t stream);
+size_t count_smem_bytes(int precision, int threads, int ipt, int jtile, int stages, int nedges);
+bool count_shape_supported(int threads, int ipt);
+cudaError_t count_set_smem_limit(int precision, int threads, int ipt, size_t bytes);
+
+}  // namespace tpcf
