@@ -87,6 +87,7 @@ extern "C" {
 /* configuration flags */
 #define TPCF_F_NO_SORT 0x1u          /* keep catalog order (no spatial sort on the device) */
 #define TPCF_F_DYNAMIC_SCHED 0x2u    /* persistent blocks take work from an atomic counter */
+#define TPCF_F_SCALAR_FMA 0x4u       /* FP32 screen with scalar FMA instead of packed FP32x2 FMA */
 #define TPCF_F_TEST_WAIT_TIMEOUT 0x100u /* test hook: the first j-tile copy of each counting
                                            launch is never issued, so its bounded wait expires
                                            and the call returns TPCF_ETIMEOUT */
@@ -103,14 +104,16 @@ typedef struct tpcf_bins tpcf_bins;
 typedef struct tpcf_config {
     int device;                /* CUDA device ordinal */
     int precision;             /* TPCF_SCREEN_RECHECK or TPCF_PLAIN_FP64 */
-    double guard_band;         /* half-width g of the recheck band in cos(theta); 0 -> 2^-20.
-                                  Must exceed the FP32 screen's error bound (about 9 * 2^-24). */
+    double guard_band;         /* half-width g of the recheck band in cos(theta); 0 -> 6 * 2^-24.
+                                  Must be >= 6 * 2^-24: the FP32 cosine is within 5.0001 * 2^-24
+                                  of the binary64 dot product (TPCF_EINVAL below that). */
     uint64_t hbm_budget_bytes; /* device memory the job server may hold for catalogs; 0 -> 120 GB
                                   capped at 80% of free memory */
     uint32_t flags;            /* TPCF_F_* */
     int threads;               /* kernel shape override: threads per block (0 = tuned default) */
     int ipt;                   /* kernel shape override: i-points per thread (0 = default) */
     int jtile;                 /* kernel shape override: j-points per shared-memory tile (0 = default) */
+    int stages;                /* kernel shape override: shared-memory pipeline stages 2..16 (0 = default) */
     uint32_t shard_index;      /* multi-process split of the pair tiles: this process's index */
     uint32_t shard_count;      /* number of shards (0 or 1 = no split); histograms of all
                                   shards sum to the unsplit result exactly */
@@ -132,10 +135,12 @@ const char *tpcf_strerror(int status);
 /* Last error message recorded on ctx (empty string if none).  Not thread-safe
  * with respect to concurrent failing calls on the same context. */
 const char *tpcf_last_error(const tpcf_ctx *ctx);
-/* Fills *cfg with the defaults (device 0, screen + recheck, g = 2^-20). */
+/* Fills *cfg with the defaults (device 0, screen + recheck, g = 6 * 2^-24). */
 void tpcf_config_default(tpcf_config *cfg);
 /* Library version as major * 10000 + minor * 100 + patch. */
 int tpcf_version(void);
+/* Number of this library's kernels launched through ctx so far (telemetry). */
+uint64_t tpcf_kernel_launches(const tpcf_ctx *ctx);
 
 /* ------------------------------------------------------------------ context */
 /* Creates a context on cfg->device (NULL cfg = defaults).  Allocates the
@@ -178,7 +183,7 @@ int tpcf_bins_create(tpcf_ctx *ctx, const double *edges_rad, int nedges, tpcf_bi
 int tpcf_bins_destroy(tpcf_bins *bins);
 /* Host-only: the thresholds for edges_rad (no context or GPU needed).
  * cos_thr[k] = C_k (+inf for t_k = 0); lo[k], hi[k] the FP32 screen bounds for
- * guard band g (0 -> 2^-20); verified[k] = 1 when the neighbour scan around
+ * guard band g (0 -> 6 * 2^-24); verified[k] = 1 when the neighbour scan around
  * C_k covered at least 4 ulps of t_k on each side and found the predicate
  * monotone, 0 otherwise.  Any output pointer may be NULL. */
 int tpcf_bins_thresholds(const double *edges_rad, int nedges, double guard_band, double *cos_thr,
@@ -228,15 +233,18 @@ int tpcf_correlate(tpcf_ctx *ctx, const double *d_xyz, uint64_t nd, const double
  *
  * tpcf_plan_coverage: enumerates the work items and tiles the counting kernel
  * uses for one histogram (na x nb points, i-block I, j-chunk Jc, j-tile J;
- * auto_mode = 1 for an auto count, na == nb) and adds 1 to counts[i * nb + j]
- * (host array of na * nb, may be NULL) for every pair the kernel would count.
- * Returns the number of items (-1 on bad sizes); *pairs (may be NULL) gets the
- * sum of the per-item pair counts the kernel reports.
+ * auto_mode = 1 for an auto count, na == nb), restricted to shard
+ * shard_index of shard_count (shard_count 0 or 1 = all items, the split of
+ * tpcf_config.shard_*), and adds 1 to counts[i * nb + j] (host array of
+ * na * nb, may be NULL) for every pair the kernel would count.  Returns the
+ * number of items (-1 on bad sizes); *pairs (may be NULL) gets the sum of the
+ * per-item pair counts the kernel reports.
  *
  * tpcf_debug_fail_alloc_after: the n-th following device allocation made by
  * the library fails with TPCF_ENOMEM (n = -1 switches this off). */
 int64_t tpcf_plan_coverage(uint32_t na, uint32_t nb, int auto_mode, uint32_t I, uint32_t Jc,
-                           uint32_t J, uint32_t *counts, uint64_t *pairs);
+                           uint32_t J, uint32_t shard_index, uint32_t shard_count, uint32_t *counts,
+                           uint64_t *pairs);
 void tpcf_debug_fail_alloc_after(int n);
 
 #ifdef __cplusplus

@@ -97,6 +97,32 @@ __device__ __forceinline__ int32_t f32_key(float v) {
     return b >= 0 ? b : -(b & 0x7fffffff);
 }
 
+// Packed FP32x2 helpers (sm_100+): two lanes of FP32 in one 64-bit register pair.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo_of(unsigned long long v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    (void)b;
+    return a;
+}
+__device__ __forceinline__ float hi_of(unsigned long long v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    (void)a;
+    return b;
+}
+// d = a * b + c on both halves, each rounded to nearest (fma.rn.f32x2).
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // ============================================================== work cursor
 // Enumerates (item, tile) pairs of one block in processing order.  The
 // consumer (all threads) and the producer (thread 0, S tiles ahead) each
@@ -153,26 +179,37 @@ __device__ void cursor_next(const WorkDesc& wd, Cursor& c) {
 }
 
 // ============================================================== shared-memory layout
+// Kernel variants: FP32 screen with scalar FMA, all-binary64 comparator, FP32
+// screen with packed FP32x2 FMA (j-points staged as (x,x,y,y),(z,z,0,0)).
+enum KernelMode { kModeScreen = 0, kModePlain = 1, kModeScreen2 = 2 };
+
+// Block-wide control words (all int32 in shared memory).
+enum Ctl { kCtlAbort = 0, kCtlWarpsDone = 1, kCtlIssued = 2, kCtlRelease = 8, kCtlQueue = 24,
+           kCtlWords = 64 };
+constexpr int kMaxStages = 16;   // release counters live at kCtlRelease + stage
+constexpr int kQueuePerWarp = 64;
+
 struct SmemLayout {
-    uint32_t bars;      // S mbarriers
-    uint32_t flags;     // abort flag etc.
+    uint32_t bars;      // S full mbarriers
+    uint32_t ctl;       // control words
     uint32_t stage;     // S * J * pt_bytes
-    uint32_t hist;      // (nedges + 1) * T uint32
+    uint32_t hist;      // (nedges + 1) * T uint32: row h, column tid
     uint32_t cos_thr;   // nedges doubles
     uint32_t lo, hi, cos32;  // nedges floats each
     uint32_t lut;       // kLutMax uint32 (screen only)
-    uint32_t red;       // 64 uint64 scratch for block reductions
+    uint32_t queue;     // W * kQueuePerWarp band entries (uint4, screen only)
     uint32_t total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(bool plain, int T, int J, int S, int nedges) {
+__host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S, int nedges) {
     SmemLayout L;
-    uint32_t pt = plain ? 32u : 16u;
+    const bool plain = mode == kModePlain;
+    const uint32_t pt = mode == kModeScreen ? 16u : 32u;
     uint32_t off = 0;
-    L.bars = off; off += 8 * 8;
-    L.flags = off; off += 64;
+    L.bars = off; off += kMaxStages * 8;
+    L.ctl = off; off += kCtlWords * 4;
     off = align_up(off, 128);
     L.stage = off; off += (uint32_t)S * J * pt;
     L.hist = off; off += (uint32_t)(nedges + 1) * T * 4;
@@ -184,7 +221,7 @@ __host__ __device__ inline SmemLayout smem_layout(bool plain, int T, int J, int 
     off = align_up(off, 16);
     L.lut = off; off += plain ? 0u : (uint32_t)kLutMax * 4;
     off = align_up(off, 16);
-    L.red = off; off += 64 * 8;
+    L.queue = off; off += plain ? 0u : (uint32_t)(T / 32) * kQueuePerWarp * 16;
     L.total = off;
     return L;
 }
@@ -209,41 +246,32 @@ __device__ void load_bins(const BinsDev* bd, unsigned char* smem, const SmemLayo
     }
 }
 
-// Merge the thread-private histogram columns into the global uint64 bins and
-// zero them.  Rows 0..nedges-1 (underflow and the B bins) are merged; the
-// last row (pairs found beyond the last edge) is dropped: overflow is derived
-// from the pair total in the finalize kernel.
+// One warp merges its 32 private histogram columns into the global uint64
+// bins and zeroes them.  Rows 0..nedges-1 (underflow and the B bins) are
+// merged; the last row (pairs found beyond the last edge) is dropped:
+// overflow is derived from the pair total by the finalize kernel.
 template <int T>
-__device__ void flush_hist(uint32_t* hist, int nedges, unsigned long long* out) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int NW = T / 32;
-    for (int h = warp; h <= nedges; h += NW) {
-        unsigned long long s = 0;
+__device__ void warp_flush_hist(uint32_t* hist, int nedges, unsigned long long* out) {
+    const int lane = threadIdx.x & 31;
+    for (int h = 0; h <= nedges; ++h) {
+        uint32_t* p = hist + h * T + threadIdx.x;
+        unsigned long long v = *p;
+        *p = 0;
 #pragma unroll
-        for (int k = 0; k < T / 32; ++k) {
-            uint32_t* p = hist + h * T + lane + 32 * k;
-            s += *p;
-            *p = 0;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0 && s != 0 && h < nedges) atomicAdd(out + h, s);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0 && v != 0 && h < nedges) atomicAdd(out + h, v);
     }
 }
 
-template <int T>
-__device__ void block_add_stat(unsigned long long v, unsigned long long* red, unsigned long long* out) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Thread-private histogram increment (one shared-memory reduction instruction).
+__device__ __forceinline__ void hist_inc(uint32_t* p) {
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(smem_addr(p)) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long s = 0;
-        for (int w = 0; w < T / 32; ++w) s += red[w];
-        if (s) atomicAdd(out, s);
-    }
-    __syncthreads();
+    return v;
 }
 
 // ============================================================== per-pair classification
@@ -265,114 +293,164 @@ struct BandStats {
     unsigned long long mismatch;
 };
 
-// Histogram index of a pair whose FP32 cosine is v (v >= T).  The LUT entry
-// for v's key range holds P = nb(v_max) and Q = na(v_min), where
-// nb(v) = #{m : v < lo_m} (edges certainly crossed) and
-// na(v) = #{m : v <= hi_m} (edges possibly crossed).  P == Q settles the
-// whole range; otherwise the few edges in [P, Q) are compared one by one and,
-// if v lies inside a guard band, the pair is recomputed in binary64.
-__device__ __forceinline__ int classify_screen(float v, const unsigned char* smem,
-                                               const SmemLayout& L, int32_t key0, int shift,
-                                               int nlut, const Point64* a64, const Point64* b64,
-                                               uint32_t ig, uint32_t jg, BandStats& bs) {
-    const uint32_t* lut = (const uint32_t*)(smem + L.lut);
-    int idx = (f32_key(v) - key0) >> shift;
-    idx = idx < 0 ? 0 : (idx < nlut ? idx : nlut - 1);
-    const uint32_t ent = lut[idx];
-    const int P = (int)(ent & 0xffffu), Q = (int)(ent >> 16);
-    if (P == Q) return P;
-    const float* lo = (const float*)(smem + L.lo);
-    const float* hi = (const float*)(smem + L.hi);
-    int nbv = P, nav = P;
-    for (int m = P; m < Q; ++m) {
-        nbv += (v < lo[m]);
-        nav += (v <= hi[m]);
-    }
-    if (nbv == nav) return nbv;
-    // guard band: exact binary64 classification
+// Exact histogram index of a band pair: h = nbv + #{m in [nbv, nav) : d <= C_m}
+// with d the binary64 dot product (the edges below nbv are certainly crossed,
+// those from nav on certainly not).  h32 is the FP32-only index, kept for the
+// mismatch statistic.
+__device__ __forceinline__ int band_index(const Point64* a64, const Point64* b64, uint32_t ig,
+                                          uint32_t jg, int nbv, int nav, int h32,
+                                          const double* cthr, BandStats& bs) {
     const double d = dot64(ldg_point(a64 + ig), ldg_point(b64 + jg));
-    const double* c = (const double*)(smem + L.cos_thr);
-    const float* c32 = (const float*)(smem + L.cos32);
-    int h = nbv, h32 = nbv;
-    for (int m = nbv; m < nav; ++m) {
-        h += (d <= c[m]);
-        h32 += (v <= c32[m]);
-    }
+    int h = nbv;
+    for (int m = nbv; m < nav; ++m) h += (d <= cthr[m]);
     bs.band += 1;
     bs.mismatch += (h != h32);
     return h;
 }
 
+// FP32 classification of a pair with FP32 cosine c >= lo_B.  The LUT entry of
+// c's key range holds P = nb(c_max) and Q = na(c_min), where
+// nb(c) = #{m : c < lo_m} (edges certainly crossed) and
+// na(c) = #{m : c <= hi_m} (edges possibly crossed).  Returns h >= 0 when the
+// index is settled; otherwise -1 and the band range [nbv, nav) plus the
+// FP32-only index h32.
+__device__ __forceinline__ int classify_f32(float c, const unsigned char* smem, const SmemLayout& L,
+                                            int32_t key0, int shift, int nlut, int& nbv, int& nav,
+                                            int& h32) {
+    const uint32_t* lut = (const uint32_t*)(smem + L.lut);
+    // c >= lo_B gives idx >= 0; c <= 1 + 6u keeps idx below nlut (clamped for safety)
+    int idx = (f32_key(c) - key0) >> shift;
+    idx = idx < nlut ? idx : nlut - 1;
+    const uint32_t ent = lut[idx];
+    const int P = (int)(ent & 0xffffu), Q = (int)(ent >> 16);
+    if (P == Q) return P;
+    const float* lo = (const float*)(smem + L.lo);
+    const float* hi = (const float*)(smem + L.hi);
+    int nb_ = P, na_ = P;
+    for (int m = P; m < Q; ++m) {
+        nb_ += (c < lo[m]);
+        na_ += (c <= hi[m]);
+    }
+    if (nb_ == na_) return nb_;
+    const float* c32 = (const float*)(smem + L.cos32);
+    int h = nb_;
+    for (int m = nb_; m < na_; ++m) h += (c <= c32[m]);
+    nbv = nb_;
+    nav = na_;
+    h32 = h;
+    return -1;
+}
+
+// One warp recomputes its queued band pairs in binary64; each lane adds to
+// its own histogram column.  Ends with the warp's queue empty.
+template <int T>
+__device__ void warp_drain_queue(const uint4* wq, volatile int* wq_count, const Point64* a64,
+                                 const Point64* b64, const double* cthr, uint32_t* hcol,
+                                 BandStats& bs) {
+    __syncwarp();
+    const int n = min(*wq_count, kQueuePerWarp);
+    for (int k = (int)(threadIdx.x & 31); k < n; k += 32) {
+        const uint4 e = wq[k];
+        const int h = band_index(a64, b64, e.x, e.y, (int)(e.z & 0xffffu), (int)(e.z >> 16),
+                                 (int)e.w, cthr, bs);
+        hist_inc(hcol + h * T);
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) *wq_count = 0;
+    __syncwarp();
+}
+
 // ============================================================== the counting kernel
-// T threads, R i-points per thread, PLAIN: all-binary64 comparator.
-template <int T, int R, bool PLAIN>
+// T threads, R i-points per thread, MODE: KernelMode.
+//
+// Pipeline: S shared-memory stages of J j-points.  Stage s holds tile seq with
+// seq % S == s; its full mbarrier completes when the TMA bulk copy lands.
+// Warps run independently (no block barrier in the main loop): after a warp
+// finishes a tile its lane 0 increments the stage's release counter, and the
+// warp that releases last issues the copy of tile seq + S into the stage.
+// Every wait is bounded; a timeout sets the abort word, after which no copy is
+// issued, warps leave the loop, and thread 0 waits (bounded) for the copies
+// still in flight before the block exits.
+template <int T, int R, int MODE>
 __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ WorkDesc wd) {
+    constexpr bool PLAIN = MODE == kModePlain;
+    constexpr bool PACKED = MODE == kModeScreen2;
     extern __shared__ __align__(128) unsigned char smem[];
-    const int S = 2;
+    constexpr int W = T / 32;
+    const int S = (int)wd.stages;
     const int J = (int)wd.J;
     const int I = T * R;
     const int nedges = wd.nedges_max;
-    const SmemLayout L = smem_layout(PLAIN, T, J, S, nedges);
+    const SmemLayout L = smem_layout(MODE, T, J, S, nedges);
     uint64_t* bars = (uint64_t*)(smem + L.bars);
-    volatile int* s_abort = (volatile int*)(smem + L.flags);
+    volatile int* ctl = (volatile int*)(smem + L.ctl);
     uint32_t* hist = (uint32_t*)(smem + L.hist);
-    unsigned long long* red = (unsigned long long*)(smem + L.red);
-    constexpr uint32_t PT = PLAIN ? 32u : 16u;
+    constexpr uint32_t PT = MODE == kModeScreen ? 16u : 32u;
     const uint32_t stage_bytes = (uint32_t)J * PT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t* hcol = hist + tid;
+    const double* cthr = (const double*)(smem + L.cos_thr);
+    uint4* wq = (uint4*)(smem + L.queue) + warp * kQueuePerWarp;
+    volatile int* wq_count = ctl + kCtlQueue + warp;
 
     Cursor cons;
     cursor_begin(wd, cons);
     if (!cons.valid) return;  // block-uniform
 
-    // ---- set up barriers, zero the histogram
+    // ---- set up: barriers, control words, histogram, bins (all sub-problems share them)
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
-        *s_abort = 0;
         fence_mbar_init();
     }
+    for (int k = tid; k < kCtlWords; k += T) ctl[k] = 0;
     for (int k = tid; k < (nedges + 1) * T; k += T) hist[k] = 0;
+    const BinsDev* bd = sub_of(wd, cons.sub).bins;
+    load_bins<T>(bd, smem, L, PLAIN);
+    const int ne = bd->nedges;
+    const float band_t = bd->range_t;
+    const float neg_fast_t = -bd->fast_t;
+    const double cos_last = bd->cos_last;
+    const int32_t key0 = bd->lut_key0;
+    const int lut_shift = bd->lut_shift, nlut = bd->nlut;
+    const bool need_idx = !(band_t > 0.f);  // zero-vector padding has cosine 0
     __syncthreads();
 
-    // ---- producer state (thread 0): S tiles ahead of the consumer
-    Cursor prod = cons;
-    uint32_t issued = 0;        // tiles issued so far (sequence numbers 0..issued-1)
-    uint32_t skipped_seq = 0xffffffffu;
-    auto issue = [&](uint32_t seq) {
-        const SubProblem& sp = sub_of(wd, prod.sub);
-        const uint32_t jbase = prod.g.j0 + prod.t * (uint32_t)J;
-        unsigned char* dst = smem + L.stage + (seq % S) * stage_bytes;
-        if ((wd.flags & TPCF_F_TEST_WAIT_TIMEOUT) && seq == 0) {
-            skipped_seq = seq;  // test hook: never issued, its wait must time out
-            return;
-        }
-        mbar_expect_tx(&bars[seq % S], stage_bytes);
-        const void* src = PLAIN ? (const void*)(sp.b64 + jbase) : (const void*)(sp.b32 + jbase);
-        bulk_copy_g2s(dst, src, stage_bytes, &bars[seq % S]);
+    auto issue = [&](uint32_t seq, const Cursor& pc) {
+        const SubProblem& sp = sub_of(wd, pc.sub);
+        const uint32_t jbase = pc.g.j0 + pc.t * (uint32_t)J;
+        unsigned char* dst = smem + L.stage + (seq % (uint32_t)S) * stage_bytes;
+        if ((wd.flags & TPCF_F_TEST_WAIT_TIMEOUT) && seq == 0) return;  // test hook: never issued
+        mbar_expect_tx(&bars[seq % (uint32_t)S], stage_bytes);
+        const void* src = PLAIN ? (const void*)(sp.b64 + jbase)
+                                : PACKED ? (const void*)(sp.b32x2 + 2ull * jbase) : (const void*)(sp.b32 + jbase);
+        bulk_copy_g2s(dst, src, stage_bytes, &bars[seq % (uint32_t)S]);
     };
-    if (tid == 0) {
-        while (prod.valid && issued < (uint32_t)S) {
-            issue(issued++);
+
+    // ---- prologue: thread 0 issues the first S tiles; every warp keeps a
+    // producer cursor S tiles ahead for its refill turns.
+    Cursor prod = cons;
+    {
+        int k = 0;
+        for (; k < S && prod.valid; ++k) {
+            if (tid == 0) issue((uint32_t)k, prod);
             cursor_next(wd, prod);
         }
+        if (tid == 0) ctl[kCtlIssued] = k;
     }
 
     // ---- consumer state
     int cur_sub = -1;
-    const BinsDev* cur_bins = nullptr;
     unsigned long long* cur_hist = nullptr;
     uint64_t j_since_flush = 0;
-    const uint64_t flush_limit = (0xffffffffull / R) - (uint64_t)J;
-    float ax[PLAIN ? 1 : R], ay[PLAIN ? 1 : R], az[PLAIN ? 1 : R];
+    // a lane adds at most R per j plus at most 2 per queue drain (one drain per 4 j)
+    const uint64_t flush_limit = (0xffffffffull / (R + 1)) - (uint64_t)J;
+    float ax[MODE == kModeScreen ? R : 1], ay[MODE == kModeScreen ? R : 1], az[MODE == kModeScreen ? R : 1];
+    unsigned long long px[PACKED ? R / 2 : 1], py[PACKED ? R / 2 : 1], pz[PACKED ? R / 2 : 1];
     double dx[PLAIN ? R : 1], dy[PLAIN ? R : 1], dz[PLAIN ? R : 1];
     uint32_t ibase = 0;
-    float negT = 0.f, rangeT = 0.f;
-    double cos_last = 0.0;
-    int32_t key0 = 0;
-    int lut_shift = 0, nlut = 1, ne = 0;
     unsigned long long pairs = 0;
     BandStats bs = {0ull, 0ull};
-    bool auto_mode = false;
+    bool auto_mode = false, aborted = false;
     uint32_t na = 0, nb = 0;
     const Point64* a64 = nullptr;
     const Point64* b64 = nullptr;
@@ -380,28 +458,17 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     uint32_t seq = 0;
     while (cons.valid) {
         if (cons.t == cons.g.t_first) {
-            // ---- new item (block-uniform)
+            // ---- new item (warp-uniform: every warp walks the same tiles)
             const SubProblem& sp = sub_of(wd, cons.sub);
             if (cons.sub != cur_sub) {
-                if (sp.hist != cur_hist && cur_hist != nullptr) {
-                    flush_hist<T>(hist, ne, cur_hist);
-                    j_since_flush = 0;
-                    __syncthreads();
-                }
-                if (sp.bins != cur_bins) {
-                    load_bins<T>(sp.bins, smem, L, PLAIN);
-                    const BinsDev* bd = sp.bins;
-                    ne = bd->nedges;
-                    rangeT = bd->range_t;
-                    negT = -rangeT;
-                    cos_last = bd->cos_last;
-                    key0 = bd->lut_key0;
-                    lut_shift = bd->lut_shift;
-                    nlut = bd->nlut;
-                    __syncthreads();
+                if (cur_hist != nullptr) {
+                    if constexpr (!PLAIN) warp_drain_queue<T>(wq, wq_count, a64, b64, cthr, hcol, bs);
+                    if (sp.hist != cur_hist) {
+                        warp_flush_hist<T>(hist, ne, cur_hist);
+                        j_since_flush = 0;
+                    }
                 }
                 cur_sub = cons.sub;
-                cur_bins = sp.bins;
                 cur_hist = sp.hist;
                 auto_mode = sp.auto_mode != 0;
                 na = sp.na;
@@ -411,13 +478,12 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             }
             const uint64_t item_j = (uint64_t)(cons.g.t_end - cons.g.t_first) * J;
             if (j_since_flush + item_j > flush_limit) {
-                flush_hist<T>(hist, ne, cur_hist);
+                if constexpr (!PLAIN) warp_drain_queue<T>(wq, wq_count, a64, b64, cthr, hcol, bs);
+                warp_flush_hist<T>(hist, ne, cur_hist);
                 j_since_flush = 0;
-                __syncthreads();
             }
             j_since_flush += item_j;
-            if (tid == 0)
-                pairs += item_pairs(cons.g, na, nb, auto_mode, (uint32_t)I, wd.Jc);
+            if (tid == 0) pairs += item_pairs(cons.g, na, nb, auto_mode, (uint32_t)I, wd.Jc);
             ibase = cons.g.i0 + (uint32_t)warp * (32u * R) + (uint32_t)lane;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -427,6 +493,18 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                     dx[r] = p.x;
                     dy[r] = p.y;
                     dz[r] = p.z;
+                } else if constexpr (PACKED) {
+                    // lanes (r, r + 1) of the packed registers hold i-points r and r + 1
+                    const float4 p = __ldg(sp.a32 + i);
+                    if ((r & 1) == 0) {
+                        px[r / 2] = pack2(p.x, 0.f);
+                        py[r / 2] = pack2(p.y, 0.f);
+                        pz[r / 2] = pack2(p.z, 0.f);
+                    } else {
+                        px[r / 2] = pack2(lo_of(px[r / 2]), p.x);
+                        py[r / 2] = pack2(lo_of(py[r / 2]), p.y);
+                        pz[r / 2] = pack2(lo_of(pz[r / 2]), p.z);
+                    }
                 } else {
                     const float4 p = __ldg(sp.a32 + i);
                     ax[r] = p.x;
@@ -437,111 +515,210 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         }
 
         // ---- wait for this tile
-        const uint32_t stage = seq % S;
-        const bool ok = mbar_wait_bounded(&bars[stage], (seq / S) & 1u, wd.wait_limit_ns);
-        if (!ok) *s_abort = 1;
-        if (ok) {
-            const uint32_t jbase = cons.g.j0 + cons.t * (uint32_t)J;
-            const bool masked = auto_mode && (jbase < cons.g.i0 + (uint32_t)I);
-            uint32_t* hcol = hist + tid;
-            if constexpr (!PLAIN) {
-                const float4* sj = (const float4*)(smem + L.stage + stage * stage_bytes);
-                // slow path for one j: classify the pairs whose screen value is >= 0
-                auto slow = [&](const float (&e)[R], uint32_t jg) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if (__float_as_int(e[r]) >= 0) {
-                            const uint32_t ig = ibase + 32u * r;
-                            if (ig < na && jg < nb) {
-                                const float v = __fadd_rn(e[r], rangeT);
-                                const int h = classify_screen(v, smem, L, key0, lut_shift, nlut,
-                                                              a64, b64, ig, jg, bs);
-                                hcol[h * T] += 1u;
-                            }
-                        }
-                    }
-                };
-                if (!masked) {
-#pragma unroll 4
-                    for (int jj = 0; jj < J; ++jj) {
-                        const float4 b = sj[jj];
-                        float e[R];
-                        int acc = -1;
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            e[r] = fmaf(az[r], b.z, fmaf(ay[r], b.y, fmaf(ax[r], b.x, negT)));
-                            acc &= __float_as_int(e[r]);
-                        }
-                        if (acc >= 0) slow(e, jbase + (uint32_t)jj);
-                    }
-                } else {
-                    for (int jj = 0; jj < J; ++jj) {
-                        const float4 b = sj[jj];
-                        const uint32_t jg = jbase + (uint32_t)jj;
-                        float e[R];
-                        int acc = -1;
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            float v = fmaf(az[r], b.z, fmaf(ay[r], b.y, fmaf(ax[r], b.x, negT)));
-                            e[r] = (jg > ibase + 32u * r) ? v : -1.0f;
-                            acc &= __float_as_int(e[r]);
-                        }
-                        if (acc >= 0) slow(e, jg);
-                    }
-                }
-            } else {
-                const Point64* sj = (const Point64*)(smem + L.stage + stage * stage_bytes);
-                const double* c = (const double*)(smem + L.cos_thr);
-                for (int jj = 0; jj < J; ++jj) {
-                    const Point64 b = sj[jj];
-                    const uint32_t jg = jbase + (uint32_t)jj;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const double d = __dadd_rn(__dadd_rn(__dmul_rn(dx[r], b.x), __dmul_rn(dy[r], b.y)),
-                                                   __dmul_rn(dz[r], b.z));
-                        if (d > cos_last) {
-                            const uint32_t ig = ibase + 32u * r;
-                            if (ig < na && jg < nb && (!masked || jg > ig)) {
-                                // h = number of edges m with d <= C_m (C decreasing)
-                                int lo = 0, hi = ne;
-                                while (lo < hi) {
-                                    const int mid = (lo + hi) >> 1;
-                                    if (c[mid] >= d) lo = mid + 1; else hi = mid;
-                                }
-                                hcol[lo * T] += 1u;
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (*s_abort) {
-            // bounded wait for copies still in flight into this block's shared memory
-            if (tid == 0) {
+        const uint32_t stage = seq % (uint32_t)S;
+        const bool ok = mbar_wait_bounded(&bars[stage], (seq / (uint32_t)S) & 1u, wd.wait_limit_ns);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (lane == 0) {
+                ctl[kCtlAbort] = 1;
                 atomicOr(wd.stats + kStatError, (unsigned long long)kErrWaitTimeout);
-                for (uint32_t s2 = seq; s2 < issued; ++s2)
-                    if (s2 != skipped_seq)
-                        (void)mbar_wait_bounded(&bars[s2 % S], (s2 / S) & 1u, wd.wait_limit_ns);
             }
-            return;
+            aborted = true;
+            break;
         }
-        // ---- refill the stage just consumed with tile seq + S
-        if (tid == 0 && prod.valid) {
-            fence_proxy_async_smem();
-            issue(issued++);
-            cursor_next(wd, prod);
+        if (ctl[kCtlAbort]) { aborted = true; break; }
+
+        const uint32_t jbase = cons.g.j0 + cons.t * (uint32_t)J;
+        const bool masked = auto_mode && (jbase < cons.g.i0 + (uint32_t)I);
+        if constexpr (PACKED) {
+            const float4* sj = (const float4*)(smem + L.stage + stage * stage_bytes);  // 2 per point
+            const unsigned long long nt2 = pack2(neg_fast_t, neg_fast_t);
+            constexpr int U = 4;  // j-points per group
+            // Fast loop with packed FMA: e for i-points (r, r + 1) in one fma.rn.f32x2.
+#pragma unroll 1
+            for (int jj = 0; jj < J; jj += U) {
+                uint32_t skip = 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const ulonglong2 bxy = *reinterpret_cast<const ulonglong2*>(sj + 2 * (jj + u));
+                    const unsigned long long bz = *reinterpret_cast<const unsigned long long*>(sj + 2 * (jj + u) + 1);
+                    int acc = -1;
+#pragma unroll
+                    for (int p = 0; p < R / 2; ++p) {
+                        const unsigned long long e = ffma2(pz[p], bz, ffma2(py[p], bxy.y, ffma2(px[p], bxy.x, nt2)));
+                        acc &= (int)(uint32_t)e & (int)(uint32_t)(e >> 32);
+                    }
+                    skip = __funnelshift_l((uint32_t)acc, skip, 1);  // (skip << 1) | sign(acc)
+                }
+                uint32_t todo = __reduce_or_sync(0xffffffffu, ~skip & ((1u << U) - 1u));
+                if (todo == 0) continue;
+                do {
+                    const int bit = 31 - __clz(todo);
+                    todo &= ~(1u << bit);
+                    const int u = U - 1 - bit;
+                    const float4 b = make_float4(sj[2 * (jj + u)].x, sj[2 * (jj + u)].z, sj[2 * (jj + u) + 1].x, 0.f);
+                    const uint32_t jg = jbase + (uint32_t)(jj + u);
+                    const bool j_ok = !need_idx || jg < nb;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float xr = (r & 1) ? hi_of(px[r / 2]) : lo_of(px[r / 2]);
+                        const float yr = (r & 1) ? hi_of(py[r / 2]) : lo_of(py[r / 2]);
+                        const float zr = (r & 1) ? hi_of(pz[r / 2]) : lo_of(pz[r / 2]);
+                        const float c = fmaf(zr, b.z, fmaf(yr, b.y, __fmul_rn(xr, b.x)));
+                        const uint32_t ig = ibase + 32u * r;
+                        if (c >= band_t && j_ok && (!need_idx || ig < na) && (!masked || jg > ig)) {
+                            int nbv, nav, h32;
+                            int h = classify_f32(c, smem, L, key0, lut_shift, nlut, nbv, nav, h32);
+                            if (h < 0) {
+                                const int pos = atomicAdd((int*)wq_count, 1);
+                                if (pos < kQueuePerWarp) {
+                                    wq[pos] = make_uint4(ig, jg, (uint32_t)nbv | ((uint32_t)nav << 16),
+                                                         (uint32_t)h32);
+                                } else {
+                                    h = band_index(a64, b64, ig, jg, nbv, nav, h32, cthr, bs);
+                                }
+                            }
+                            if (h >= 0) hist_inc(hcol + h * T);
+                        }
+                    }
+                } while (todo);
+                __syncwarp();
+                if (*wq_count >= kQueuePerWarp / 2)
+                    warp_drain_queue<T>(wq, wq_count, a64, b64, cthr, hcol, bs);
+            }
+        } else if constexpr (MODE == kModeScreen) {
+            const float4* sj = (const float4*)(smem + L.stage + stage * stage_bytes);
+            constexpr int U = 4;  // j-points per group
+            // Fast loop: e = FP32 dot minus the fast range limit, for R i-points x
+            // U j-points; one funnel shift per j appends "all R negative" to a bit
+            // mask.  A j with some e >= 0 goes to the warp-uniform slow path.
+#pragma unroll 1
+            for (int jj = 0; jj < J; jj += U) {
+                uint32_t skip = 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float4 b = sj[jj + u];
+                    int acc = -1;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float e = fmaf(az[r], b.z, fmaf(ay[r], b.y, fmaf(ax[r], b.x, neg_fast_t)));
+                        acc &= __float_as_int(e);
+                    }
+                    skip = __funnelshift_l((uint32_t)acc, skip, 1);  // (skip << 1) | sign(acc)
+                }
+                uint32_t todo = __reduce_or_sync(0xffffffffu, ~skip & ((1u << U) - 1u));
+                if (todo == 0) continue;
+                do {
+                    // bit U-1-u stands for j = jj + u
+                    const int bit = 31 - __clz(todo);
+                    todo &= ~(1u << bit);
+                    const int u = U - 1 - bit;
+                    const float4 b = sj[jj + u];
+                    const uint32_t jg = jbase + (uint32_t)(jj + u);
+                    // Plain FP32 cosine (error bound 5u against the binary64 dot).
+                    // Padding points are zero vectors (cosine 0): they need an
+                    // index test only when the range reaches cos <= 0.
+                    const bool j_ok = !need_idx || jg < nb;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float c = fmaf(az[r], b.z, fmaf(ay[r], b.y, __fmul_rn(ax[r], b.x)));
+                        const uint32_t ig = ibase + 32u * r;
+                        if (c >= band_t && j_ok && (!need_idx || ig < na) && (!masked || jg > ig)) {
+                            int nbv, nav, h32;
+                            int h = classify_f32(c, smem, L, key0, lut_shift, nlut, nbv, nav, h32);
+                            if (h < 0) {
+                                const int pos = atomicAdd((int*)wq_count, 1);
+                                if (pos < kQueuePerWarp) {
+                                    wq[pos] = make_uint4(ig, jg, (uint32_t)nbv | ((uint32_t)nav << 16),
+                                                         (uint32_t)h32);
+                                } else {
+                                    h = band_index(a64, b64, ig, jg, nbv, nav, h32, cthr, bs);
+                                }
+                            }
+                            if (h >= 0) hist_inc(hcol + h * T);
+                        }
+                    }
+                } while (todo);
+                __syncwarp();
+                if (*wq_count >= kQueuePerWarp / 2)
+                    warp_drain_queue<T>(wq, wq_count, a64, b64, cthr, hcol, bs);
+            }
+        } else {
+            const Point64* sj = (const Point64*)(smem + L.stage + stage * stage_bytes);
+            for (int jj = 0; jj < J; ++jj) {
+                const Point64 b = sj[jj];
+                const uint32_t jg = jbase + (uint32_t)jj;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const double d = __dadd_rn(__dadd_rn(__dmul_rn(dx[r], b.x), __dmul_rn(dy[r], b.y)),
+                                               __dmul_rn(dz[r], b.z));
+                    if (d > cos_last) {
+                        const uint32_t ig = ibase + 32u * r;
+                        if (ig < na && jg < nb && (!masked || jg > ig)) {
+                            // h = number of edges m with d <= C_m (C decreasing)
+                            int lo = 0, hi = ne;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (cthr[mid] >= d) lo = mid + 1; else hi = mid;
+                            }
+                            hist_inc(hcol + lo * T);
+                        }
+                    }
+                }
+            }
+        }
+
+        // ---- release the stage; the last warp to release refills it with tile seq + S
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            const int old = atomicAdd((int*)&ctl[kCtlRelease + stage], 1);
+            if (old == W - 1) {
+                __threadfence_block();
+                ctl[kCtlRelease + stage] = 0;
+                if (prod.valid && !ctl[kCtlAbort]) {
+                    fence_proxy_async_smem();
+                    issue(seq + (uint32_t)S, prod);
+                    atomicAdd((int*)&ctl[kCtlIssued], 1);
+                }
+            }
         }
         ++seq;
         cursor_next(wd, cons);
+        cursor_next(wd, prod);
     }
 
-    // ---- final merge
-    flush_hist<T>(hist, ne, cur_hist);
-    if (tid == 0) atomicAdd(wd.stats + kStatPairs, pairs);
-    if constexpr (!PLAIN) {
-        block_add_stat<T>(bs.band, red, wd.stats + kStatBand);
-        block_add_stat<T>(bs.mismatch, red, wd.stats + kStatMismatch);
+    // ---- merge this warp's columns (skipped after an abort: outputs are invalid)
+    if (!aborted && cur_hist != nullptr) {
+        if constexpr (!PLAIN) warp_drain_queue<T>(wq, wq_count, a64, b64, cthr, hcol, bs);
+        warp_flush_hist<T>(hist, ne, cur_hist);
+        if constexpr (!PLAIN) {
+            const unsigned long long b = warp_sum(bs.band), m = warp_sum(bs.mismatch);
+            if (lane == 0) {
+                if (b) atomicAdd(wd.stats + kStatBand, b);
+                if (m) atomicAdd(wd.stats + kStatMismatch, m);
+            }
+        }
+        if (tid == 0) atomicAdd(wd.stats + kStatPairs, pairs);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence_block();
+        atomicAdd((int*)&ctl[kCtlWarpsDone], 1);
+    }
+    if (tid == 0) {
+        // wait (bounded) until every warp has left the loop, then, after an
+        // abort, for the copies still in flight into this block's shared memory
+        const uint64_t t0 = global_ns();
+        while (ctl[kCtlWarpsDone] < W && global_ns() - t0 < wd.wait_limit_ns) __nanosleep(256);
+        __threadfence_block();
+        if (ctl[kCtlAbort]) {
+            const uint32_t issued = (uint32_t)ctl[kCtlIssued];
+            const uint32_t first = issued > (uint32_t)S ? issued - (uint32_t)S : 0u;
+            for (uint32_t s2 = first; s2 < issued; ++s2) {
+                if ((wd.flags & TPCF_F_TEST_WAIT_TIMEOUT) && s2 == 0) continue;
+                (void)mbar_wait_bounded(&bars[s2 % (uint32_t)S], (s2 / (uint32_t)S) & 1u, wd.wait_limit_ns);
+            }
+        }
     }
 }
 
@@ -680,53 +857,61 @@ __global__ void __launch_bounds__(1024) bitonic_local_kernel(unsigned long long*
 // zero the padding.
 __global__ void prep_gather_kernel(const double* __restrict__ xyz, uint32_t n,
                                    const uint32_t* __restrict__ order, Point64* out64,
-                                   float4* out32, uint32_t n_pad) {
+                                   float4* out32, float4* out32x2, uint32_t n_pad) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pad) return;
     if (p >= n) {
         out64[p] = Point64{0.0, 0.0, 0.0, 0.0};
         out32[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out32x2[2ull * p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out32x2[2ull * p + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     const uint32_t s = order ? order[p] : p;
     const double x = xyz[3ull * s], y = xyz[3ull * s + 1], z = xyz[3ull * s + 2];
+    const float fx = __double2float_rn(x), fy = __double2float_rn(y), fz = __double2float_rn(z);
     out64[p] = Point64{x, y, z, 0.0};
-    out32[p] = make_float4(__double2float_rn(x), __double2float_rn(y), __double2float_rn(z), 0.f);
+    out32[p] = make_float4(fx, fy, fz, 0.f);
+    out32x2[2ull * p] = make_float4(fx, fx, fy, fy);
+    out32x2[2ull * p + 1] = make_float4(fz, fz, 0.f, 0.f);
 }
 
 // ============================================================== launchers
-template <int T, int R, bool PLAIN>
+template <int T, int R, int MODE>
 static cudaError_t launch_t(const WorkDesc& wd, const Shape& sh, cudaStream_t stream) {
-    count_kernel<T, R, PLAIN><<<sh.blocks, T, sh.smem, stream>>>(wd);
+    count_kernel<T, R, MODE><<<sh.blocks, T, sh.smem, stream>>>(wd);
     return cudaGetLastError();
 }
 
-template <int T, int R, bool PLAIN>
+template <int T, int R, int MODE>
 static cudaError_t set_smem_t(size_t bytes) {
-    return cudaFuncSetAttribute(count_kernel<T, R, PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(count_kernel<T, R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)bytes);
 }
 
 #define TPCF_SHAPES(X) X(128, 8) X(256, 8) X(512, 8) X(256, 16)
 
-cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int precision, int nedges,
+cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int mode, int nedges,
                          cudaStream_t stream) {
     (void)nedges;
-    const bool plain = precision == TPCF_PLAIN_FP64;
-#define X(T_, R_)                                                              \
-    if (sh.threads == T_ && sh.ipt == R_)                                      \
-        return plain ? launch_t<T_, R_, true>(wd, sh, stream)                  \
-                     : launch_t<T_, R_, false>(wd, sh, stream);
+#define X(T_, R_)                                                                \
+    if (sh.threads == T_ && sh.ipt == R_) {                                      \
+        if (mode == kModePlain) return launch_t<T_, R_, kModePlain>(wd, sh, stream);   \
+        if (mode == kModeScreen2) return launch_t<T_, R_, kModeScreen2>(wd, sh, stream); \
+        return launch_t<T_, R_, kModeScreen>(wd, sh, stream);                    \
+    }
     TPCF_SHAPES(X)
 #undef X
     return cudaErrorInvalidConfiguration;
 }
 
-cudaError_t count_set_smem_limit(int precision, int threads, int ipt, size_t bytes) {
-    const bool plain = precision == TPCF_PLAIN_FP64;
-#define X(T_, R_)                                                              \
-    if (threads == T_ && ipt == R_)                                            \
-        return plain ? set_smem_t<T_, R_, true>(bytes) : set_smem_t<T_, R_, false>(bytes);
+cudaError_t count_set_smem_limit(int mode, int threads, int ipt, size_t bytes) {
+#define X(T_, R_)                                                                \
+    if (threads == T_ && ipt == R_) {                                            \
+        if (mode == kModePlain) return set_smem_t<T_, R_, kModePlain>(bytes);    \
+        if (mode == kModeScreen2) return set_smem_t<T_, R_, kModeScreen2>(bytes); \
+        return set_smem_t<T_, R_, kModeScreen>(bytes);                           \
+    }
     TPCF_SHAPES(X)
 #undef X
     return cudaErrorInvalidConfiguration;
@@ -739,9 +924,9 @@ bool count_shape_supported(int threads, int ipt) {
     return false;
 }
 
-size_t count_smem_bytes(int precision, int threads, int ipt, int jtile, int stages, int nedges) {
+size_t count_smem_bytes(int mode, int threads, int ipt, int jtile, int stages, int nedges) {
     (void)ipt;
-    return smem_layout(precision == TPCF_PLAIN_FP64, threads, jtile, stages, nedges).total;
+    return smem_layout(mode, threads, jtile, stages, nedges).total;
 }
 
 cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long long* out,
@@ -752,13 +937,15 @@ cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long l
 }
 
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
-                           int sort, Point64* out64, float4* out32, uint32_t n_pad,
+                           int sort, Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
                            unsigned long long* keys, uint32_t* vals, uint32_t n_pow2,
-                           unsigned long long* err_word, cudaStream_t stream) {
+                           unsigned long long* err_word, cudaStream_t stream, uint32_t* launches) {
     cudaError_t e;
+    uint32_t nl = 0;
     if (n > 0) {
         prep_keys_kernel<<<(n_pow2 + 255) / 256, 256, 0, stream>>>(xyz_in, n, seg_of_point, sort,
                                                                     keys, vals, n_pow2, err_word);
+        ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const bool do_sort = sort && n > 1;
@@ -766,22 +953,27 @@ cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg
         // n_pow2 >= 2048 (the host rounds it up)
         const uint32_t chunks = n_pow2 / 2048u;
         bitonic_local_kernel<<<chunks, 1024, 0, stream>>>(keys, vals, n_pow2, 0u);
+        ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         for (uint32_t k = 4096; k <= n_pow2; k <<= 1) {
             for (uint32_t j = k / 2; j >= 2048; j >>= 1) {
                 bitonic_global_kernel<<<(n_pow2 / 2 + 255) / 256, 256, 0, stream>>>(keys, vals,
                                                                                     n_pow2, k, j);
+                ++nl;
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
             bitonic_local_kernel<<<chunks, 1024, 0, stream>>>(keys, vals, n_pow2, k);
+            ++nl;
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
     if (n_pad > 0) {
         prep_gather_kernel<<<(n_pad + 255) / 256, 256, 0, stream>>>(xyz_in, n, do_sort ? vals : nullptr,
-                                                                   out64, out32, n_pad);
+                                                                   out64, out32, out32x2, n_pad);
+        ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    if (launches) *launches = nl;
     return cudaSuccess;
 }
 

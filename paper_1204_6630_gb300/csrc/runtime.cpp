@@ -31,7 +31,14 @@ constexpr int kSlots = 16;
 constexpr size_t kHistStride = TPCF_MAX_EDGES + 1;          // words per histogram in a slot
 constexpr size_t kStatOff = 3 * kHistStride;                 // stats words after 3 histograms
 constexpr size_t kSlotWords = ((kStatOff + kStatWords) + 31) / 32 * 32;
-constexpr double kDefaultGuard = 1.0 / 1048576.0;            // 2^-20
+// Guard band g in cos(theta).  The FP32 cosine of a pair (inputs rounded to
+// FP32, fma(az,bz, fma(ay,by, ax*bx))) is within 5.0001 u of the binary64 dot
+// product (u = 2^-24: 2u from rounding the inputs, 3u from the three
+// roundings), so any g >= 6u keeps the FP32 classification outside the bands
+// exact.  Default: g = 6u.
+constexpr double kUnit = 5.9604644775390625e-08;             // u = 2^-24
+constexpr double kDefaultGuard = 6.0 * kUnit;
+constexpr double kMinGuard = 6.0 * kUnit;
 constexpr uint32_t kDefaultWaitUs = 2000000;
 
 std::atomic<int> g_alloc_fail_countdown{-1};
@@ -61,6 +68,7 @@ struct tpcf_ctx {
     };
     Slot slots[kSlots];
     std::atomic<uint32_t> slot_rr{0};
+    std::atomic<uint64_t> launches{0};  // kernels of this library launched through the context
 
     int fail(int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
 };
@@ -82,6 +90,7 @@ struct tpcf_catalog {
     uint32_t n_pad = 0;
     Point64* d64 = nullptr;
     float4* d32 = nullptr;
+    float4* d32x2 = nullptr;        // (x,x,y,y),(z,z,0,0) per point for the packed screen
     std::vector<uint64_t> offsets;  // segments (empty = one segment)
 };
 
@@ -137,6 +146,8 @@ extern "C" void tpcf_config_default(tpcf_config* cfg) {
 
 extern "C" int tpcf_version(void) { return 100; }
 
+extern "C" uint64_t tpcf_kernel_launches(const tpcf_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
 // Test hook: make the n-th following device allocation fail (n = -1: never).
 extern "C" void tpcf_debug_fail_alloc_after(int n) { g_alloc_fail_countdown.store(n); }
 
@@ -149,7 +160,7 @@ extern "C" int tpcf_create(tpcf_ctx** out, const tpcf_config* cfg_in) {
     if (cfg_in) cfg = *cfg_in;
     if (cfg.guard_band == 0.0) cfg.guard_band = kDefaultGuard;
     if (cfg.wait_timeout_us == 0) cfg.wait_timeout_us = kDefaultWaitUs;
-    if (!(cfg.guard_band > 0.0 && cfg.guard_band < 0.25)) return TPCF_EINVAL;
+    if (!(cfg.guard_band >= kMinGuard && cfg.guard_band < 0.25)) return TPCF_EINVAL;
     if (cfg.precision != TPCF_SCREEN_RECHECK && cfg.precision != TPCF_PLAIN_FP64) return TPCF_EINVAL;
     if (cfg.shard_count > 1 && cfg.shard_index >= cfg.shard_count) return TPCF_EINVAL;
     int ndev = 0;
@@ -323,7 +334,7 @@ extern "C" int tpcf_bins_thresholds(const double* edges, int nedges, double guar
                                     float* lo, float* hi, int* verified) {
     if (!edges_valid(edges, nedges)) return TPCF_EINVAL;
     if (guard == 0.0) guard = kDefaultGuard;
-    if (!(guard > 0.0 && guard < 0.25)) return TPCF_EINVAL;
+    if (!(guard >= kMinGuard && guard < 0.25)) return TPCF_EINVAL;
     std::vector<double> C;
     std::vector<float> l, h, c;
     std::vector<int> v;
@@ -383,6 +394,11 @@ extern "C" int tpcf_bins_create(tpcf_ctx* ctx, const double* edges, int nedges, 
     b->host.lut_shift = shift;
     b->host.lut_key0 = key0;
     b->host.range_t = b->lo[nedges - 1];
+    // The fast skip test evaluates fma(az,bz, fma(ay,by, fma(ax,bx, -T))): its
+    // error against the binary64 dot minus T is at most 8.0003 u (2u input
+    // rounding, 3 roundings of terms up to |T| + 1), so a negative value means
+    // d < T + 8.0003u; T = RD(C_B - 10u) makes that certainly overflow.
+    b->host.fast_t = round_down_f32(b->cos_thr[nedges - 1] - 10.0 * kUnit);
     b->host.cos_last = b->cos_thr[nedges - 1];
     if (dev_malloc((void**)&b->dev_desc, sizeof(BinsDev)) != cudaSuccess) return cleanup(TPCF_ENOMEM);
     if (cudaMemcpy(b->dev_desc, &b->host, sizeof(BinsDev), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -449,11 +465,13 @@ extern "C" int tpcf_catalog_create_segmented(tpcf_ctx* ctx, const double* xyz, u
         release();
         if (c->d64) cudaFree(c->d64);
         if (c->d32) cudaFree(c->d32);
+        if (c->d32x2) cudaFree(c->d32x2);
         delete c;
         return ctx->fail(code, "catalog: %s", what);
     };
     if (dev_malloc((void**)&c->d64, (size_t)c->n_pad * sizeof(Point64)) != cudaSuccess ||
-        dev_malloc((void**)&c->d32, (size_t)c->n_pad * sizeof(float4)) != cudaSuccess)
+        dev_malloc((void**)&c->d32, (size_t)c->n_pad * sizeof(float4)) != cudaSuccess ||
+        dev_malloc((void**)&c->d32x2, (size_t)c->n_pad * 2 * sizeof(float4)) != cudaSuccess)
         return fail_with(TPCF_ENOMEM, "device allocation failed");
     const double* in = xyz;
     if (n > 0 && where == TPCF_HOST) {
@@ -478,8 +496,10 @@ extern "C" int tpcf_catalog_create_segmented(tpcf_ctx* ctx, const double* xyz, u
             cudaStreamSynchronize(st) != cudaSuccess)
             return fail_with(TPCF_ECUDA, "segment copy failed");
     }
-    cudaError_t e = launch_prepare(in, (uint32_t)n, seg, sort ? 1 : 0, c->d64, c->d32, c->n_pad, keys,
-                                   vals, n_pow2, err, st);
+    uint32_t nl = 0;
+    cudaError_t e = launch_prepare(in, (uint32_t)n, seg, sort ? 1 : 0, c->d64, c->d32, c->d32x2, c->n_pad, keys,
+                                   vals, n_pow2, err, st, &nl);
+    ctx->launches.fetch_add(nl);
     if (e != cudaSuccess) return fail_with(TPCF_ECUDA, cudaGetErrorString(e));
     unsigned long long herr = 0;
     if (cudaMemcpyAsync(&herr, err, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -505,6 +525,7 @@ extern "C" int tpcf_catalog_destroy(tpcf_catalog* c) {
     cudaDeviceSynchronize();
     if (c->d64) cudaFree(c->d64);
     if (c->d32) cudaFree(c->d32);
+    if (c->d32x2) cudaFree(c->d32x2);
     delete c;
     return TPCF_OK;
 }
@@ -522,37 +543,47 @@ struct SubSpec {
     uint32_t a_off, b_off;  // first point of the range in the catalog
 };
 
-bool choose_shape(tpcf_ctx* ctx, int precision, int nedges, uint64_t total_pairs, Shape* sh) {
-    const bool plain = precision == TPCF_PLAIN_FP64;
+int kernel_mode(const tpcf_config& cfg) {
+    if (cfg.precision == TPCF_PLAIN_FP64) return kModePlainFP64;
+    return (cfg.flags & TPCF_F_SCALAR_FMA) ? kModeScreenScalar : kModeScreenPacked;
+}
+
+bool choose_shape(tpcf_ctx* ctx, int mode, int nedges, uint64_t total_pairs, Shape* sh) {
     const tpcf_config& cfg = ctx->cfg;
     // candidate (T, R): the override, or by problem size, then smaller blocks
     // when the per-thread histograms do not fit in shared memory
-    int cand[3][2];
+    int cand[4][2];
     int nc = 0;
     if (cfg.threads != 0 && cfg.ipt != 0) {
         cand[nc][0] = cfg.threads; cand[nc][1] = cfg.ipt; ++nc;
     } else {
         const double per_sm = (double)total_pairs / std::max(1, ctx->num_sms);
-        if (per_sm >= 4e7) { cand[nc][0] = 256; cand[nc][1] = 8; ++nc; }
+        if (per_sm >= 4e7) {
+            cand[nc][0] = 512; cand[nc][1] = 8; ++nc;
+            cand[nc][0] = 256; cand[nc][1] = 8; ++nc;
+        }
         cand[nc][0] = 128; cand[nc][1] = 8; ++nc;
     }
     for (int c = 0; c < nc; ++c) {
         const int T = cand[c][0], R = cand[c][1];
         if (!count_shape_supported(T, R)) continue;
         const int I = T * R;
-        int J = cfg.jtile ? cfg.jtile : (plain ? 1024 : 2048);
+        int J = cfg.jtile ? cfg.jtile : 512;
         if (J > I) J = I;
         if ((int)kPad % J != 0 || (int)kPad % I != 0 || J % 32 != 0 || I % J != 0) continue;
-        size_t smem = count_smem_bytes(precision, T, R, J, 2, nedges);
-        while (smem > ctx->smem_optin && J > 256 && cfg.jtile == 0) {
-            J /= 2;
-            smem = count_smem_bytes(precision, T, R, J, 2, nedges);
+        // deepest pipeline (4 .. 2 stages, or the override) that fits; shrink the tile if needed
+        int S = cfg.stages ? cfg.stages : 4;
+        if (S < 2 || S > 16) continue;
+        size_t smem = count_smem_bytes(mode, T, R, J, S, nedges);
+        while (smem > ctx->smem_optin && ((S > 2 && cfg.stages == 0) || (J > 256 && cfg.jtile == 0))) {
+            if (S > 2 && cfg.stages == 0) --S; else { J /= 2; S = cfg.stages ? cfg.stages : 4; }
+            smem = count_smem_bytes(mode, T, R, J, S, nedges);
         }
         if (smem > ctx->smem_optin) continue;
         sh->threads = T;
         sh->ipt = R;
         sh->jtile = J;
-        sh->stages = 2;
+        sh->stages = S;
         sh->smem = smem;
         sh->blocks = ctx->num_sms;  // one persistent block per SM
         sh->jchunk = I;
@@ -590,7 +621,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     }
     cudaSetDevice(ctx->cfg.device);
     const int ne = bins->nedges;
-    const int prec = ctx->cfg.precision;
+    const int prec = kernel_mode(ctx->cfg);
     uint64_t all_pairs = 0;
     for (int s = 0; s < nsub; ++s) all_pairs += full_pairs(specs[s]);
     Shape sh;
@@ -615,6 +646,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         SubProblem& sp = wd.sub[s];
         sp.a32 = p.a->d32 + p.a_off;
         sp.b32 = p.b->d32 + p.b_off;
+        sp.b32x2 = p.b->d32x2 + 2ull * p.b_off;
         sp.a64 = p.a->d64 + p.a_off;
         sp.b64 = p.b->d64 + p.b_off;
         sp.na = p.na;
@@ -641,6 +673,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     wd.I = I;
     wd.J = J;
     wd.Jc = Jc;
+    wd.stages = (uint32_t)sh.stages;
     wd.flags = ctx->cfg.flags;
     wd.nedges_max = ne;
     wd.wait_limit_ns = (uint64_t)ctx->cfg.wait_timeout_us * 1000ull;
@@ -651,7 +684,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         CUDA_TRY(ctx, cudaEventCreate(&t1));
         CUDA_TRY(ctx, cudaEventRecord(t0, st));
     }
-    uint32_t launches = 1;  // memset is not a kernel of ours
+    uint32_t launches = 0;
     if (wd.item_hi > wd.item_lo) {
         const uint64_t n_launch_items = wd.item_hi - wd.item_lo;
         Shape sl = sh;
@@ -693,6 +726,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         if (errw & kErrWaitTimeout) rc = ctx->fail(TPCF_ETIMEOUT, "a bounded device wait timed out");
         else if (errw) rc = ctx->fail(TPCF_ECUDA, "device error word 0x%llx", errw);
     }
+    ctx->launches.fetch_add(launches);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     CUDA_TRY(ctx, cudaEventRecord(slot.ev, st));
@@ -793,14 +827,22 @@ extern "C" int tpcf_correlate(tpcf_ctx* ctx, const double* d_xyz, uint64_t nd, c
 // and adds 1 to counts[i * nb + j] for every pair (i, j) an item counts.
 // Returns the number of items; *pairs receives the item_pairs total.
 extern "C" int64_t tpcf_plan_coverage(uint32_t na, uint32_t nb, int auto_mode, uint32_t I,
-                                      uint32_t Jc, uint32_t J, uint32_t* counts, uint64_t* pairs) {
+                                      uint32_t Jc, uint32_t J, uint32_t shard_index,
+                                      uint32_t shard_count, uint32_t* counts, uint64_t* pairs) {
     if (I == 0 || J == 0 || Jc == 0 || Jc % J != 0 || (I % Jc != 0 && Jc % I != 0)) return -1;
     if (auto_mode && na != nb) return -1;
+    if (shard_count > 1 && shard_index >= shard_count) return -1;
     if (na == 0 || nb == 0) { if (pairs) *pairs = 0; return 0; }
     const uint32_t n_iblk = (na + I - 1) / I, n_jchunk = (nb + Jc - 1) / Jc;
     const uint64_t items = items_of(n_iblk, n_jchunk, auto_mode != 0, I, Jc);
+    // the same split as the counting launch: items [items*s/S, items*(s+1)/S)
+    uint64_t q_lo = 0, q_hi = items;
+    if (shard_count > 1) {
+        q_lo = items * shard_index / shard_count;
+        q_hi = items * (shard_index + 1) / shard_count;
+    }
     uint64_t total = 0;
-    for (uint64_t q = 0; q < items; ++q) {
+    for (uint64_t q = q_lo; q < q_hi; ++q) {
         ItemGeom g = item_geom(q, na, nb, n_iblk, n_jchunk, auto_mode != 0, I, Jc, J);
         if (g.t_first >= g.t_end) continue;
         total += item_pairs(g, na, nb, auto_mode != 0, I, Jc);
@@ -821,5 +863,5 @@ extern "C" int64_t tpcf_plan_coverage(uint32_t na, uint32_t nb, int auto_mode, u
         }
     }
     if (pairs) *pairs = total;
-    return (int64_t)items;
+    return (int64_t)(q_hi - q_lo);
 }

@@ -31,7 +31,8 @@ struct BinsDev {
     int nlut;
     int lut_shift;
     int32_t lut_key0;       // ordered key of lo[B] (the range limit T)
-    float range_t;          // T = lo[B]: an FP32 cosine below T is certainly overflow
+    float range_t;          // lo[B]: a plain FP32 cosine below it is certainly overflow
+    float fast_t;           // RD(C_B - 10u): a range-offset FP32 screen value below 0 is overflow
     double cos_last;        // C_B (binary64 range limit, plain kernel)
 };
 
@@ -41,6 +42,7 @@ struct BinsDev {
 struct SubProblem {
     const float4* a32;    // FP32 screen copy of A (padded to kPad)
     const float4* b32;
+    const float4* b32x2;  // B as (x,x,y,y),(z,z,0,0): two float4 per point (packed FMA)
     const Point64* a64;   // binary64 copy of A (padded)
     const Point64* b64;
     uint32_t na, nb;      // real point counts
@@ -70,6 +72,7 @@ struct WorkDesc {
     uint64_t item_lo, item_hi;       // item range of this launch (shards, serving quanta)
     unsigned long long* stats;       // kStatWords words
     uint32_t I, J, Jc;               // i-block, j-tile, j-chunk sizes (points)
+    uint32_t stages;                 // shared-memory pipeline depth S (2..16)
     uint32_t flags;                  // TPCF_F_* subset used on the device
     int nedges_max;                  // largest B + 1 over the sub-problems (shared-memory sizing)
     uint64_t wait_limit_ns;          // bounded waits
@@ -86,19 +89,24 @@ struct Shape {
     size_t smem;   // dynamic shared memory bytes
 };
 
+// Kernel variants (mode argument of the launchers): FP32 screen with scalar
+// FMA, all-binary64 comparator, FP32 screen with packed FP32x2 FMA.
+enum { kModeScreenScalar = 0, kModePlainFP64 = 1, kModeScreenPacked = 2 };
+
 // Launchers (kernels.cu).  All are asynchronous in `stream` and return a
 // cudaError_t from the launch.
-cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int precision, int nedges,
+cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int mode, int nedges,
                          cudaStream_t stream);
 cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long long* out,
                             unsigned long long total, unsigned long long* err_word,
                             cudaStream_t stream);
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
-                           int sort, Point64* out64, float4* out32, uint32_t n_pad,
+                           int sort, Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
                            unsigned long long* key_scratch, uint32_t* val_scratch,
-                           uint32_t n_pow2, unsigned long long* err_word, cudaStream_t stream);
-size_t count_smem_bytes(int precision, int threads, int ipt, int jtile, int stages, int nedges);
+                           uint32_t n_pow2, unsigned long long* err_word, cudaStream_t stream,
+                           uint32_t* launches);
+size_t count_smem_bytes(int mode, int threads, int ipt, int jtile, int stages, int nedges);
 bool count_shape_supported(int threads, int ipt);
-cudaError_t count_set_smem_limit(int precision, int threads, int ipt, size_t bytes);
+cudaError_t count_set_smem_limit(int mode, int threads, int ipt, size_t bytes);
 
 }  // namespace tpcf

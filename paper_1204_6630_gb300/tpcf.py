@@ -31,6 +31,7 @@ TPCF_SCREEN_RECHECK, TPCF_PLAIN_FP64 = 0, 1
 TPCF_LS_EXACT, TPCF_LS_PAPER = 0, 1
 TPCF_F_NO_SORT = 0x1
 TPCF_F_DYNAMIC_SCHED = 0x2
+TPCF_F_SCALAR_FMA = 0x4
 TPCF_F_TEST_WAIT_TIMEOUT = 0x100
 TPCF_MAX_EDGES = 321
 
@@ -47,7 +48,7 @@ class TpcfError(RuntimeError):
 class tpcf_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("precision", ctypes.c_int), ("guard_band", ctypes.c_double),
                 ("hbm_budget_bytes", ctypes.c_uint64), ("flags", ctypes.c_uint32),
-                ("threads", ctypes.c_int), ("ipt", ctypes.c_int), ("jtile", ctypes.c_int),
+                ("threads", ctypes.c_int), ("ipt", ctypes.c_int), ("jtile", ctypes.c_int), ("stages", ctypes.c_int),
                 ("shard_index", ctypes.c_uint32), ("shard_count", ctypes.c_uint32),
                 ("wait_timeout_us", ctypes.c_uint32)]
 
@@ -74,6 +75,7 @@ _SIGS = {
     "tpcf_last_error": (ctypes.c_char_p, [_vp]),
     "tpcf_config_default": (None, [ctypes.POINTER(tpcf_config)]),
     "tpcf_version": (ctypes.c_int, []),
+    "tpcf_kernel_launches": (_u64, [_vp]),
     "tpcf_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(tpcf_config)]),
     "tpcf_destroy": (ctypes.c_int, [_vp]),
     "tpcf_catalog_create": (ctypes.c_int, [_vp, _vp, _u64, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
@@ -95,7 +97,7 @@ _SIGS = {
     "tpcf_correlate": (ctypes.c_int, [_vp, _vp, _u64, _vp, _u64, _dp, ctypes.c_int, ctypes.c_int, _vp,
                                       _u64p, _u64p, _u64p, _dp, ctypes.POINTER(tpcf_stats)]),
     "tpcf_plan_coverage": (ctypes.c_int64, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32,
-                                            ctypes.c_uint32, ctypes.c_uint32,
+                                            ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_uint32), _u64p]),
     "tpcf_debug_fail_alloc_after": (None, [ctypes.c_int]),
 }
@@ -178,6 +180,10 @@ def tpcf_config_default() -> tpcf_config:
 
 def tpcf_version() -> int:
     return load().tpcf_version()
+
+
+def tpcf_kernel_launches(ctx: int) -> int:
+    return int(load().tpcf_kernel_launches(ctx))
 
 
 def tpcf_create(cfg: tpcf_config | None = None) -> int:
@@ -339,10 +345,11 @@ def tpcf_correlate(ctx: int, d_xyz, r_xyz, edges_rad, estimator: int = TPCF_LS_E
     return (dd, dr, rr, w, st.as_dict()) if st is not None else (dd, dr, rr, w)
 
 
-def tpcf_plan_coverage(na: int, nb: int, auto_mode: bool, I: int, Jc: int, J: int, with_counts=True):
+def tpcf_plan_coverage(na: int, nb: int, auto_mode: bool, I: int, Jc: int, J: int, with_counts=True,
+                       shard_index: int = 0, shard_count: int = 0):
     counts = np.zeros(na * nb, np.uint32) if with_counts else None
     pairs = ctypes.c_uint64(0)
-    items = load().tpcf_plan_coverage(na, nb, int(auto_mode), I, Jc, J,
+    items = load().tpcf_plan_coverage(na, nb, int(auto_mode), I, Jc, J, shard_index, shard_count,
                                       counts.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
                                       if counts is not None else None, ctypes.byref(pairs))
     if items < 0:
