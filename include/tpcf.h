@@ -228,6 +228,35 @@ int tpcf_correlate(tpcf_ctx *ctx, const double *d_xyz, uint64_t nd, const double
                    uint64_t nr, const double *edges_rad, int nedges, int estimator, void *stream,
                    uint64_t *dd, uint64_t *dr, uint64_t *rr, double *w, tpcf_stats *st);
 
+/* ------------------------------------------------------------------ no-allocation variant
+ * tpcf_count_auto_noalloc: the auto-count histogram (DD or RR; same
+ * conventions and the same counts as tpcf_count_auto) of n unit vectors that
+ * the caller already holds in device memory, computed without allocating any
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory themselves, such as code running inside
+ * a framework whose caching allocator owns the device memory, or a
+ * latency-sensitive loop that cannot afford cudaMalloc / cudaFree (both
+ * synchronize the device).  It needs no context.
+ *   xyz_dev: device array of n x 3 binary64 unit vectors, row-major (not
+ *            validated: non-finite or non-unit input gives unspecified counts);
+ *   edges_rad: host array of nedges edges (as in tpcf_bins_create);
+ *   hist_dev: device array of nedges + 1 uint64, written in `stream` order.
+ * Every pair is computed in binary64 (the all-FP64 kernel), one launch plus a
+ * finalize launch, asynchronous in `stream`.
+ * Scratch: the uint64 accumulators live in a fixed 4 KB __device__ array of
+ * the library, held by every GPU that loads the library until the process
+ * exits.  Limit: nedges <= TPCF_MAX_EDGES (321); larger values return
+ * TPCF_EOVERFLOW before anything is launched, as do n > TPCF_MAX_POINTS.
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress on the current device); make that first call
+ * before any stream capture.  All calls on a device share the one array: the
+ * call clears it first, and calls that overlap on the GPU (other streams,
+ * other threads) race and give wrong counts; serialize them.
+ * Returns TPCF_EINVAL for NULL pointers or invalid edges, TPCF_ECUDA when a
+ * CUDA call fails. */
+int tpcf_count_auto_noalloc(const double *xyz_dev, uint64_t n, const double *edges_rad, int nedges,
+                            void *stream, uint64_t *hist_dev);
+
 /* ------------------------------------------------------------------ self-check hooks
  * Host-only helpers used by the test-suite (no GPU needed).
  *

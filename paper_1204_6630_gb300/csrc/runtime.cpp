@@ -330,6 +330,17 @@ void build_lut(const std::vector<float>& lo, const std::vector<float>& hi, std::
 
 }  // namespace
 
+// Binary64 thresholds C_k for nedges valid edges into a caller array; no
+// allocation (used by the no-allocation entry point).
+bool tpcf::derive_cos_thresholds(const double* edges, int nedges, double* cos_thr) {
+    if (!edges_valid(edges, nedges)) return false;
+    for (int k = 0; k < nedges; ++k) {
+        int ver;
+        cos_thr[k] = derive_threshold(edges[k], &ver);
+    }
+    return true;
+}
+
 extern "C" int tpcf_bins_thresholds(const double* edges, int nedges, double guard, double* cos_thr,
                                     float* lo, float* hi, int* verified) {
     if (!edges_valid(edges, nedges)) return TPCF_EINVAL;
@@ -621,11 +632,16 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     }
     cudaSetDevice(ctx->cfg.device);
     const int ne = bins->nedges;
-    const int prec = kernel_mode(ctx->cfg);
+    int prec = kernel_mode(ctx->cfg);
     uint64_t all_pairs = 0;
     for (int s = 0; s < nsub; ++s) all_pairs += full_pairs(specs[s]);
     Shape sh;
-    if (!choose_shape(ctx, prec, ne, all_pairs, &sh))
+    bool fits = choose_shape(ctx, prec, ne, all_pairs, &sh);
+    if (!fits && prec == kModeScreenPacked) {  // the packed stage layout is twice as large
+        prec = kModeScreenScalar;
+        fits = choose_shape(ctx, prec, ne, all_pairs, &sh);
+    }
+    if (!fits)
         return ctx->fail(TPCF_EINVAL, "no kernel shape fits (threads=%d ipt=%d jtile=%d)",
                          ctx->cfg.threads, ctx->cfg.ipt, ctx->cfg.jtile);
     const uint32_t I = (uint32_t)(sh.threads * sh.ipt), J = (uint32_t)sh.jtile;

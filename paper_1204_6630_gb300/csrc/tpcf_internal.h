@@ -107,6 +107,7 @@ cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg
                            uint32_t* launches);
 size_t count_smem_bytes(int mode, int threads, int ipt, int jtile, int stages, int nedges);
 bool count_shape_supported(int threads, int ipt);
+bool derive_cos_thresholds(const double* edges, int nedges, double* cos_thr);
 cudaError_t count_set_smem_limit(int mode, int threads, int ipt, size_t bytes);
 
 }  // namespace tpcf

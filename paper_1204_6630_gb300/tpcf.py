@@ -100,6 +100,7 @@ _SIGS = {
                                             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_uint32), _u64p]),
     "tpcf_debug_fail_alloc_after": (None, [ctypes.c_int]),
+    "tpcf_count_auto_noalloc": (ctypes.c_int, [_vp, _u64, _dp, ctypes.c_int, _vp, _vp]),
 }
 
 
@@ -355,6 +356,26 @@ def tpcf_plan_coverage(na: int, nb: int, auto_mode: bool, I: int, Jc: int, J: in
     if items < 0:
         raise ValueError("bad plan sizes")
     return items, int(pairs.value), (counts.reshape(na, nb) if counts is not None else None)
+
+
+def tpcf_count_auto_noalloc(xyz_dev, edges_rad, out_dev, stream=None) -> None:
+    """Auto-count histogram without any allocation (see include/tpcf.h).
+
+    ``xyz_dev``: CUDA tensor (n, 3) float64; ``out_dev``: CUDA tensor of
+    len(edges) + 1 int64 (uint64 bit patterns), written in stream order.
+    """
+    if not (_is_torch(xyz_dev) and xyz_dev.is_cuda and _is_torch(out_dev) and out_dev.is_cuda):
+        raise ValueError("xyz_dev and out_dev must be CUDA tensors")
+    import torch
+    if xyz_dev.dtype != torch.float64 or not xyz_dev.is_contiguous() or xyz_dev.dim() != 2 \
+            or xyz_dev.shape[1] != 3:
+        raise ValueError("xyz_dev must be a contiguous (n, 3) float64 tensor")
+    e = np.ascontiguousarray(edges_rad, dtype=np.float64)
+    if out_dev.dtype != torch.int64 or not out_dev.is_contiguous() or out_dev.numel() != len(e) + 1:
+        raise ValueError("out_dev must be a contiguous int64 tensor of len(edges) + 1")
+    rc = load().tpcf_count_auto_noalloc(xyz_dev.data_ptr(), xyz_dev.shape[0], e.ctypes.data_as(_dp), len(e),
+                                        _stream_ptr(stream), out_dev.data_ptr())
+    _check(rc, "tpcf_count_auto_noalloc")
 
 
 def tpcf_debug_fail_alloc_after(n: int) -> None:
