@@ -87,7 +87,7 @@ extern "C" {
 /* configuration flags */
 #define TPCF_F_NO_SORT 0x1u          /* keep catalog order (no spatial sort on the device) */
 #define TPCF_F_DYNAMIC_SCHED 0x2u    /* persistent blocks take work from an atomic counter */
-#define TPCF_F_SCALAR_FMA 0x4u       /* FP32 screen with scalar FMA instead of packed FP32x2 FMA */
+#define TPCF_F_PACKED_FMA 0x4u       /* FP32 screen with packed FP32x2 FMA (fma.rn.f32x2) instead of scalar FMA */
 #define TPCF_F_TEST_WAIT_TIMEOUT 0x100u /* test hook: the first j-tile copy of each counting
                                            launch is never issued, so its bounded wait expires
                                            and the call returns TPCF_ETIMEOUT */
@@ -104,9 +104,10 @@ typedef struct tpcf_bins tpcf_bins;
 typedef struct tpcf_config {
     int device;                /* CUDA device ordinal */
     int precision;             /* TPCF_SCREEN_RECHECK or TPCF_PLAIN_FP64 */
-    double guard_band;         /* half-width g of the recheck band in cos(theta); 0 -> 6 * 2^-24.
-                                  Must be >= 6 * 2^-24: the FP32 cosine is within 5.0001 * 2^-24
-                                  of the binary64 dot product (TPCF_EINVAL below that). */
+    double guard_band;         /* half-width g of the recheck band in cos(theta); 0 -> 9 * 2^-24.
+                                  Must be >= 9 * 2^-24: the FP32 screen value is within
+                                  8.0003 * 2^-24 of the binary64 dot product minus the range
+                                  offset (TPCF_EINVAL below that). */
     uint64_t hbm_budget_bytes; /* device memory the job server may hold for catalogs; 0 -> 120 GB
                                   capped at 80% of free memory */
     uint32_t flags;            /* TPCF_F_* */
@@ -135,7 +136,7 @@ const char *tpcf_strerror(int status);
 /* Last error message recorded on ctx (empty string if none).  Not thread-safe
  * with respect to concurrent failing calls on the same context. */
 const char *tpcf_last_error(const tpcf_ctx *ctx);
-/* Fills *cfg with the defaults (device 0, screen + recheck, g = 6 * 2^-24). */
+/* Fills *cfg with the defaults (device 0, screen + recheck, g = 9 * 2^-24). */
 void tpcf_config_default(tpcf_config *cfg);
 /* Library version as major * 10000 + minor * 100 + patch. */
 int tpcf_version(void);
@@ -183,7 +184,7 @@ int tpcf_bins_create(tpcf_ctx *ctx, const double *edges_rad, int nedges, tpcf_bi
 int tpcf_bins_destroy(tpcf_bins *bins);
 /* Host-only: the thresholds for edges_rad (no context or GPU needed).
  * cos_thr[k] = C_k (+inf for t_k = 0); lo[k], hi[k] the FP32 screen bounds for
- * guard band g (0 -> 6 * 2^-24); verified[k] = 1 when the neighbour scan around
+ * guard band g (0 -> 9 * 2^-24); verified[k] = 1 when the neighbour scan around
  * C_k covered at least 4 ulps of t_k on each side and found the predicate
  * monotone, 0 otherwise.  Any output pointer may be NULL. */
 int tpcf_bins_thresholds(const double *edges_rad, int nedges, double guard_band, double *cos_thr,

@@ -118,9 +118,7 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
 // consumer (all threads) and the producer (thread 0, S tiles ahead) each
 // keep one.
 struct Cursor {
-    uint64_t q;       // global item index
-    uint64_t q_end;
-    uint32_t stride;
+    uint32_t q;       // walk position
     int sub;
     ItemGeom g;
     uint32_t t;       // current tile within the item
@@ -140,31 +138,34 @@ __device__ int find_sub(const WorkDesc& wd, uint64_t q) {
     return lo;
 }
 
-// Load item q (and skip items without countable tiles).
+// Load the item at walk position c.q (and skip items without countable
+// tiles).  Within a sub-problem, position item_begin + k visits local item
+// (k * walk_mult) mod n_items (see walk_item).  Positions fit 32 bits (the
+// host checks the item count).
 __device__ void cursor_load(const WorkDesc& wd, Cursor& c) {
-    while (c.q < c.q_end) {
+    const uint32_t q_end = (uint32_t)wd.item_hi;
+    while (c.q < q_end) {
         c.sub = find_sub(wd, c.q);
         const SubProblem& sp = sub_of(wd, c.sub);
-        c.g = item_geom(c.q - sp.item_begin, sp.na, sp.nb, sp.n_iblk, sp.n_jchunk,
-                        sp.auto_mode != 0, wd.I, wd.Jc, wd.J);
+        const uint64_t local = walk_item(c.q - sp.item_begin, sp.n_items, sp.walk_mult);
+        c.g = item_geom(local, sp.na, sp.nb, sp.n_iblk, sp.n_jchunk, sp.auto_mode != 0, wd.I, wd.Jc,
+                        wd.J);
         c.t = c.g.t_first;
         if (c.t < c.g.t_end) { c.valid = true; return; }
-        c.q += c.stride;
+        c.q += gridDim.x;
     }
     c.valid = false;
 }
 
 __device__ void cursor_begin(const WorkDesc& wd, Cursor& c) {
-    c.q = wd.item_lo + blockIdx.x;
-    c.q_end = wd.item_hi;
-    c.stride = gridDim.x;
+    c.q = (uint32_t)wd.item_lo + blockIdx.x;
     cursor_load(wd, c);
 }
 
 __device__ void cursor_next(const WorkDesc& wd, Cursor& c) {
     if (!c.valid) return;
     if (++c.t < c.g.t_end) return;
-    c.q += c.stride;
+    c.q += gridDim.x;
     cursor_load(wd, c);
 }
 
@@ -177,17 +178,18 @@ enum KernelMode { kModeScreen = 0, kModePlain = 1, kModeScreen2 = 2 };
 enum Ctl { kCtlAbort = 0, kCtlWarpsDone = 1, kCtlIssued = 2, kCtlRelease = 8, kCtlQueue = 24,
            kCtlWords = 64 };
 constexpr int kMaxStages = 16;   // release counters live at kCtlRelease + stage
-constexpr int kQueuePerWarp = 64;
+constexpr int kQueuePerWarp = 64;   // band pairs per warp awaiting the binary64 recheck
 
 struct SmemLayout {
     uint32_t bars;      // S full mbarriers
     uint32_t ctl;       // control words
     uint32_t stage;     // S * J * pt_bytes
-    uint32_t hist;      // (nedges + 1) * T uint32: row h, column tid
+    uint32_t hist;      // ceil((nedges + 1) / 2) * T uint32: rows 2w, 2w+1 as 16-bit halves, column tid
     uint32_t cos_thr;   // nedges doubles
     uint32_t lo, hi, cos32;  // nedges floats each
     uint32_t lut;       // kLutMax uint32 (screen only)
-    uint32_t queue;     // W * kQueuePerWarp band entries (uint4, screen only)
+    uint32_t queue;     // W * kQueuePerWarp band pairs (uint4, screen only)
+    uint32_t prod;      // W producer cursors (one per warp, used by its lane 0)
     uint32_t total;
 };
 
@@ -202,7 +204,7 @@ __host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S,
     L.ctl = off; off += kCtlWords * 4;
     off = align_up(off, 128);
     L.stage = off; off += (uint32_t)S * J * pt;
-    L.hist = off; off += (uint32_t)(nedges + 1) * T * 4;
+    L.hist = off; off += (uint32_t)((nedges + 2) / 2) * T * 4;
     off = align_up(off, 16);
     L.cos_thr = off; off += (uint32_t)nedges * 8;
     L.lo = off; off += (uint32_t)nedges * 4;
@@ -212,6 +214,8 @@ __host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S,
     L.lut = off; off += plain ? 0u : (uint32_t)kLutMax * 4;
     off = align_up(off, 16);
     L.queue = off; off += plain ? 0u : (uint32_t)(T / 32) * kQueuePerWarp * 16;
+    off = align_up(off, 16);
+    L.prod = off; off += (uint32_t)(T / 32) * (uint32_t)align_up(sizeof(Cursor), 16);
     L.total = off;
     return L;
 }
@@ -231,31 +235,53 @@ __device__ void load_bins(const BinsDev* bd, unsigned char* smem, const SmemLayo
         c32[k] = bd->cos32[k];
     }
     if (!plain) {
+        // Shared copy of the LUT re-encoded for this block shape: a settled entry
+        // (P == Q) holds the word offset (P / 2) * T of the thread's histogram
+        // word in bits 0..15 and the 16-bit half (P & 1) in bit 16; an
+        // unsettled entry has bit 31 set and P, Q in bits 0..11, 12..23.
         uint32_t* lut = (uint32_t*)(smem + L.lut);
-        for (int k = threadIdx.x; k < bd->nlut; k += T) lut[k] = bd->lut[k];
+        for (int k = threadIdx.x; k < bd->nlut; k += T) {
+            const uint32_t e = bd->lut[k];
+            const uint32_t P = e & 0xffffu, Q = e >> 16;
+            lut[k] = (P == Q) ? ((P >> 1) * (uint32_t)T) | ((P & 1u) << 16)
+                              : 0x80000000u | P | (Q << 12);
+        }
     }
 }
 
 // One warp merges its 32 private histogram columns into the global uint64
-// bins and zeroes them.  Rows 0..nedges-1 (underflow and the B bins) are
-// merged; the last row (pairs found beyond the last edge) is dropped:
-// overflow is derived from the pair total by the finalize kernel.
+// bins and zeroes them.  Each 32-bit word holds two 16-bit counters (rows 2w
+// and 2w + 1).  Rows 0..nedges-1 (underflow and the B bins) are merged; row
+// nedges (pairs found beyond the last edge) is dropped: overflow is derived
+// from the pair total by the finalize kernel.
 template <int T>
 __device__ void warp_flush_hist(uint32_t* hist, int nedges, unsigned long long* out) {
     const int lane = threadIdx.x & 31;
-    for (int h = 0; h <= nedges; ++h) {
-        uint32_t* p = hist + h * T + threadIdx.x;
-        unsigned long long v = *p;
+    const int words = (nedges + 2) / 2;
+    for (int w = 0; w < words; ++w) {
+        uint32_t* p = hist + w * T + threadIdx.x;
+        const uint32_t v = *p;
         *p = 0;
+        uint32_t lo = v & 0xffffu, hi = v >> 16;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0 && v != 0 && h < nedges) atomicAdd(out + h, v);
+        for (int o = 16; o > 0; o >>= 1) {
+            lo += __shfl_down_sync(0xffffffffu, lo, o);
+            hi += __shfl_down_sync(0xffffffffu, hi, o);
+        }
+        if (lane == 0) {
+            if (lo != 0 && 2 * w < nedges) atomicAdd(out + 2 * w, (unsigned long long)lo);
+            if (hi != 0 && 2 * w + 1 < nedges) atomicAdd(out + 2 * w + 1, (unsigned long long)hi);
+        }
     }
 }
 
-// Thread-private histogram increment (one shared-memory reduction instruction).
-__device__ __forceinline__ void hist_inc(uint32_t* p) {
-    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(smem_addr(p)) : "memory");
+// Thread-private histogram increment of row h (one shared-memory reduction
+// instruction on the 16-bit half of the row pair's word).
+template <int T>
+__device__ __forceinline__ void hist_inc(uint32_t* hcol, int h) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_addr(hcol + (h >> 1) * T)),
+                 "r"(1u << ((h & 1) << 4))
+                 : "memory");
 }
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
@@ -301,53 +327,142 @@ __device__ __forceinline__ int band_index(const Point64* a64, const Point64* b64
 // FP32 classification of a pair with FP32 cosine c >= lo_B.  The LUT entry of
 // c's key range holds P = nb(c_max) and Q = na(c_min), where
 // nb(c) = #{m : c < lo_m} (edges certainly crossed) and
-// na(c) = #{m : c <= hi_m} (edges possibly crossed).  Returns h >= 0 when the
-// index is settled; otherwise -1 and the band range [nbv, nav) plus the
-// FP32-only index h32.
-__device__ __forceinline__ int classify_f32(float c, const unsigned char* smem, const SmemLayout& L,
-                                            int32_t key0, int shift, int nlut, int& nbv, int& nav,
-                                            int& h32) {
-    const uint32_t* lut = (const uint32_t*)(smem + L.lut);
-    // c >= lo_B gives idx >= 0; c <= 1 + 6u keeps idx below nlut (clamped for safety)
-    int idx = (f32_key(c) - key0) >> shift;
-    idx = idx < nlut ? idx : nlut - 1;
-    const uint32_t ent = lut[idx];
-    const int P = (int)(ent & 0xffffu), Q = (int)(ent >> 16);
-    if (P == Q) return P;
-    const float* lo = (const float*)(smem + L.lo);
-    const float* hi = (const float*)(smem + L.hi);
+// na(c) = #{m : c <= hi_m} (edges possibly crossed); P == Q settles the index.
+// resolve_f32: for an unsettled entry, compare c with the few edges in [P, Q).
+// Returns h >= 0 when settled; otherwise h = -1 with the band range
+// [nbv, nav) and the FP32-only index h32.  Arguments and result are plain
+// values so that no local object's address escapes into this rare call.
+struct Resolved {
+    int h, nbv, nav, h32;
+};
+
+__device__ __noinline__ Resolved resolve_f32(float c, int P, int Q, const float* lo, const float* hi,
+                                             const float* c32) {
     int nb_ = P, na_ = P;
     for (int m = P; m < Q; ++m) {
         nb_ += (c < lo[m]);
         na_ += (c <= hi[m]);
     }
-    if (nb_ == na_) return nb_;
-    const float* c32 = (const float*)(smem + L.cos32);
+    if (nb_ == na_) return Resolved{nb_, 0, 0, 0};
     int h = nb_;
     for (int m = nb_; m < na_; ++m) h += (c <= c32[m]);
-    nbv = nb_;
-    nav = na_;
-    h32 = h;
-    return -1;
+    return Resolved{-1, nb_, na_, h};
 }
 
-// One warp recomputes its queued band pairs in binary64; each lane adds to
-// its own histogram column.  Ends with the warp's queue empty.
+// One warp recomputes its queued band pairs in binary64: entry (i, j,
+// nbv | nav << 16, h32).  Each lane adds to its own histogram column; ends
+// with the warp's queue empty.  Not inlined (rare and large); returns the
+// lane's band statistics so that no local object's address escapes.
 template <int T>
-__device__ void warp_drain_queue(const uint4* wq, volatile int* wq_count, const Point64* a64,
-                                 const Point64* b64, const double* cthr, uint32_t* hcol,
-                                 BandStats& bs) {
+__device__ __forceinline__ BandStats warp_drain_queue(const uint4* wq, volatile int* wq_count,
+                                                   const Point64* a64, const Point64* b64,
+                                                   const double* cthr, uint32_t* hcol) {
+    BandStats bs = {0ull, 0ull};
     __syncwarp();
     const int n = min(*wq_count, kQueuePerWarp);
     for (int k = (int)(threadIdx.x & 31); k < n; k += 32) {
-        const uint4 e = wq[k];
-        const int h = band_index(a64, b64, e.x, e.y, (int)(e.z & 0xffffu), (int)(e.z >> 16),
-                                 (int)e.w, cthr, bs);
-        hist_inc(hcol + h * T);
+        const uint4 q = wq[k];
+        const int h = band_index(a64, b64, q.x, q.y, (int)(q.z & 0xffffu), (int)(q.z >> 16), (int)q.w,
+                                 cthr, bs);
+        hist_inc<T>(hcol, h);
     }
     __syncwarp();
     if ((threadIdx.x & 31) == 0) *wq_count = 0;
     __syncwarp();
+    return bs;
+}
+
+// Slow path for one j (warp-uniform).  Branch-free over the R pairs of each
+// lane: every in-range pair's LUT entry is loaded (G independent shared loads
+// in flight) and pairs with a settled entry increment the thread's own
+// histogram word directly from the entry (predicated red.shared).  The rare
+// unsettled pairs are compared with the edges left open (resolve_f32); pairs
+// inside a guard band go to the warp's queue for the binary64 recheck.
+struct SlowCtx {
+    const uint32_t* lut;
+    const float* lo;
+    const float* hi;
+    const float* c32;
+    int32_t key0;
+    int shift, nlut;
+    bool need_idx;
+    uint32_t na;
+    const Point64* a64;
+    const Point64* b64;
+    const double* cthr;
+    uint4* wq;
+    volatile int* wq_count;
+};
+
+template <int T>
+__device__ __forceinline__ void drain(const SlowCtx& sc, uint32_t* hcol, BandStats& bs) {
+    const BandStats d = warp_drain_queue<T>(sc.wq, sc.wq_count, sc.a64, sc.b64, sc.cthr, hcol);
+    bs.band += d.band;
+    bs.mismatch += d.mismatch;
+}
+
+template <int T>
+__device__ __forceinline__ void resolve_pair(float e, uint32_t ent, uint32_t ig, uint32_t jg,
+                                             const SlowCtx& sc, uint32_t* hcol, BandStats& bs) {
+    const Resolved rs = resolve_f32(e, (int)(ent & 0xfffu), (int)((ent >> 12) & 0xfffu), sc.lo, sc.hi, sc.c32);
+    int h = rs.h;
+    if (h < 0) {
+        const int pos = atomicAdd((int*)sc.wq_count, 1);
+        if (pos < kQueuePerWarp) {
+            sc.wq[pos] = make_uint4(ig, jg, (uint32_t)rs.nbv | ((uint32_t)rs.nav << 16), (uint32_t)rs.h32);
+            return;
+        }
+        h = band_index(sc.a64, sc.b64, ig, jg, rs.nbv, rs.nav, rs.h32, sc.cthr, bs);
+    }
+    hist_inc<T>(hcol, h);
+}
+
+template <int T, int R>
+__device__ __forceinline__ void slow_e(const float (&e)[R], uint32_t ibase, uint32_t jg, bool j_ok,
+                                       bool masked, const SlowCtx& sc, uint32_t* hcol, BandStats& bs) {
+    constexpr int G = 4;  // pairs per batch: G LUT loads in flight per lane
+    const uint32_t hbase = smem_addr(hcol);
+    // pairs that may be counted: all, unless indices need checking (padding
+    // inside the range) or the tile straddles the diagonal (j > i only)
+    uint32_t valid = (1u << R) - 1u;
+    if (sc.need_idx || masked) {
+        valid = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t ig = ibase + 32u * r;
+            const bool ok = (!sc.need_idx || (j_ok && ig < sc.na)) && (!masked || jg > ig);
+            valid |= ok ? (1u << r) : 0u;
+        }
+    }
+#pragma unroll
+    for (int r0 = 0; r0 < R; r0 += G) {
+        uint32_t ent[G];
+        uint32_t amb = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int r = r0 + g;
+            const bool in = e[r] >= 0.f && (valid & (1u << r));
+            // LUT index from the bits of RN(1 + e): linear in e on [0, 1)
+            int idx = (__float_as_int(__fadd_rn(1.0f, e[r])) - sc.key0) >> sc.shift;
+            idx = in ? min(idx, sc.nlut - 1) : 0;
+            ent[g] = sc.lut[idx];
+            const bool settled = (int)ent[g] >= 0;
+            if (in && settled) {
+                asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hbase + ((ent[g] & 0xffffu) << 2)),
+                             "r"(1u << ((ent[g] >> 12) & 16u))
+                             : "memory");
+            }
+            amb |= (in && !settled) ? (1u << g) : 0u;
+        }
+        if (amb) {
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (amb & (1u << g))
+                    resolve_pair<T>(e[r0 + g], ent[g], ibase + 32u * (r0 + g), jg, sc, hcol, bs);
+        }
+    }
+    __syncwarp();
+    if (*sc.wq_count >= kQueuePerWarp / 2) drain<T>(sc, hcol, bs);
 }
 
 // ============================================================== the counting kernel
@@ -393,17 +508,33 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         fence_mbar_init();
     }
     for (int k = tid; k < kCtlWords; k += T) ctl[k] = 0;
-    for (int k = tid; k < (nedges + 1) * T; k += T) hist[k] = 0;
+    for (int k = tid; k < ((nedges + 2) / 2) * T; k += T) hist[k] = 0;
     const BinsDev* bd = sub_of(wd, cons.sub).bins;
     load_bins<T>(bd, smem, L, PLAIN);
     const int ne = bd->nedges;
-    const float band_t = bd->range_t;
     const float neg_fast_t = -bd->fast_t;
     const double cos_last = bd->cos_last;
     const int32_t key0 = bd->lut_key0;
     const int lut_shift = bd->lut_shift, nlut = bd->nlut;
-    const bool need_idx = !(band_t > 0.f);  // zero-vector padding has cosine 0
+    // zero-vector padding has screen value e = -T: it can look in range only when T <= 0
+    const bool need_idx = !(bd->fast_t > 0.f);
     __syncthreads();
+    SlowCtx sctx;
+    sctx.lut = (const uint32_t*)(smem + L.lut);
+    sctx.lo = (const float*)(smem + L.lo);
+    sctx.hi = (const float*)(smem + L.hi);
+    sctx.c32 = (const float*)(smem + L.cos32);
+    sctx.key0 = key0;
+    sctx.shift = lut_shift;
+    sctx.nlut = nlut;
+    sctx.need_idx = need_idx;
+    sctx.na = 0;
+    sctx.a64 = nullptr;
+    sctx.b64 = nullptr;
+    sctx.cthr = cthr;
+    sctx.wq = wq;
+    sctx.wq_count = wq_count;
+
 
     auto issue = [&](uint32_t seq, const Cursor& pc) {
         const SubProblem& sp = sub_of(wd, pc.sub);
@@ -416,24 +547,30 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         bulk_copy_g2s(dst, src, stage_bytes, &bars[seq % (uint32_t)S]);
     };
 
-    // ---- prologue: thread 0 issues the first S tiles; every warp keeps a
-    // producer cursor S tiles ahead for its refill turns.
-    Cursor prod = cons;
-    {
+    // ---- prologue: thread 0 issues the first S tiles; lane 0 of every warp
+    // keeps a producer cursor S tiles ahead (in shared memory) for its refill
+    // turns.
+    Cursor* prod = (Cursor*)(smem + L.prod + (uint32_t)warp * align_up(sizeof(Cursor), 16));
+    if (lane == 0) {
+        Cursor pc = cons;
         int k = 0;
-        for (; k < S && prod.valid; ++k) {
-            if (tid == 0) issue((uint32_t)k, prod);
-            cursor_next(wd, prod);
+        for (; k < S && pc.valid; ++k) {
+            if (tid == 0) issue((uint32_t)k, pc);
+            cursor_next(wd, pc);
         }
+        *prod = pc;
         if (tid == 0) ctl[kCtlIssued] = k;
     }
+    __syncwarp();
 
     // ---- consumer state
     int cur_sub = -1;
     unsigned long long* cur_hist = nullptr;
     uint64_t j_since_flush = 0;
-    // a lane adds at most R per j plus at most 2 per queue drain (one drain per 4 j)
-    const uint64_t flush_limit = (0xffffffffull / (R + 1)) - (uint64_t)J;
+    // 16-bit counters: a lane adds at most R per j to one row plus at most 2 per
+    // queue drain (one drain per 4 j), so merging every 65535 / (R + 1) - J
+    // j-points keeps every counter below 2^16
+    const uint64_t flush_limit = (0xffffull / (R + 1)) - (uint64_t)J;
     float ax[MODE == kModeScreen ? R : 1], ay[MODE == kModeScreen ? R : 1], az[MODE == kModeScreen ? R : 1];
     unsigned long long px[PACKED ? R / 2 : 1], py[PACKED ? R / 2 : 1], pz[PACKED ? R / 2 : 1];
     double dx[PLAIN ? R : 1], dy[PLAIN ? R : 1], dz[PLAIN ? R : 1];
@@ -452,7 +589,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             const SubProblem& sp = sub_of(wd, cons.sub);
             if (cons.sub != cur_sub) {
                 if (cur_hist != nullptr) {
-                    if constexpr (!PLAIN) warp_drain_queue<T>(wq, wq_count, a64, b64, cthr, hcol, bs);
+                    if constexpr (!PLAIN) drain<T>(sctx, hcol, bs);
                     if (sp.hist != cur_hist) {
                         warp_flush_hist<T>(hist, ne, cur_hist);
                         j_since_flush = 0;
@@ -465,10 +602,13 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                 nb = sp.nb;
                 a64 = sp.a64;
                 b64 = sp.b64;
+                sctx.na = na;
+                sctx.a64 = a64;
+                sctx.b64 = b64;
             }
             const uint64_t item_j = (uint64_t)(cons.g.t_end - cons.g.t_first) * J;
             if (j_since_flush + item_j > flush_limit) {
-                if constexpr (!PLAIN) warp_drain_queue<T>(wq, wq_count, a64, b64, cthr, hcol, bs);
+                if constexpr (!PLAIN) drain<T>(sctx, hcol, bs);
                 warp_flush_hist<T>(hist, ne, cur_hist);
                 j_since_flush = 0;
             }
@@ -522,67 +662,37 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         if constexpr (PACKED) {
             const float4* sj = (const float4*)(smem + L.stage + stage * stage_bytes);  // 2 per point
             const unsigned long long nt2 = pack2(neg_fast_t, neg_fast_t);
-            constexpr int U = 4;  // j-points per group
-            // Fast loop with packed FMA: e for i-points (r, r + 1) in one fma.rn.f32x2.
+            // Fast loop with packed FMA: e for i-points (r, r + 1) in one fma.rn.f32x2;
+            // a j with some e >= 0 in the warp takes the inline slow path.
 #pragma unroll 1
-            for (int jj = 0; jj < J; jj += U) {
-                uint32_t skip = 0;
+            for (int jj = 0; jj < J; ++jj) {
+                const ulonglong2 bxy = *reinterpret_cast<const ulonglong2*>(sj + 2 * jj);
+                const unsigned long long bz = *reinterpret_cast<const unsigned long long*>(sj + 2 * jj + 1);
+                float e[R];
+                int acc = -1;
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const ulonglong2 bxy = *reinterpret_cast<const ulonglong2*>(sj + 2 * (jj + u));
-                    const unsigned long long bz = *reinterpret_cast<const unsigned long long*>(sj + 2 * (jj + u) + 1);
-                    int acc = -1;
-#pragma unroll
-                    for (int p = 0; p < R / 2; ++p) {
-                        const unsigned long long e = ffma2(pz[p], bz, ffma2(py[p], bxy.y, ffma2(px[p], bxy.x, nt2)));
-                        acc &= (int)(uint32_t)e & (int)(uint32_t)(e >> 32);
-                    }
-                    skip = __funnelshift_l((uint32_t)acc, skip, 1);  // (skip << 1) | sign(acc)
+                for (int p = 0; p < R / 2; ++p) {
+                    const unsigned long long v = ffma2(pz[p], bz, ffma2(py[p], bxy.y, ffma2(px[p], bxy.x, nt2)));
+                    e[2 * p] = lo_of(v);
+                    e[2 * p + 1] = hi_of(v);
+                    acc &= (int)(uint32_t)v & (int)(uint32_t)(v >> 32);
                 }
-                uint32_t todo = __reduce_or_sync(0xffffffffu, ~skip & ((1u << U) - 1u));
-                if (todo == 0) continue;
-                do {
-                    const int bit = 31 - __clz(todo);
-                    todo &= ~(1u << bit);
-                    const int u = U - 1 - bit;
-                    const float4 b = make_float4(sj[2 * (jj + u)].x, sj[2 * (jj + u)].z, sj[2 * (jj + u) + 1].x, 0.f);
-                    const uint32_t jg = jbase + (uint32_t)(jj + u);
-                    const bool j_ok = !need_idx || jg < nb;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float xr = (r & 1) ? hi_of(px[r / 2]) : lo_of(px[r / 2]);
-                        const float yr = (r & 1) ? hi_of(py[r / 2]) : lo_of(py[r / 2]);
-                        const float zr = (r & 1) ? hi_of(pz[r / 2]) : lo_of(pz[r / 2]);
-                        const float c = fmaf(zr, b.z, fmaf(yr, b.y, __fmul_rn(xr, b.x)));
-                        const uint32_t ig = ibase + 32u * r;
-                        if (c >= band_t && j_ok && (!need_idx || ig < na) && (!masked || jg > ig)) {
-                            int nbv, nav, h32;
-                            int h = classify_f32(c, smem, L, key0, lut_shift, nlut, nbv, nav, h32);
-                            if (h < 0) {
-                                const int pos = atomicAdd((int*)wq_count, 1);
-                                if (pos < kQueuePerWarp) {
-                                    wq[pos] = make_uint4(ig, jg, (uint32_t)nbv | ((uint32_t)nav << 16),
-                                                         (uint32_t)h32);
-                                } else {
-                                    h = band_index(a64, b64, ig, jg, nbv, nav, h32, cthr, bs);
-                                }
-                            }
-                            if (h >= 0) hist_inc(hcol + h * T);
-                        }
-                    }
-                } while (todo);
-                __syncwarp();
-                if (*wq_count >= kQueuePerWarp / 2)
-                    warp_drain_queue<T>(wq, wq_count, a64, b64, cthr, hcol, bs);
+                if (__any_sync(0xffffffffu, acc >= 0)) {
+                    const uint32_t jg = jbase + (uint32_t)jj;
+                    slow_e<T, R>(e, ibase, jg, !need_idx || jg < nb, masked, sctx, hcol, bs);
+                }
             }
         } else if constexpr (MODE == kModeScreen) {
             const float4* sj = (const float4*)(smem + L.stage + stage * stage_bytes);
-            constexpr int U = 4;  // j-points per group
-            // Fast loop: e = FP32 dot minus the fast range limit, for R i-points x
-            // U j-points; one funnel shift per j appends "all R negative" to a bit
-            // mask.  A j with some e >= 0 goes to the warp-uniform slow path.
+            // Fast loop: e = FP32 dot minus the range offset T for R i-points; the AND
+            // of the R sign bits is negative when every pair is certainly overflow.
+            // A j with some e >= 0 in the warp takes the inline slow path.
+            // j-points per group: the group's screen values stay in registers until
+            // the slow path has used them (2 x R at 512 threads, 4 x R below)
+            constexpr int U = T >= 512 ? 2 : 4;
 #pragma unroll 1
             for (int jj = 0; jj < J; jj += U) {
+                float eu[U][R];
                 uint32_t skip = 0;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -590,47 +700,30 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                     int acc = -1;
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        const float e = fmaf(az[r], b.z, fmaf(ay[r], b.y, fmaf(ax[r], b.x, neg_fast_t)));
-                        acc &= __float_as_int(e);
+                        eu[u][r] = fmaf(az[r], b.z, fmaf(ay[r], b.y, fmaf(ax[r], b.x, neg_fast_t)));
+                        acc &= __float_as_int(eu[u][r]);
                     }
                     skip = __funnelshift_l((uint32_t)acc, skip, 1);  // (skip << 1) | sign(acc)
                 }
-                uint32_t todo = __reduce_or_sync(0xffffffffu, ~skip & ((1u << U) - 1u));
-                if (todo == 0) continue;
+                const uint32_t need = ~skip & ((1u << U) - 1u);
+                if (!__any_sync(0xffffffffu, need != 0u)) continue;
+                uint32_t todo = __reduce_or_sync(0xffffffffu, need);
                 do {
-                    // bit U-1-u stands for j = jj + u
+                    // bit U-1-u stands for j = jj + u; u is warp-uniform
                     const int bit = 31 - __clz(todo);
                     todo &= ~(1u << bit);
                     const int u = U - 1 - bit;
-                    const float4 b = sj[jj + u];
-                    const uint32_t jg = jbase + (uint32_t)(jj + u);
-                    // Plain FP32 cosine (error bound 5u against the binary64 dot).
-                    // Padding points are zero vectors (cosine 0): they need an
-                    // index test only when the range reaches cos <= 0.
-                    const bool j_ok = !need_idx || jg < nb;
+                    float e[R];
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        const float c = fmaf(az[r], b.z, fmaf(ay[r], b.y, __fmul_rn(ax[r], b.x)));
-                        const uint32_t ig = ibase + 32u * r;
-                        if (c >= band_t && j_ok && (!need_idx || ig < na) && (!masked || jg > ig)) {
-                            int nbv, nav, h32;
-                            int h = classify_f32(c, smem, L, key0, lut_shift, nlut, nbv, nav, h32);
-                            if (h < 0) {
-                                const int pos = atomicAdd((int*)wq_count, 1);
-                                if (pos < kQueuePerWarp) {
-                                    wq[pos] = make_uint4(ig, jg, (uint32_t)nbv | ((uint32_t)nav << 16),
-                                                         (uint32_t)h32);
-                                } else {
-                                    h = band_index(a64, b64, ig, jg, nbv, nav, h32, cthr, bs);
-                                }
-                            }
-                            if (h >= 0) hist_inc(hcol + h * T);
-                        }
+                        e[r] = eu[0][r];
+#pragma unroll
+                        for (int uu = 1; uu < U; ++uu)
+                            if (u == uu) e[r] = eu[uu][r];
                     }
+                    const uint32_t jg = jbase + (uint32_t)(jj + u);
+                    slow_e<T, R>(e, ibase, jg, !need_idx || jg < nb, masked, sctx, hcol, bs);
                 } while (todo);
-                __syncwarp();
-                if (*wq_count >= kQueuePerWarp / 2)
-                    warp_drain_queue<T>(wq, wq_count, a64, b64, cthr, hcol, bs);
             }
         } else {
             const Point64* sj = (const Point64*)(smem + L.stage + stage * stage_bytes);
@@ -650,7 +743,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                                 const int mid = (lo + hi) >> 1;
                                 if (cthr[mid] >= d) lo = mid + 1; else hi = mid;
                             }
-                            hist_inc(hcol + lo * T);
+                            hist_inc<T>(hcol, lo);
                         }
                     }
                 }
@@ -665,21 +758,21 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             if (old == W - 1) {
                 __threadfence_block();
                 ctl[kCtlRelease + stage] = 0;
-                if (prod.valid && !ctl[kCtlAbort]) {
+                if (prod->valid && !ctl[kCtlAbort]) {
                     fence_proxy_async_smem();
-                    issue(seq + (uint32_t)S, prod);
+                    issue(seq + (uint32_t)S, *prod);
                     atomicAdd((int*)&ctl[kCtlIssued], 1);
                 }
             }
         }
         ++seq;
         cursor_next(wd, cons);
-        cursor_next(wd, prod);
+        if (lane == 0) cursor_next(wd, *prod);
     }
 
     // ---- merge this warp's columns (skipped after an abort: outputs are invalid)
     if (!aborted && cur_hist != nullptr) {
-        if constexpr (!PLAIN) warp_drain_queue<T>(wq, wq_count, a64, b64, cthr, hcol, bs);
+        if constexpr (!PLAIN) drain<T>(sctx, hcol, bs);
         warp_flush_hist<T>(hist, ne, cur_hist);
         if constexpr (!PLAIN) {
             const unsigned long long b = warp_sum(bs.band), m = warp_sum(bs.mismatch);
@@ -879,7 +972,7 @@ static cudaError_t set_smem_t(size_t bytes) {
                                 (int)bytes);
 }
 
-#define TPCF_SHAPES(X) X(128, 8) X(256, 8) X(512, 8) X(256, 16)
+#define TPCF_SHAPES(X) X(128, 8) X(256, 8) X(512, 8) X(256, 16) X(1024, 4) X(512, 4)
 
 cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int mode, int nedges,
                          cudaStream_t stream) {

@@ -96,4 +96,26 @@ __host__ __device__ inline uint64_t item_pairs(const ItemGeom& g, uint32_t na, u
     return total;
 }
 
+// Walk order of one sub-problem's items: position k (0 <= k < n) visits item
+// (k * m) mod n, with m an odd number near 0.618 n coprime with n.  Items that
+// are neighbours in the triangle or rectangle (and cost alike: near-diagonal
+// tiles of sky-sorted catalogs are almost entirely in range) are thereby
+// spread over the persistent blocks instead of landing on a few.
+__host__ __device__ inline uint64_t walk_multiplier(uint64_t n) {
+    if (n <= 2) return 1;
+    uint64_t m = (uint64_t)((double)n * 0.6180339887498949) | 1u;
+    for (;;) {
+        uint64_t a = m, b = n;
+        while (b) { const uint64_t t = a % b; a = b; b = t; }
+        if (a == 1) break;
+        m += 2;
+    }
+    m %= n;
+    return m ? m : 1;
+}
+
+__host__ __device__ inline uint64_t walk_item(uint64_t k, uint64_t n, uint64_t m) {
+    return n ? (k * m) % n : 0;
+}
+
 }  // namespace tpcf

@@ -31,14 +31,14 @@ constexpr int kSlots = 16;
 constexpr size_t kHistStride = TPCF_MAX_EDGES + 1;          // words per histogram in a slot
 constexpr size_t kStatOff = 3 * kHistStride;                 // stats words after 3 histograms
 constexpr size_t kSlotWords = ((kStatOff + kStatWords) + 31) / 32 * 32;
-// Guard band g in cos(theta).  The FP32 cosine of a pair (inputs rounded to
-// FP32, fma(az,bz, fma(ay,by, ax*bx))) is within 5.0001 u of the binary64 dot
-// product (u = 2^-24: 2u from rounding the inputs, 3u from the three
-// roundings), so any g >= 6u keeps the FP32 classification outside the bands
-// exact.  Default: g = 6u.
+// Guard band g in cos(theta).  The kernel's FP32 screen value of a pair,
+// e = fma(az,bz, fma(ay,by, fma(ax,bx, -T))) on FP32-rounded inputs, is within
+// 8.0003u of d - T (u = 2^-24: 2u from rounding the inputs, 3 roundings of
+// terms bounded by |T| + 1), so any g >= 9u keeps the FP32 classification
+// outside the bands exact.  Default: g = 9u.
 constexpr double kUnit = 5.9604644775390625e-08;             // u = 2^-24
-constexpr double kDefaultGuard = 6.0 * kUnit;
-constexpr double kMinGuard = 6.0 * kUnit;
+constexpr double kDefaultGuard = 9.0 * kUnit;
+constexpr double kMinGuard = 9.0 * kUnit;
 constexpr uint32_t kDefaultWaitUs = 2000000;
 
 std::atomic<int> g_alloc_fail_countdown{-1};
@@ -98,7 +98,8 @@ struct tpcf_bins {
     tpcf_ctx* ctx = nullptr;
     int nedges = 0;
     std::vector<double> edges, cos_thr;
-    std::vector<float> lo, hi, c32;
+    std::vector<float> lo, hi, c32;      // cos-space FP32 bounds (reported by the ABI)
+    std::vector<float> elo, ehi, ec;     // screen-value (e-space) bounds used by the kernel
     std::vector<uint32_t> lut;
     std::vector<int> verified;
     BinsDev host;                  // device pointers, host copy
@@ -296,30 +297,56 @@ void derive_all(const double* edges, int ne, double g, std::vector<double>& C,
     }
 }
 
-// LUT over the ordered keys of FP32 cosines from T = lo[B] to a little above
-// 1: entry e covers keys [key0 + (e << shift), key0 + ((e + 1) << shift) - 1]
-// and stores P = #{m : v_max < lo_m}, Q = #{m : v_min <= hi_m}.  The last
-// entry also covers everything above and stores P = 0 (always resolved by
-// explicit comparisons).
-void build_lut(const std::vector<float>& lo, const std::vector<float>& hi, std::vector<uint32_t>& lut,
-               int32_t* key0_out, int* shift_out) {
-    const int ne = (int)lo.size();
-    const float T = lo[ne - 1];
-    const int64_t key0 = fkey(T);
-    const int64_t key_hi = (int64_t)fkey(1.0f) + 64;
+// The counting kernel classifies a pair by its screen value
+//   e = fma(az,bz, fma(ay,by, fma(ax,bx, -T))),  T = RD(C_B - 10u),
+// whose distance from d - T (d the binary64 dot) is at most 8.0003u.  With
+// D_k = C_k - T, the e-space bounds elo_k = RD(D_k - g), ehi_k = RU(D_k + g),
+// g >= 9u, decide every edge outside [elo_k, ehi_k]: e < elo_k => d <= C_k,
+// e > ehi_k => d > C_k.  ec_k = RN(D_k) gives the FP32-only statistic.
+void derive_e_space(const std::vector<double>& C, float T, double g, std::vector<float>& elo,
+                    std::vector<float>& ehi, std::vector<float>& ec) {
+    const int ne = (int)C.size();
+    elo.resize(ne); ehi.resize(ne); ec.resize(ne);
+    for (int k = 0; k < ne; ++k) {
+        if (isinf(C[k])) {
+            elo[k] = ehi[k] = ec[k] = INFINITY;
+        } else {
+            const double D = C[k] - (double)T;
+            elo[k] = round_down_f32(D - g);
+            ehi[k] = round_up_f32(D + g);
+            ec[k] = (float)D;
+        }
+    }
+}
+
+// LUT over e >= 0, indexed by the bits of RN(1 + e): idx = (bits(1 + e) -
+// bits(1)) >> shift, at most kLutMax entries.  Entry k covers keys
+// [key0 + (k << shift), key0 + ((k + 1) << shift) - 1]; the e values that round
+// into that range lie within one ulp of (value - 1), so the entry stores
+// P = #{m : e_max < elo_m} and Q = #{m : e_min <= ehi_m} for the widened range.
+// The last entry also covers every larger e and stores P = 0.
+void build_lut(const std::vector<float>& elo, const std::vector<float>& ehi, float T,
+               std::vector<uint32_t>& lut, int32_t* key0_out, int* shift_out) {
+    const int ne = (int)elo.size();
+    const int64_t key0 = fkey(1.0f);
+    const double e_top = (1.0 + 1e-6) - (double)T;  // d <= 1 + 1e-15, plus the error bound
+    const int64_t key_hi = (int64_t)fkey(round_up_f32(1.0 + e_top)) + 64;
     const int64_t span = key_hi - key0 + 1;
     int shift = 0;
     while (((span - 1) >> shift) + 1 > kLutMax) ++shift;
     const int nlut = (int)(((span - 1) >> shift) + 1);
     lut.assign(nlut, 0);
+    auto ulp_above = [](float v) { return (double)nextafterf(v, INFINITY) - (double)v; };
     for (int e = 0; e < nlut; ++e) {
         const int64_t ka = key0 + ((int64_t)e << shift);
         const int64_t kb = std::min(key0 + (((int64_t)e + 1) << shift) - 1, key_hi);
         const float va = ffromkey(ka), vb = ffromkey(kb);
+        const double e_min = ((double)va - 1.0) - ulp_above(va);
+        const double e_max = ((double)vb - 1.0) + ulp_above(vb);
         uint32_t P = 0, Q = 0;
         for (int m = 0; m < ne; ++m) {
-            P += (vb < lo[m]);
-            Q += (va <= hi[m]);
+            P += (e_max < (double)elo[m]);
+            Q += (e_min <= (double)ehi[m]);
         }
         if (e == nlut - 1) P = 0;
         lut[e] = P | (Q << 16);
@@ -371,9 +398,14 @@ extern "C" int tpcf_bins_create(tpcf_ctx* ctx, const double* edges, int nedges, 
     b->nedges = nedges;
     b->edges.assign(edges, edges + nedges);
     derive_all(edges, nedges, ctx->cfg.guard_band, b->cos_thr, b->lo, b->hi, b->c32, b->verified);
+    // screen offset T: the fast test fma(az,bz, fma(ay,by, fma(ax,bx, -T))) has
+    // error <= 8.0003u against d - T (2u input rounding, 3 roundings of terms
+    // bounded by |T| + 1), so a negative value means d < T + 8.0003u <= C_B.
+    const float T = round_down_f32(b->cos_thr[nedges - 1] - 10.0 * kUnit);
+    derive_e_space(b->cos_thr, T, ctx->cfg.guard_band, b->elo, b->ehi, b->ec);
     int32_t key0;
     int shift;
-    build_lut(b->lo, b->hi, b->lut, &key0, &shift);
+    build_lut(b->elo, b->ehi, T, b->lut, &key0, &shift);
     // one device buffer: C (double), lo, hi, c32 (float), lut (uint32)
     const size_t nd = (size_t)nedges * 8, nf = (size_t)nedges * 4, nl = b->lut.size() * 4;
     const size_t off_lo = (nd + 15) / 16 * 16, off_hi = off_lo + (nf + 15) / 16 * 16,
@@ -381,9 +413,9 @@ extern "C" int tpcf_bins_create(tpcf_ctx* ctx, const double* edges, int nedges, 
                  total = off_lut + nl;
     std::vector<unsigned char> host(total, 0);
     memcpy(host.data(), b->cos_thr.data(), nd);
-    memcpy(host.data() + off_lo, b->lo.data(), nf);
-    memcpy(host.data() + off_hi, b->hi.data(), nf);
-    memcpy(host.data() + off_c32, b->c32.data(), nf);
+    memcpy(host.data() + off_lo, b->elo.data(), nf);
+    memcpy(host.data() + off_hi, b->ehi.data(), nf);
+    memcpy(host.data() + off_c32, b->ec.data(), nf);
     memcpy(host.data() + off_lut, b->lut.data(), nl);
     auto cleanup = [&](int code) {
         if (b->dev_buf) cudaFree(b->dev_buf);
@@ -404,12 +436,8 @@ extern "C" int tpcf_bins_create(tpcf_ctx* ctx, const double* edges, int nedges, 
     b->host.nlut = (int)b->lut.size();
     b->host.lut_shift = shift;
     b->host.lut_key0 = key0;
-    b->host.range_t = b->lo[nedges - 1];
-    // The fast skip test evaluates fma(az,bz, fma(ay,by, fma(ax,bx, -T))): its
-    // error against the binary64 dot minus T is at most 8.0003 u (2u input
-    // rounding, 3 roundings of terms up to |T| + 1), so a negative value means
-    // d < T + 8.0003u; T = RD(C_B - 10u) makes that certainly overflow.
-    b->host.fast_t = round_down_f32(b->cos_thr[nedges - 1] - 10.0 * kUnit);
+    b->host.range_t = b->elo[nedges - 1];
+    b->host.fast_t = T;
     b->host.cos_last = b->cos_thr[nedges - 1];
     if (dev_malloc((void**)&b->dev_desc, sizeof(BinsDev)) != cudaSuccess) return cleanup(TPCF_ENOMEM);
     if (cudaMemcpy(b->dev_desc, &b->host, sizeof(BinsDev), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -556,7 +584,7 @@ struct SubSpec {
 
 int kernel_mode(const tpcf_config& cfg) {
     if (cfg.precision == TPCF_PLAIN_FP64) return kModePlainFP64;
-    return (cfg.flags & TPCF_F_SCALAR_FMA) ? kModeScreenScalar : kModeScreenPacked;
+    return (cfg.flags & TPCF_F_PACKED_FMA) ? kModeScreenPacked : kModeScreenScalar;
 }
 
 bool choose_shape(tpcf_ctx* ctx, int mode, int nedges, uint64_t total_pairs, Shape* sh) {
@@ -579,7 +607,7 @@ bool choose_shape(tpcf_ctx* ctx, int mode, int nedges, uint64_t total_pairs, Sha
         const int T = cand[c][0], R = cand[c][1];
         if (!count_shape_supported(T, R)) continue;
         const int I = T * R;
-        int J = cfg.jtile ? cfg.jtile : 512;
+        int J = cfg.jtile ? cfg.jtile : 1024;
         if (J > I) J = I;
         if ((int)kPad % J != 0 || (int)kPad % I != 0 || J % 32 != 0 || I % J != 0) continue;
         // deepest pipeline (4 .. 2 stages, or the override) that fits; shrink the tile if needed
@@ -613,8 +641,8 @@ uint64_t range_pairs(const SubProblem& sp, uint64_t lo, uint64_t hi, uint32_t I,
     uint64_t a = std::max(lo, sp.item_begin), b = std::min(hi, sp.item_begin + sp.n_items);
     uint64_t total = 0;
     for (uint64_t q = a; q < b; ++q) {
-        ItemGeom g = item_geom(q - sp.item_begin, sp.na, sp.nb, sp.n_iblk, sp.n_jchunk,
-                               sp.auto_mode != 0, I, Jc, J);
+        const uint64_t local = walk_item(q - sp.item_begin, sp.n_items, sp.walk_mult);
+        ItemGeom g = item_geom(local, sp.na, sp.nb, sp.n_iblk, sp.n_jchunk, sp.auto_mode != 0, I, Jc, J);
         if (g.t_first < g.t_end) total += item_pairs(g, sp.na, sp.nb, sp.auto_mode != 0, I, Jc);
     }
     return total;
@@ -673,10 +701,13 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         sp.kratio = I / Jc;
         sp.item_begin = items;
         sp.n_items = (p.na == 0 || p.nb == 0) ? 0 : items_of(sp.n_iblk, sp.n_jchunk, p.auto_mode, I, Jc);
+        sp.walk_mult = walk_multiplier(sp.n_items);
         sp.hist = slot.dev + (size_t)s * kHistStride;
         sp.bins = bins->dev_desc;
         items += sp.n_items;
     }
+    if (items > 0xffff0000ull)
+        return ctx->fail(TPCF_EOVERFLOW, "too many work items (%llu) for one launch", (unsigned long long)items);
     wd.sub_dev = nullptr;
     wd.nsub = nsub;
     wd.item_lo = 0;
@@ -858,8 +889,9 @@ extern "C" int64_t tpcf_plan_coverage(uint32_t na, uint32_t nb, int auto_mode, u
         q_hi = items * (shard_index + 1) / shard_count;
     }
     uint64_t total = 0;
+    const uint64_t mult = walk_multiplier(items);
     for (uint64_t q = q_lo; q < q_hi; ++q) {
-        ItemGeom g = item_geom(q, na, nb, n_iblk, n_jchunk, auto_mode != 0, I, Jc, J);
+        ItemGeom g = item_geom(walk_item(q, items, mult), na, nb, n_iblk, n_jchunk, auto_mode != 0, I, Jc, J);
         if (g.t_first >= g.t_end) continue;
         total += item_pairs(g, na, nb, auto_mode != 0, I, Jc);
         if (!counts) continue;

@@ -12,7 +12,7 @@ namespace tpcf {
 constexpr uint32_t kPad = 4096;
 
 // Lookup table from FP32 cosine to the candidate histogram index range.
-constexpr int kLutMax = 4096;
+constexpr int kLutMax = 16384;
 
 // Binary64 point (x, y, z, 0), 32-byte aligned for two 16-byte loads.
 struct __align__(32) Point64 {
@@ -21,18 +21,21 @@ struct __align__(32) Point64 {
 
 // Device-resident description of one bin set (Section 3: angle -> bin).
 // All arrays live in one device allocation owned by tpcf_bins.
+// The FP32 screen value of a pair is e = fma(az,bz, fma(ay,by, fma(ax,bx, -T)))
+// with T = fast_t; the e-space bounds below are the cos-space thresholds
+// shifted by T and widened by the guard band.
 struct BinsDev {
     const double* cos_thr;  // [nedges] C_k, decreasing (C_0 may be +inf)
-    const float* lo;        // [nedges] RD(C_k - g)
-    const float* hi;        // [nedges] RU(C_k + g)
-    const float* cos32;     // [nedges] RN(C_k): FP32-only classification (statistics)
-    const uint32_t* lut;    // [nlut] (P | Q << 16): see kernels.cu
+    const float* lo;        // [nedges] RD(C_k - T - g)   (e-space)
+    const float* hi;        // [nedges] RU(C_k - T + g)   (e-space)
+    const float* cos32;     // [nedges] RN(C_k - T): FP32-only classification (statistics)
+    const uint32_t* lut;    // [nlut] (P | Q << 16), indexed by bits(RN(1 + e)): see runtime.cpp
     int nedges;             // B + 1
     int nlut;
     int lut_shift;
-    int32_t lut_key0;       // ordered key of lo[B] (the range limit T)
-    float range_t;          // lo[B]: a plain FP32 cosine below it is certainly overflow
-    float fast_t;           // RD(C_B - 10u): a range-offset FP32 screen value below 0 is overflow
+    int32_t lut_key0;       // bits(1.0f)
+    float range_t;          // lo[B] in e-space
+    float fast_t;           // T = RD(C_B - 10u): a screen value e < 0 is certainly overflow
     double cos_last;        // C_B (binary64 range limit, plain kernel)
 };
 
@@ -50,8 +53,9 @@ struct SubProblem {
     uint32_t n_jchunk;    // ceil(nb / Jc)
     uint32_t auto_mode;   // 1: A == B, count j > i only
     uint32_t kratio;      // I / Jc (auto mode: first chunk of i-block ib is ib * kratio)
-    uint64_t item_begin;  // global index of this sub-problem's first item
+    uint64_t item_begin;  // global walk position of this sub-problem's first item
     uint64_t n_items;
+    uint64_t walk_mult;   // position item_begin + k visits local item (k * walk_mult) mod n_items
     unsigned long long* hist;   // B + 2 accumulators (device)
     const BinsDev* bins;        // device pointer to this sub-problem's bins
 };
@@ -69,7 +73,7 @@ struct WorkDesc {
     SubProblem sub[kMaxInlineSub];   // used when sub_dev == nullptr
     const SubProblem* sub_dev;       // device array of nsub sub-problems (batched launches)
     int nsub;
-    uint64_t item_lo, item_hi;       // item range of this launch (shards, serving quanta)
+    uint64_t item_lo, item_hi;       // walk positions of this launch (shards, serving quanta)
     unsigned long long* stats;       // kStatWords words
     uint32_t I, J, Jc;               // i-block, j-tile, j-chunk sizes (points)
     uint32_t stages;                 // shared-memory pipeline depth S (2..16)

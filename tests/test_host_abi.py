@@ -72,7 +72,7 @@ def test_thresholds_define_the_oracle_predicate(tpcf, edges):
         if up <= 1.0:
             assert math.acos(up) < t
     assert np.all(np.diff(c) < 0)
-    g = 6.0 * 2.0 ** -24
+    g = 9.0 * 2.0 ** -24
     fin = np.isfinite(c)
     assert np.all(lo[fin].astype(np.float64) <= c[fin] - g)
     assert np.all(hi[fin].astype(np.float64) >= c[fin] + g)
