@@ -27,6 +27,15 @@
 
 namespace tpcf {
 
+// Dynamic shared memory of the counting kernel.  Helpers address it through
+// 32-bit byte offsets (one register each instead of a 64-bit pointer).
+extern __shared__ __align__(128) unsigned char dyn_smem[];
+
+template <class Tp>
+__device__ __forceinline__ Tp* sptr(uint32_t off) {
+    return reinterpret_cast<Tp*>(dyn_smem + off);
+}
+
 // ============================================================== PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -315,7 +324,8 @@ struct BandStats {
 // mismatch statistic.
 __device__ __forceinline__ int band_index(const Point64* a64, const Point64* b64, uint32_t ig,
                                           uint32_t jg, int nbv, int nav, int h32,
-                                          const double* cthr, BandStats& bs) {
+                                          uint32_t cthr_o, BandStats& bs) {
+    const double* cthr = sptr<const double>(cthr_o);
     const double d = dot64(ldg_point(a64 + ig), ldg_point(b64 + jg));
     int h = nbv;
     for (int m = nbv; m < nav; ++m) h += (d <= cthr[m]);
@@ -336,8 +346,11 @@ struct Resolved {
     int h, nbv, nav, h32;
 };
 
-__device__ __noinline__ Resolved resolve_f32(float c, int P, int Q, const float* lo, const float* hi,
-                                             const float* c32) {
+__device__ __forceinline__ Resolved resolve_f32(float c, int P, int Q, uint32_t lo_o, uint32_t hi_o,
+                                               uint32_t c32_o) {
+    const float* lo = sptr<const float>(lo_o);
+    const float* hi = sptr<const float>(hi_o);
+    const float* c32 = sptr<const float>(c32_o);
     int nb_ = P, na_ = P;
     for (int m = P; m < Q; ++m) {
         nb_ += (c < lo[m]);
@@ -349,21 +362,39 @@ __device__ __noinline__ Resolved resolve_f32(float c, int P, int Q, const float*
     return Resolved{-1, nb_, na_, h};
 }
 
-// One warp recomputes its queued band pairs in binary64: entry (i, j,
-// nbv | nav << 16, h32).  Each lane adds to its own histogram column; ends
-// with the warp's queue empty.  Not inlined (rare and large); returns the
-// lane's band statistics so that no local object's address escapes.
+// One warp classifies its queued pairs.  Two kinds of entry (i, j, z, w):
+// unsettled pairs with w = their LUT entry (bit 31 set) and z = the screen
+// value's bits, first compared with the edges the entry leaves open; and band
+// pairs with z = nbv | nav << 16, w = h32.  Pairs inside a guard band are
+// recomputed in binary64.  Each lane adds to its own histogram column; ends
+// with the warp's queue empty.  Returns the lane's band statistics so that no
+// local object's address escapes.
 template <int T>
-__device__ __forceinline__ BandStats warp_drain_queue(const uint4* wq, volatile int* wq_count,
-                                                   const Point64* a64, const Point64* b64,
-                                                   const double* cthr, uint32_t* hcol) {
+__device__ __forceinline__ BandStats warp_drain_queue(uint32_t wq_o, uint32_t wqc_o, const Point64* a64,
+                                                      const Point64* b64, uint32_t cthr_o, uint32_t lo_o,
+                                                      uint32_t hi_o, uint32_t c32_o, uint32_t* hcol) {
+    const uint4* wq = sptr<const uint4>(wq_o);
+    volatile int* wq_count = sptr<volatile int>(wqc_o);
     BandStats bs = {0ull, 0ull};
     __syncwarp();
     const int n = min(*wq_count, kQueuePerWarp);
     for (int k = (int)(threadIdx.x & 31); k < n; k += 32) {
         const uint4 q = wq[k];
-        const int h = band_index(a64, b64, q.x, q.y, (int)(q.z & 0xffffu), (int)(q.z >> 16), (int)q.w,
-                                 cthr, bs);
+        int h, nbv, nav, h32;
+        if (q.w >> 31) {
+            const Resolved rs = resolve_f32(__uint_as_float(q.z), (int)(q.w & 0xfffu),
+                                            (int)((q.w >> 12) & 0xfffu), lo_o, hi_o, c32_o);
+            h = rs.h;
+            nbv = rs.nbv;
+            nav = rs.nav;
+            h32 = rs.h32;
+        } else {
+            h = -1;
+            nbv = (int)(q.z & 0xffffu);
+            nav = (int)(q.z >> 16);
+            h32 = (int)q.w;
+        }
+        if (h < 0) h = band_index(a64, b64, q.x, q.y, nbv, nav, h32, cthr_o, bs);
         hist_inc<T>(hcol, h);
     }
     __syncwarp();
@@ -379,41 +410,37 @@ __device__ __forceinline__ BandStats warp_drain_queue(const uint4* wq, volatile 
 // unsettled pairs are compared with the edges left open (resolve_f32); pairs
 // inside a guard band go to the warp's queue for the binary64 recheck.
 struct SlowCtx {
-    const uint32_t* lut;
-    const float* lo;
-    const float* hi;
-    const float* c32;
+    uint32_t lut_o, lo_o, hi_o, c32_o, cthr_o;  // shared-memory byte offsets
+    uint32_t wq_o, wqc_o;                       // this warp's queue and its count
     int32_t key0;
     int shift, nlut;
     bool need_idx;
     uint32_t na;
     const Point64* a64;
     const Point64* b64;
-    const double* cthr;
-    uint4* wq;
-    volatile int* wq_count;
 };
 
 template <int T>
 __device__ __forceinline__ void drain(const SlowCtx& sc, uint32_t* hcol, BandStats& bs) {
-    const BandStats d = warp_drain_queue<T>(sc.wq, sc.wq_count, sc.a64, sc.b64, sc.cthr, hcol);
+    const BandStats d = warp_drain_queue<T>(sc.wq_o, sc.wqc_o, sc.a64, sc.b64, sc.cthr_o, sc.lo_o, sc.hi_o,
+                                            sc.c32_o, hcol);
     bs.band += d.band;
     bs.mismatch += d.mismatch;
 }
 
+// An unsettled pair: queued for the warp's drain when there is room, else
+// classified at once.
 template <int T>
 __device__ __forceinline__ void resolve_pair(float e, uint32_t ent, uint32_t ig, uint32_t jg,
                                              const SlowCtx& sc, uint32_t* hcol, BandStats& bs) {
-    const Resolved rs = resolve_f32(e, (int)(ent & 0xfffu), (int)((ent >> 12) & 0xfffu), sc.lo, sc.hi, sc.c32);
-    int h = rs.h;
-    if (h < 0) {
-        const int pos = atomicAdd((int*)sc.wq_count, 1);
-        if (pos < kQueuePerWarp) {
-            sc.wq[pos] = make_uint4(ig, jg, (uint32_t)rs.nbv | ((uint32_t)rs.nav << 16), (uint32_t)rs.h32);
-            return;
-        }
-        h = band_index(sc.a64, sc.b64, ig, jg, rs.nbv, rs.nav, rs.h32, sc.cthr, bs);
+    const int pos = atomicAdd(sptr<int>(sc.wqc_o), 1);
+    if (pos < kQueuePerWarp) {
+        sptr<uint4>(sc.wq_o)[pos] = make_uint4(ig, jg, __float_as_uint(e), ent);
+        return;
     }
+    const Resolved rs = resolve_f32(e, (int)(ent & 0xfffu), (int)((ent >> 12) & 0xfffu), sc.lo_o, sc.hi_o,
+                                    sc.c32_o);
+    const int h = rs.h >= 0 ? rs.h : band_index(sc.a64, sc.b64, ig, jg, rs.nbv, rs.nav, rs.h32, sc.cthr_o, bs);
     hist_inc<T>(hcol, h);
 }
 
@@ -445,7 +472,7 @@ __device__ __forceinline__ void slow_e(const float (&e)[R], uint32_t ibase, uint
             // LUT index from the bits of RN(1 + e): linear in e on [0, 1)
             int idx = (__float_as_int(__fadd_rn(1.0f, e[r])) - sc.key0) >> sc.shift;
             idx = in ? min(idx, sc.nlut - 1) : 0;
-            ent[g] = sc.lut[idx];
+            ent[g] = sptr<const uint32_t>(sc.lut_o)[idx];
             const bool settled = (int)ent[g] >= 0;
             if (in && settled) {
                 asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hbase + ((ent[g] & 0xffffu) << 2)),
@@ -462,7 +489,7 @@ __device__ __forceinline__ void slow_e(const float (&e)[R], uint32_t ibase, uint
         }
     }
     __syncwarp();
-    if (*sc.wq_count >= kQueuePerWarp / 2) drain<T>(sc, hcol, bs);
+    if (*sptr<volatile int>(sc.wqc_o) >= kQueuePerWarp / 2) drain<T>(sc, hcol, bs);
 }
 
 // ============================================================== the counting kernel
@@ -480,7 +507,7 @@ template <int T, int R, int MODE>
 __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ WorkDesc wd) {
     constexpr bool PLAIN = MODE == kModePlain;
     constexpr bool PACKED = MODE == kModeScreen2;
-    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* smem = dyn_smem;
     constexpr int W = T / 32;
     const int S = (int)wd.stages;
     const int J = (int)wd.J;
@@ -495,8 +522,6 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t* hcol = hist + tid;
     const double* cthr = (const double*)(smem + L.cos_thr);
-    uint4* wq = (uint4*)(smem + L.queue) + warp * kQueuePerWarp;
-    volatile int* wq_count = ctl + kCtlQueue + warp;
 
     Cursor cons;
     cursor_begin(wd, cons);
@@ -520,10 +545,11 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     const bool need_idx = !(bd->fast_t > 0.f);
     __syncthreads();
     SlowCtx sctx;
-    sctx.lut = (const uint32_t*)(smem + L.lut);
-    sctx.lo = (const float*)(smem + L.lo);
-    sctx.hi = (const float*)(smem + L.hi);
-    sctx.c32 = (const float*)(smem + L.cos32);
+    sctx.lut_o = L.lut;
+    sctx.lo_o = L.lo;
+    sctx.hi_o = L.hi;
+    sctx.c32_o = L.cos32;
+    sctx.cthr_o = L.cos_thr;
     sctx.key0 = key0;
     sctx.shift = lut_shift;
     sctx.nlut = nlut;
@@ -531,9 +557,8 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     sctx.na = 0;
     sctx.a64 = nullptr;
     sctx.b64 = nullptr;
-    sctx.cthr = cthr;
-    sctx.wq = wq;
-    sctx.wq_count = wq_count;
+    sctx.wq_o = L.queue + (uint32_t)warp * kQueuePerWarp * 16;
+    sctx.wqc_o = L.ctl + (kCtlQueue + warp) * 4;
 
 
     auto issue = [&](uint32_t seq, const Cursor& pc) {
@@ -972,7 +997,7 @@ static cudaError_t set_smem_t(size_t bytes) {
                                 (int)bytes);
 }
 
-#define TPCF_SHAPES(X) X(128, 8) X(256, 8) X(512, 8) X(256, 16) X(1024, 4) X(512, 4)
+#define TPCF_SHAPES(X) X(128, 8) X(256, 8) X(512, 8) X(256, 16)
 
 cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int mode, int nedges,
                          cudaStream_t stream) {
