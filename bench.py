@@ -279,6 +279,20 @@ def run_gpu(args):
     return 0
 
 
+def run_count_only(args):
+    """One warm-up and one fused DD/DR/RR launch on the octant workload of
+    args.count_only points per catalog (the command the profiles use)."""
+    from paper_1204_6630_gb300 import synth, tpcf
+    w = synth.octant_precision(seed=0, n=args.count_only)
+    with tpcf.Context() as ctx:
+        d, r, b = ctx.catalog(w.data), ctx.catalog(w.rand), ctx.bins(w.edges)
+        for _ in range(2):
+            _, st = ctx.count_all(d, r, b, stats=True)
+        print(json.dumps({"n": args.count_only, "kernel_ms": st["kernel_ms"],
+                          "pairs_per_s": st["pairs"] / st["kernel_ms"] * 1e3, "band_pairs": st["band_pairs"]}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -289,7 +303,11 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=40_000, help="points per catalog for the oracle timing")
     ap.add_argument("--ref-sample", type=int, default=16_000, help="points per catalog per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--count-only", type=int, default=0, metavar="N",
+                    help="profiling helper: one fused counting launch on the N-point octant workload")
     args = ap.parse_args()
+    if args.count_only:
+        return run_count_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

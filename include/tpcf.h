@@ -88,6 +88,8 @@ extern "C" {
 #define TPCF_F_NO_SORT 0x1u          /* keep catalog order (no spatial sort on the device) */
 #define TPCF_F_DYNAMIC_SCHED 0x2u    /* persistent blocks take work from an atomic counter */
 #define TPCF_F_PACKED_FMA 0x4u       /* FP32 screen with packed FP32x2 FMA (fma.rn.f32x2) instead of scalar FMA */
+#define TPCF_F_AUTOTUNE 0x8u         /* the first counting call of a workload class times every kernel
+                                        shape that fits and the context keeps the fastest */
 #define TPCF_F_TEST_WAIT_TIMEOUT 0x100u /* test hook: the first j-tile copy of each counting
                                            launch is never issued, so its bounded wait expires
                                            and the call returns TPCF_ETIMEOUT */
@@ -207,6 +209,17 @@ int tpcf_count_cross(tpcf_ctx *ctx, const tpcf_catalog *d, const tpcf_catalog *r
 int tpcf_count_all(tpcf_ctx *ctx, const tpcf_catalog *d, const tpcf_catalog *r,
                    const tpcf_bins *bins, void *stream, uint64_t *dd, uint64_t *dr, uint64_t *rr,
                    int where, tpcf_stats *st);
+
+/* Jackknife patches: per-patch DD, DR and RR of two segmented catalogs with
+ * the same number P of segments (tpcf_catalog_create_segmented), all 3 P
+ * histograms in one persistent launch.  For patch p: DD_p = auto count of the
+ * data points of segment p, DR_p = cross count of data segment p with random
+ * segment p, RR_p = auto count of random segment p.  hists: P * 3 * (B + 2)
+ * uint64, histogram (p, k) at offset (3 p + k) (B + 2) with k = 0 DD, 1 DR,
+ * 2 RR; host or device as `where` (see above). */
+int tpcf_count_patches(tpcf_ctx *ctx, const tpcf_catalog *d, const tpcf_catalog *r,
+                       const tpcf_bins *bins, void *stream, uint64_t *hists, int where,
+                       tpcf_stats *st);
 
 /* ------------------------------------------------------------------ estimator
  * Landy-Szalay w(theta) (Eq. 1) for nbins bins.  dd, dr, rr: the per-bin

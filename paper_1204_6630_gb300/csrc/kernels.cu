@@ -541,8 +541,9 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     const double cos_last = bd->cos_last;
     const int32_t key0 = bd->lut_key0;
     const int lut_shift = bd->lut_shift, nlut = bd->nlut;
-    // zero-vector padding has screen value e = -T: it can look in range only when T <= 0
-    const bool need_idx = !(bd->fast_t > 0.f);
+    // zero-vector padding has screen value e = -T: it can look in range only when
+    // T <= 0; sub-ranges of segmented catalogs are followed by real points
+    const bool need_idx = wd.force_idx || !(bd->fast_t > 0.f);
     __syncthreads();
     SlowCtx sctx;
     sctx.lut_o = L.lut;
@@ -854,6 +855,43 @@ __global__ void finalize_kernel(unsigned long long* acc, int nedges, unsigned lo
             out[nedges] = total - sum;
         }
     }
+}
+
+// Batched finalize: block b turns accumulator row b (stride acc_stride words)
+// into histogram b of `out` (stride out_stride words): bins copied, overflow =
+// totals[b] - sum.
+__global__ void finalize_batch_kernel(const unsigned long long* acc, int acc_stride, int nedges,
+                                      unsigned long long* out, int out_stride,
+                                      const unsigned long long* totals, unsigned long long* err_word) {
+    __shared__ unsigned long long part[256];
+    const unsigned long long* a = acc + (size_t)blockIdx.x * acc_stride;
+    unsigned long long* o = out + (size_t)blockIdx.x * out_stride;
+    unsigned long long s = 0;
+    for (int h = threadIdx.x; h < nedges; h += blockDim.x) s += a[h];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) part[threadIdx.x] += part[threadIdx.x + k];
+        __syncthreads();
+    }
+    for (int h = threadIdx.x; h < nedges; h += blockDim.x) o[h] = a[h];
+    if (threadIdx.x == 0) {
+        const unsigned long long total = totals[blockIdx.x];
+        if (part[0] > total) {
+            atomicOr(err_word, (unsigned long long)kErrBadHist);
+            o[nedges] = 0;
+        } else {
+            o[nedges] = total - part[0];
+        }
+    }
+}
+
+cudaError_t launch_finalize_batch(const unsigned long long* acc, int acc_stride, int nedges,
+                                  unsigned long long* out, int out_stride, const unsigned long long* totals,
+                                  int count, unsigned long long* err_word, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    finalize_batch_kernel<<<count, 256, 0, stream>>>(acc, acc_stride, nedges, out, out_stride, totals, err_word);
+    return cudaGetLastError();
 }
 
 // ============================================================== catalog preparation

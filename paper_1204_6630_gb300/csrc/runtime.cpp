@@ -14,7 +14,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -69,6 +71,8 @@ struct tpcf_ctx {
     Slot slots[kSlots];
     std::atomic<uint32_t> slot_rr{0};
     std::atomic<uint64_t> launches{0};  // kernels of this library launched through the context
+    std::mutex tune_mu;
+    std::map<std::array<int, 5>, Shape> tuned;  // autotuned shapes by workload class
 
     int fail(int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
 };
@@ -481,6 +485,8 @@ extern "C" int tpcf_catalog_create_segmented(tpcf_ctx* ctx, const double* xyz, u
     c->n = n;
     c->n_pad = (uint32_t)(((n + kPad - 1) / kPad) * kPad);
     if (c->n_pad == 0) c->n_pad = kPad;
+    // a segment's tiles and i-blocks may run up to one block past its last point
+    if (nseg > 0) c->n_pad += kPad;
     if (nseg > 0) c->offsets.assign(offsets, offsets + nseg + 1);
     const bool sort = !(ctx->cfg.flags & TPCF_F_NO_SORT);
     uint32_t n_pow2 = 2048;
@@ -587,48 +593,44 @@ int kernel_mode(const tpcf_config& cfg) {
     return (cfg.flags & TPCF_F_PACKED_FMA) ? kModeScreenPacked : kModeScreenScalar;
 }
 
-bool choose_shape(tpcf_ctx* ctx, int mode, int nedges, uint64_t total_pairs, Shape* sh) {
+// Shape for T threads x R i-points, j-tile J (0: default) and S stages (0:
+// deepest that fits); false when it does not fit shared memory.
+bool shape_for(tpcf_ctx* ctx, int mode, int nedges, int T, int R, int Jreq, int Sreq, Shape* sh) {
+    if (!count_shape_supported(T, R)) return false;
+    const int I = T * R;
+    int J = Jreq ? Jreq : 1024;
+    if (J > I) J = I;
+    if ((int)kPad % J != 0 || (int)kPad % I != 0 || J % 32 != 0 || I % J != 0) return false;
+    int S = Sreq ? Sreq : 4;
+    if (S < 2 || S > 16) return false;
+    size_t smem = count_smem_bytes(mode, T, R, J, S, nedges);
+    while (smem > ctx->smem_optin && ((S > 2 && Sreq == 0) || (J > 256 && Jreq == 0))) {
+        if (S > 2 && Sreq == 0) --S; else { J /= 2; S = Sreq ? Sreq : 4; }
+        smem = count_smem_bytes(mode, T, R, J, S, nedges);
+    }
+    if (smem > ctx->smem_optin) return false;
+    sh->threads = T;
+    sh->ipt = R;
+    sh->jtile = J;
+    sh->stages = S;
+    sh->smem = smem;
+    sh->blocks = ctx->num_sms;  // one persistent block per SM
+    sh->jchunk = I;
+    return true;
+}
+
+// Default shape: 512 x 8 for large problems, smaller i-blocks when the
+// catalogs (or sub-ranges) are small or the per-thread histograms do not fit.
+bool choose_shape(tpcf_ctx* ctx, int mode, int nedges, uint64_t total_pairs, uint64_t max_n, Shape* sh) {
     const tpcf_config& cfg = ctx->cfg;
-    // candidate (T, R): the override, or by problem size, then smaller blocks
-    // when the per-thread histograms do not fit in shared memory
-    int cand[4][2];
-    int nc = 0;
-    if (cfg.threads != 0 && cfg.ipt != 0) {
-        cand[nc][0] = cfg.threads; cand[nc][1] = cfg.ipt; ++nc;
-    } else {
-        const double per_sm = (double)total_pairs / std::max(1, ctx->num_sms);
-        if (per_sm >= 4e7) {
-            cand[nc][0] = 512; cand[nc][1] = 8; ++nc;
-            cand[nc][0] = 256; cand[nc][1] = 8; ++nc;
-        }
-        cand[nc][0] = 128; cand[nc][1] = 8; ++nc;
+    if (cfg.threads != 0 && cfg.ipt != 0)
+        return shape_for(ctx, mode, nedges, cfg.threads, cfg.ipt, cfg.jtile, cfg.stages, sh);
+    const double per_sm = (double)total_pairs / std::max(1, ctx->num_sms);
+    if (per_sm >= 4e7 && max_n >= 8192) {
+        if (shape_for(ctx, mode, nedges, 512, 8, cfg.jtile, cfg.stages, sh)) return true;
+        if (shape_for(ctx, mode, nedges, 256, 8, cfg.jtile, cfg.stages, sh)) return true;
     }
-    for (int c = 0; c < nc; ++c) {
-        const int T = cand[c][0], R = cand[c][1];
-        if (!count_shape_supported(T, R)) continue;
-        const int I = T * R;
-        int J = cfg.jtile ? cfg.jtile : 1024;
-        if (J > I) J = I;
-        if ((int)kPad % J != 0 || (int)kPad % I != 0 || J % 32 != 0 || I % J != 0) continue;
-        // deepest pipeline (4 .. 2 stages, or the override) that fits; shrink the tile if needed
-        int S = cfg.stages ? cfg.stages : 4;
-        if (S < 2 || S > 16) continue;
-        size_t smem = count_smem_bytes(mode, T, R, J, S, nedges);
-        while (smem > ctx->smem_optin && ((S > 2 && cfg.stages == 0) || (J > 256 && cfg.jtile == 0))) {
-            if (S > 2 && cfg.stages == 0) --S; else { J /= 2; S = cfg.stages ? cfg.stages : 4; }
-            smem = count_smem_bytes(mode, T, R, J, S, nedges);
-        }
-        if (smem > ctx->smem_optin) continue;
-        sh->threads = T;
-        sh->ipt = R;
-        sh->jtile = J;
-        sh->stages = S;
-        sh->smem = smem;
-        sh->blocks = ctx->num_sms;  // one persistent block per SM
-        sh->jchunk = I;
-        return true;
-    }
-    return false;
+    return shape_for(ctx, mode, nedges, 128, 8, cfg.jtile, cfg.stages, sh);
 }
 
 uint64_t full_pairs(const SubSpec& s) {
@@ -648,46 +650,19 @@ uint64_t range_pairs(const SubProblem& sp, uint64_t lo, uint64_t hi, uint32_t I,
     return total;
 }
 
-int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* bins,
-               cudaStream_t st, unsigned long long* const* outs, int where, tpcf_stats* stats) {
-    if (where != TPCF_HOST && where != TPCF_DEVICE) return ctx->fail(TPCF_EINVAL, "bad where");
-    if (where == TPCF_DEVICE && stats) return ctx->fail(TPCF_EINVAL, "stats need where = TPCF_HOST");
-    if (!bins || bins->ctx != ctx) return ctx->fail(TPCF_EINVAL, "bins missing or from another context");
-    for (int s = 0; s < nsub; ++s) {
-        if (!outs[s]) return ctx->fail(TPCF_EINVAL, "NULL histogram");
-        if (!specs[s].a || !specs[s].b || specs[s].a->ctx != ctx || specs[s].b->ctx != ctx)
-            return ctx->fail(TPCF_EINVAL, "catalog missing or from another context");
-    }
-    cudaSetDevice(ctx->cfg.device);
-    const int ne = bins->nedges;
-    int prec = kernel_mode(ctx->cfg);
-    uint64_t all_pairs = 0;
-    for (int s = 0; s < nsub; ++s) all_pairs += full_pairs(specs[s]);
-    Shape sh;
-    bool fits = choose_shape(ctx, prec, ne, all_pairs, &sh);
-    if (!fits && prec == kModeScreenPacked) {  // the packed stage layout is twice as large
-        prec = kModeScreenScalar;
-        fits = choose_shape(ctx, prec, ne, all_pairs, &sh);
-    }
-    if (!fits)
-        return ctx->fail(TPCF_EINVAL, "no kernel shape fits (threads=%d ipt=%d jtile=%d)",
-                         ctx->cfg.threads, ctx->cfg.ipt, ctx->cfg.jtile);
-    const uint32_t I = (uint32_t)(sh.threads * sh.ipt), J = (uint32_t)sh.jtile;
-    uint32_t Jc = (uint32_t)sh.jchunk;
-
-    // ---- slot
-    const uint32_t si = ctx->slot_rr.fetch_add(1) % kSlots;
-    tpcf_ctx::Slot& slot = ctx->slots[si];
-    std::lock_guard<std::mutex> slot_lock(slot.mu);
-    CUDA_TRY(ctx, cudaStreamWaitEvent(st, slot.ev, 0));
-    CUDA_TRY(ctx, cudaMemsetAsync(slot.dev, 0, kSlotWords * 8, st));
-
-    WorkDesc wd;
-    memset(&wd, 0, sizeof wd);
+// Fill the kernel's work description for `nsub` sub-problems with shape sh.
+// subs_out receives the sub-problem records (placed inline or uploaded by the
+// caller); acc is the accumulator array (stride acc_stride words per
+// histogram); returns the number of items.
+uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* bins, const Shape& sh,
+                    unsigned long long* acc, size_t acc_stride, std::vector<SubProblem>& subs) {
+    const uint32_t I = (uint32_t)(sh.threads * sh.ipt), Jc = (uint32_t)sh.jchunk;
+    subs.assign(nsub, SubProblem());
     uint64_t items = 0;
     for (int s = 0; s < nsub; ++s) {
         const SubSpec& p = specs[s];
-        SubProblem& sp = wd.sub[s];
+        SubProblem& sp = subs[s];
+        memset(&sp, 0, sizeof sp);
         sp.a32 = p.a->d32 + p.a_off;
         sp.b32 = p.b->d32 + p.b_off;
         sp.b32x2 = p.b->d32x2 + 2ull * p.b_off;
@@ -702,68 +677,222 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         sp.item_begin = items;
         sp.n_items = (p.na == 0 || p.nb == 0) ? 0 : items_of(sp.n_iblk, sp.n_jchunk, p.auto_mode, I, Jc);
         sp.walk_mult = walk_multiplier(sp.n_items);
-        sp.hist = slot.dev + (size_t)s * kHistStride;
+        sp.hist = acc + (size_t)s * acc_stride;
         sp.bins = bins->dev_desc;
         items += sp.n_items;
     }
-    if (items > 0xffff0000ull)
-        return ctx->fail(TPCF_EOVERFLOW, "too many work items (%llu) for one launch", (unsigned long long)items);
-    wd.sub_dev = nullptr;
-    wd.nsub = nsub;
-    wd.item_lo = 0;
-    wd.item_hi = items;
-    if (ctx->cfg.shard_count > 1) {
-        wd.item_lo = items * ctx->cfg.shard_index / ctx->cfg.shard_count;
-        wd.item_hi = items * (ctx->cfg.shard_index + 1) / ctx->cfg.shard_count;
-    }
-    wd.stats = slot.dev + kStatOff;
-    wd.I = I;
-    wd.J = J;
-    wd.Jc = Jc;
-    wd.stages = (uint32_t)sh.stages;
-    wd.flags = ctx->cfg.flags;
-    wd.nedges_max = ne;
-    wd.wait_limit_ns = (uint64_t)ctx->cfg.wait_timeout_us * 1000ull;
+    (void)ctx;
+    return items;
+}
 
+int ilog2_u64(uint64_t v) { int k = 0; while (v > 1) { v >>= 1; ++k; } return k; }
+
+int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* bins,
+               cudaStream_t st, unsigned long long* const* outs, int where, tpcf_stats* stats,
+               bool force_idx = false) {
+    if (where != TPCF_HOST && where != TPCF_DEVICE) return ctx->fail(TPCF_EINVAL, "bad where");
+    if (where == TPCF_DEVICE && stats) return ctx->fail(TPCF_EINVAL, "stats need where = TPCF_HOST");
+    if (!bins || bins->ctx != ctx) return ctx->fail(TPCF_EINVAL, "bins missing or from another context");
+    if (nsub < 1) return ctx->fail(TPCF_EINVAL, "no histogram to count");
+    for (int s = 0; s < nsub; ++s) {
+        if (!outs[s]) return ctx->fail(TPCF_EINVAL, "NULL histogram");
+        if (!specs[s].a || !specs[s].b || specs[s].a->ctx != ctx || specs[s].b->ctx != ctx)
+            return ctx->fail(TPCF_EINVAL, "catalog missing or from another context");
+    }
+    cudaSetDevice(ctx->cfg.device);
+    const int ne = bins->nedges;
+    int mode = kernel_mode(ctx->cfg);
+    uint64_t all_pairs = 0, max_n = 0;
+    for (int s = 0; s < nsub; ++s) {
+        all_pairs += full_pairs(specs[s]);
+        max_n = std::max<uint64_t>(max_n, std::max(specs[s].na, specs[s].nb));
+    }
+    Shape sh;
+    bool fits = choose_shape(ctx, mode, ne, all_pairs, max_n, &sh);
+    if (!fits && mode == kModeScreenPacked) {  // the packed stage layout is twice as large
+        mode = kModeScreenScalar;
+        fits = choose_shape(ctx, mode, ne, all_pairs, max_n, &sh);
+    }
+    if (!fits)
+        return ctx->fail(TPCF_EINVAL, "no kernel shape fits (threads=%d ipt=%d jtile=%d)",
+                         ctx->cfg.threads, ctx->cfg.ipt, ctx->cfg.jtile);
+
+    // ---- accumulators and statistics: a context slot for up to 3 histograms,
+    // otherwise one stream-ordered allocation for this call
+    const bool use_slot = nsub <= 3;
+    tpcf_ctx::Slot* slot = nullptr;
+    std::unique_lock<std::mutex> slot_lock;
+    unsigned long long* acc = nullptr;
+    unsigned long long* stat_w = nullptr;
+    size_t acc_stride = 0;
+    void* call_buf = nullptr;
+    SubProblem* dev_subs = nullptr;
+    unsigned long long* dev_totals = nullptr;
+    const size_t sub_bytes = ((size_t)nsub * sizeof(SubProblem) + 255) / 256 * 256;
+    size_t acc_words = 0;
+    if (use_slot) {
+        slot = &ctx->slots[ctx->slot_rr.fetch_add(1) % kSlots];
+        slot_lock = std::unique_lock<std::mutex>(slot->mu);
+        CUDA_TRY(ctx, cudaStreamWaitEvent(st, slot->ev, 0));
+        acc = slot->dev;
+        acc_stride = kHistStride;
+        stat_w = slot->dev + kStatOff;
+        acc_words = kSlotWords;
+    } else {
+        acc_stride = (size_t)ne + 1;
+        acc_words = (size_t)nsub * acc_stride + kStatWords;
+        const size_t bytes = acc_words * 8 + sub_bytes + (size_t)nsub * 8;
+        if (cudaMallocAsync(&call_buf, bytes, st) != cudaSuccess)
+            return ctx->fail(TPCF_ENOMEM, "accumulator allocation failed (%zu bytes)", bytes);
+        acc = (unsigned long long*)call_buf;
+        stat_w = acc + (size_t)nsub * acc_stride;
+        dev_subs = (SubProblem*)((char*)call_buf + acc_words * 8);
+        dev_totals = (unsigned long long*)((char*)dev_subs + sub_bytes);
+    }
+    auto release = [&](int rc) {
+        if (call_buf) cudaFreeAsync(call_buf, st);
+        if (slot) cudaEventRecord(slot->ev, st);
+        return rc;
+    };
+
+    WorkDesc wd;
+    memset(&wd, 0, sizeof wd);
+    std::vector<SubProblem> subs;
+    auto setup = [&](const Shape& shp) -> int {
+        const uint64_t items = build_work(ctx, specs, nsub, bins, shp, acc, acc_stride, subs);
+        if (items > 0xffff0000ull) return TPCF_EOVERFLOW;
+        if (use_slot) {
+            for (int s2 = 0; s2 < nsub; ++s2) wd.sub[s2] = subs[s2];
+            wd.sub_dev = nullptr;
+        } else {
+            if (cudaMemcpyAsync(dev_subs, subs.data(), (size_t)nsub * sizeof(SubProblem),
+                                cudaMemcpyHostToDevice, st) != cudaSuccess)
+                return TPCF_ECUDA;
+            wd.sub_dev = dev_subs;
+        }
+        wd.nsub = nsub;
+        wd.item_lo = 0;
+        wd.item_hi = items;
+        if (ctx->cfg.shard_count > 1) {
+            wd.item_lo = items * ctx->cfg.shard_index / ctx->cfg.shard_count;
+            wd.item_hi = items * (ctx->cfg.shard_index + 1) / ctx->cfg.shard_count;
+        }
+        wd.stats = stat_w;
+        wd.I = (uint32_t)(shp.threads * shp.ipt);
+        wd.J = (uint32_t)shp.jtile;
+        wd.Jc = (uint32_t)shp.jchunk;
+        wd.stages = (uint32_t)shp.stages;
+        wd.flags = ctx->cfg.flags;
+        wd.force_idx = force_idx ? 1u : 0u;
+        wd.nedges_max = ne;
+        wd.wait_limit_ns = (uint64_t)ctx->cfg.wait_timeout_us * 1000ull;
+        return TPCF_OK;
+    };
+    auto launch = [&](const Shape& shp) -> cudaError_t {
+        if (wd.item_hi <= wd.item_lo) return cudaSuccess;
+        Shape sl = shp;
+        const uint64_t n_launch_items = wd.item_hi - wd.item_lo;
+        if ((uint64_t)sl.blocks > n_launch_items) sl.blocks = (int)n_launch_items;
+        cudaError_t e = count_set_smem_limit(mode, shp.threads, shp.ipt, shp.smem);
+        if (e != cudaSuccess) return e;
+        return launch_count(wd, sl, mode, ne, st);
+    };
+
+    // ---- optional autotuning: time every fitting shape once, keep the fastest
+    if ((ctx->cfg.flags & TPCF_F_AUTOTUNE) && ctx->cfg.threads == 0 && ctx->cfg.jtile == 0) {
+        const std::array<int, 5> key{mode, ne, nsub, ilog2_u64(all_pairs + 1), ilog2_u64(max_n + 1)};
+        std::lock_guard<std::mutex> tl(ctx->tune_mu);
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) {
+            sh = it->second;
+        } else {
+            const int cand_t[3] = {128, 256, 512};
+            const int cand_j[3] = {256, 512, 1024};
+            float best = 1e30f;
+            Shape best_sh = sh;
+            cudaEvent_t a0, a1;
+            cudaEventCreate(&a0);
+            cudaEventCreate(&a1);
+            for (int ti = 0; ti < 3; ++ti) {
+                for (int ji = 0; ji < 3; ++ji) {
+                    Shape c;
+                    if (!shape_for(ctx, mode, ne, cand_t[ti], 8, cand_j[ji], 0, &c)) continue;
+                    if (setup(c) != TPCF_OK) continue;
+                    cudaMemsetAsync(acc, 0, acc_words * 8, st);
+                    cudaEventRecord(a0, st);
+                    if (launch(c) != cudaSuccess) continue;
+                    cudaEventRecord(a1, st);
+                    float ms = 1e30f;
+                    if (cudaEventSynchronize(a1) == cudaSuccess) cudaEventElapsedTime(&ms, a0, a1);
+                    if (ms < best) { best = ms; best_sh = c; }
+                }
+            }
+            cudaEventDestroy(a0);
+            cudaEventDestroy(a1);
+            sh = best_sh;
+            ctx->tuned[key] = sh;
+        }
+    }
+
+    {
+        const int rc = setup(sh);
+        if (rc != TPCF_OK) return release(ctx->fail(rc, "work description failed"));
+    }
+    if (cudaMemsetAsync(acc, 0, acc_words * 8, st) != cudaSuccess)
+        return release(ctx->fail(TPCF_ECUDA, "memset failed"));
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (stats) {
-        CUDA_TRY(ctx, cudaEventCreate(&t0));
-        CUDA_TRY(ctx, cudaEventCreate(&t1));
-        CUDA_TRY(ctx, cudaEventRecord(t0, st));
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        cudaEventRecord(t0, st);
     }
     uint32_t launches = 0;
-    if (wd.item_hi > wd.item_lo) {
-        const uint64_t n_launch_items = wd.item_hi - wd.item_lo;
-        Shape sl = sh;
-        if ((uint64_t)sl.blocks > n_launch_items) sl.blocks = (int)n_launch_items;
-        CUDA_TRY(ctx, count_set_smem_limit(prec, sh.threads, sh.ipt, sh.smem));
-        CUDA_TRY(ctx, launch_count(wd, sl, prec, ne, st));
-        ++launches;
+    {
+        const cudaError_t e = launch(sh);
+        if (e != cudaSuccess) return release(ctx->fail(TPCF_ECUDA, "count launch failed: %s", cudaGetErrorString(e)));
+        if (wd.item_hi > wd.item_lo) ++launches;
     }
-    if (stats) CUDA_TRY(ctx, cudaEventRecord(t1, st));
-    // ---- finalize each histogram
-    for (int s = 0; s < nsub; ++s) {
-        uint64_t total = full_pairs(specs[s]);
-        if (ctx->cfg.shard_count > 1)
-            total = range_pairs(wd.sub[s], wd.item_lo, wd.item_hi, I, Jc, J);
-        unsigned long long* acc = wd.sub[s].hist;
-        unsigned long long* dst = where == TPCF_DEVICE ? outs[s] : acc;
-        CUDA_TRY(ctx, launch_finalize(acc, ne, dst, total, wd.stats + kStatError, st));
+    if (stats) cudaEventRecord(t1, st);
+
+    // ---- finalize: overflow of each histogram = its pair total - sum of the other entries
+    const uint32_t I = wd.I, J = wd.J, Jc = wd.Jc;
+    std::vector<unsigned long long> totals(nsub);
+    for (int s2 = 0; s2 < nsub; ++s2)
+        totals[s2] = ctx->cfg.shard_count > 1 ? range_pairs(subs[s2], wd.item_lo, wd.item_hi, I, Jc, J)
+                                              : full_pairs(specs[s2]);
+    if (use_slot) {
+        for (int s2 = 0; s2 < nsub; ++s2) {
+            unsigned long long* a = acc + (size_t)s2 * acc_stride;
+            unsigned long long* dst = where == TPCF_DEVICE ? outs[s2] : a;
+            if (launch_finalize(a, ne, dst, totals[s2], stat_w + kStatError, st) != cudaSuccess)
+                return release(ctx->fail(TPCF_ECUDA, "finalize launch failed"));
+            ++launches;
+        }
+    } else {
+        if (cudaMemcpyAsync(dev_totals, totals.data(), (size_t)nsub * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return release(ctx->fail(TPCF_ECUDA, "totals upload failed"));
+        // device outputs must be one contiguous array (outs[s] = outs[0] + s * (ne + 1))
+        unsigned long long* dst = where == TPCF_DEVICE ? outs[0] : acc;
+        if (launch_finalize_batch(acc, (int)acc_stride, ne, dst, ne + 1, dev_totals, nsub, stat_w + kStatError, st) !=
+            cudaSuccess)
+            return release(ctx->fail(TPCF_ECUDA, "finalize launch failed"));
         ++launches;
     }
     int rc = TPCF_OK;
     if (where == TPCF_HOST) {
-        std::vector<unsigned long long> h(kSlotWords);
-        CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), slot.dev, kSlotWords * 8, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(ctx, cudaStreamSynchronize(st));
-        for (int s = 0; s < nsub; ++s)
-            memcpy(outs[s], h.data() + (size_t)s * kHistStride, (size_t)(ne + 1) * 8);
-        const unsigned long long errw = h[kStatOff + kStatError];
+        std::vector<unsigned long long> h(acc_words);
+        if (cudaMemcpyAsync(h.data(), acc, acc_words * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return release(ctx->fail(TPCF_ECUDA, "result copy failed"));
+        for (int s2 = 0; s2 < nsub; ++s2)
+            memcpy(outs[s2], h.data() + (size_t)s2 * acc_stride, (size_t)(ne + 1) * 8);
+        const unsigned long long* hs = h.data() + (stat_w - acc);
+        const unsigned long long errw = hs[kStatError];
         if (stats) {
             memset(stats, 0, sizeof *stats);
-            stats->pairs = h[kStatOff + kStatPairs];
-            stats->band_pairs = h[kStatOff + kStatBand];
-            stats->band_mismatch = h[kStatOff + kStatMismatch];
+            stats->pairs = hs[kStatPairs];
+            stats->band_pairs = hs[kStatBand];
+            stats->band_mismatch = hs[kStatMismatch];
             stats->device_error = (uint32_t)errw;
             stats->launches = launches;
             float ms = 0.f;
@@ -776,8 +905,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     ctx->launches.fetch_add(launches);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
-    CUDA_TRY(ctx, cudaEventRecord(slot.ev, st));
-    return rc;
+    return release(rc);
 }
 
 }  // namespace
@@ -811,6 +939,28 @@ extern "C" int tpcf_count_all(tpcf_ctx* ctx, const tpcf_catalog* d, const tpcf_c
     unsigned long long* outs[3] = {(unsigned long long*)rr, (unsigned long long*)dr,
                                    (unsigned long long*)dd};
     return run_counts(ctx, s, 3, bins, (cudaStream_t)stream, outs, where, st);
+}
+
+extern "C" int tpcf_count_patches(tpcf_ctx* ctx, const tpcf_catalog* d, const tpcf_catalog* r,
+                                  const tpcf_bins* bins, void* stream, uint64_t* hists, int where,
+                                  tpcf_stats* st) {
+    if (!ctx || !d || !r || !hists) return ctx ? ctx->fail(TPCF_EINVAL, "NULL argument") : TPCF_EINVAL;
+    if (d->offsets.empty() || r->offsets.empty() || d->offsets.size() != r->offsets.size())
+        return ctx->fail(TPCF_EINVAL, "patches: both catalogs must be segmented with the same count");
+    const int np = (int)d->offsets.size() - 1;
+    if (!bins) return ctx->fail(TPCF_EINVAL, "NULL bins");
+    const size_t hs = (size_t)bins->nedges + 1;
+    std::vector<SubSpec> specs(3 * (size_t)np);
+    std::vector<unsigned long long*> outs(3 * (size_t)np);
+    for (int p = 0; p < np; ++p) {
+        const uint32_t d0 = (uint32_t)d->offsets[p], dn = (uint32_t)(d->offsets[p + 1] - d->offsets[p]);
+        const uint32_t r0 = (uint32_t)r->offsets[p], rn = (uint32_t)(r->offsets[p + 1] - r->offsets[p]);
+        specs[3 * p + 0] = SubSpec{d, d, true, dn, dn, d0, d0};
+        specs[3 * p + 1] = SubSpec{d, r, false, dn, rn, d0, r0};
+        specs[3 * p + 2] = SubSpec{r, r, true, rn, rn, r0, r0};
+        for (int k = 0; k < 3; ++k) outs[3 * p + k] = (unsigned long long*)hists + (3 * (size_t)p + k) * hs;
+    }
+    return run_counts(ctx, specs.data(), 3 * np, bins, (cudaStream_t)stream, outs.data(), where, st, true);
 }
 
 // ====================================================================== estimator

@@ -78,6 +78,7 @@ struct WorkDesc {
     uint32_t I, J, Jc;               // i-block, j-tile, j-chunk sizes (points)
     uint32_t stages;                 // shared-memory pipeline depth S (2..16)
     uint32_t flags;                  // TPCF_F_* subset used on the device
+    uint32_t force_idx;              // 1: always check indices (sub-ranges of segmented catalogs)
     int nedges_max;                  // largest B + 1 over the sub-problems (shared-memory sizing)
     uint64_t wait_limit_ns;          // bounded waits
 };
@@ -104,6 +105,9 @@ cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int mode, int nedg
 cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long long* out,
                             unsigned long long total, unsigned long long* err_word,
                             cudaStream_t stream);
+cudaError_t launch_finalize_batch(const unsigned long long* acc, int acc_stride, int nedges,
+                                  unsigned long long* out, int out_stride, const unsigned long long* totals,
+                                  int count, unsigned long long* err_word, cudaStream_t stream);
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
                            int sort, Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
                            unsigned long long* key_scratch, uint32_t* val_scratch,

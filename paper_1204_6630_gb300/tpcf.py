@@ -32,6 +32,7 @@ TPCF_LS_EXACT, TPCF_LS_PAPER = 0, 1
 TPCF_F_NO_SORT = 0x1
 TPCF_F_DYNAMIC_SCHED = 0x2
 TPCF_F_PACKED_FMA = 0x4
+TPCF_F_AUTOTUNE = 0x8
 TPCF_F_TEST_WAIT_TIMEOUT = 0x100
 TPCF_MAX_EDGES = 321
 
@@ -93,6 +94,8 @@ _SIGS = {
                                         ctypes.POINTER(tpcf_stats)]),
     "tpcf_count_all": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
                                       ctypes.POINTER(tpcf_stats)]),
+    "tpcf_count_patches": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                          ctypes.POINTER(tpcf_stats)]),
     "tpcf_estimate": (ctypes.c_int, [_u64p, _u64p, _u64p, ctypes.c_int, _u64, _u64, ctypes.c_int, _dp]),
     "tpcf_correlate": (ctypes.c_int, [_vp, _vp, _u64, _vp, _u64, _dp, ctypes.c_int, ctypes.c_int, _vp,
                                       _u64p, _u64p, _u64p, _dp, ctypes.POINTER(tpcf_stats)]),
@@ -317,6 +320,23 @@ def tpcf_count_all(ctx: int, d: int, r: int, bins: int, nedges: int, stream=None
     return (tuple(outs), st.as_dict()) if st is not None else tuple(outs)
 
 
+def tpcf_count_patches(ctx: int, d: int, r: int, bins: int, nedges: int, npatch: int, stream=None,
+                       out=None, device_out: bool = False, stats: bool = False):
+    """Per-patch (DD, DR, RR) of segmented catalogs: array (npatch, 3, nedges + 1)."""
+    if out is None:
+        if device_out:
+            import torch
+            out = torch.empty((npatch, 3, nedges + 1), dtype=torch.int64, device="cuda")
+        else:
+            out = np.empty((npatch, 3, nedges + 1), dtype=np.uint64)
+    where, (p,) = _hist_args([out])
+    st = tpcf_stats() if (stats and where == TPCF_HOST) else None
+    rc = load().tpcf_count_patches(ctx, d, r, bins, _stream_ptr(stream), p, where,
+                                   ctypes.byref(st) if st is not None else None)
+    _check(rc, "tpcf_count_patches", ctx)
+    return (out, st.as_dict()) if st is not None else out
+
+
 def tpcf_estimate(dd, dr, rr, nd: int, nr: int, estimator: int = TPCF_LS_EXACT) -> np.ndarray:
     """w(theta) from per-bin counts (no underflow/overflow entries)."""
     a = [np.ascontiguousarray(x, dtype=np.uint64) for x in (dd, dr, rr)]
@@ -398,7 +418,7 @@ class Context:
 
     def catalog(self, xyz, stream=None, offsets=None) -> "Catalog":
         h = tpcf_catalog_create(self.handle, xyz, stream, offsets)
-        c = Catalog(self, h, tpcf_catalog_size(h))
+        c = Catalog(self, h, tpcf_catalog_size(h), 0 if offsets is None else len(offsets) - 1)
         self._owned.append(("cat", h))
         return c
 
@@ -419,6 +439,11 @@ class Context:
                   stats=False):
         return tpcf_count_all(self.handle, d.handle, r.handle, bins.handle, bins.nedges, stream, outs,
                               device_out, stats)
+
+    def count_patches(self, d: "Catalog", r: "Catalog", bins: "Bins", stream=None, out=None, device_out=False,
+                      stats=False):
+        return tpcf_count_patches(self.handle, d.handle, r.handle, bins.handle, bins.nedges, d.npatch, stream, out,
+                                  device_out, stats)
 
     def correlate(self, d_xyz, r_xyz, edges_rad, estimator=TPCF_LS_EXACT, stream=None, stats=False):
         return tpcf_correlate(self.handle, d_xyz, r_xyz, edges_rad, estimator, stream, stats)
@@ -451,8 +476,8 @@ class Context:
 
 
 class Catalog:
-    def __init__(self, ctx: Context, handle: int, n: int):
-        self.ctx, self.handle, self.n = ctx, handle, n
+    def __init__(self, ctx: Context, handle: int, n: int, npatch: int = 0):
+        self.ctx, self.handle, self.n, self.npatch = ctx, handle, n, npatch
 
 
 class Bins:
