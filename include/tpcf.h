@@ -121,6 +121,7 @@ typedef struct tpcf_config {
     uint32_t shard_count;      /* number of shards (0 or 1 = no split); histograms of all
                                   shards sum to the unsplit result exactly */
     uint32_t wait_timeout_us;  /* limit of every device-side wait; 0 -> 2,000,000 us */
+    int server_workers;        /* job server: jobs in flight at once, one CUDA stream each (0 -> 4) */
 } tpcf_config;
 
 typedef struct tpcf_stats {
@@ -241,6 +242,65 @@ int tpcf_estimate(const uint64_t *dd, const uint64_t *dr, const uint64_t *rr, in
 int tpcf_correlate(tpcf_ctx *ctx, const double *d_xyz, uint64_t nd, const double *r_xyz,
                    uint64_t nr, const double *edges_rad, int nedges, int estimator, void *stream,
                    uint64_t *dd, uint64_t *dr, uint64_t *rr, double *w, tpcf_stats *st);
+
+/* ------------------------------------------------------------------ job server
+ * Asynchronous correlation jobs (the per-request path of a serving loop; the
+ * paper runs one problem at a time and has no counterpart).  A job is what
+ * tpcf_correlate computes: both catalogs from host arrays, the bins, DD, DR
+ * and RR (Section 3) and w(theta) (Eq. 1).
+ *
+ * tpcf_submit copies the job's arrays (the caller may free them on return)
+ * and queues it; *job_id receives an id > 0.  The context's server starts on
+ * the first submit with cfg.server_workers worker threads, each owning a CUDA
+ * stream, so up to that many jobs run on the device at once.  Admission: a job
+ * needs an estimated amount of device memory (both prepared catalogs, the
+ * preparation scratch and the bins); queued jobs start in submission order,
+ * except that a job that does not fit the memory left under
+ * cfg.hbm_budget_bytes lets later jobs that fit go first.  A job that alone
+ * exceeds the budget is refused with TPCF_EBUDGET.  Job buffers are allocated
+ * and freed in stream order (no device-wide synchronization between jobs).
+ * Validation as tpcf_submit returns: TPCF_EINVAL for NULL arrays, bad edges or
+ * estimator, TPCF_EOVERFLOW for catalogs above TPCF_MAX_POINTS; bad points are
+ * found when the job runs and reported by tpcf_poll.
+ *
+ * tpcf_poll waits up to timeout_ms (0 = do not wait, < 0 = no limit) for the
+ * job.  Not finished: TPCF_EAGAIN (the job stays known).  Finished: returns the
+ * job's status (TPCF_OK, an error of the counting path, or TPCF_ECANCELED),
+ * fills *out (may be NULL; the histogram and w pointers inside may be NULL,
+ * else hold B + 2 resp. B entries, written only for TPCF_OK) and forgets the
+ * job, so a second poll returns TPCF_ENOTFOUND.
+ *
+ * tpcf_cancel: a queued job is removed and finishes as TPCF_ECANCELED; a
+ * running job finishes its device work and then reports TPCF_ECANCELED; a
+ * finished job is unaffected.  TPCF_ENOTFOUND for an unknown id.
+ *
+ * tpcf_destroy waits for running jobs and drops queued ones. */
+typedef struct tpcf_job {
+    const double *d_xyz; /* nd x 3 host binary64 unit vectors */
+    uint64_t nd;
+    const double *r_xyz; /* nr x 3 host binary64 unit vectors */
+    uint64_t nr;
+    const double *edges_rad; /* nedges host edges (as in tpcf_bins_create) */
+    int nedges;
+    int estimator; /* TPCF_LS_EXACT or TPCF_LS_PAPER */
+} tpcf_job;
+
+typedef struct tpcf_result {
+    uint64_t *dd, *dr, *rr; /* caller arrays of B + 2 (may be NULL) */
+    double *w;              /* caller array of B (may be NULL); NaN where RR = 0 or n < 2 */
+    int status;             /* the job's status (as returned by tpcf_poll) */
+    int nedges;
+    double submit_ms;  /* submission time, ms since the server started */
+    double queued_ms;  /* submit -> start on a worker */
+    double run_ms;     /* start -> done (upload, preparation, counting, estimator) */
+    double latency_ms; /* submit -> done */
+    double kernel_ms;  /* device time of the counting launch */
+    uint64_t pairs;    /* pairs visited */
+} tpcf_result;
+
+int tpcf_submit(tpcf_ctx *ctx, const tpcf_job *job, uint64_t *job_id);
+int tpcf_poll(tpcf_ctx *ctx, uint64_t job_id, int timeout_ms, tpcf_result *out);
+int tpcf_cancel(tpcf_ctx *ctx, uint64_t job_id);
 
 /* ------------------------------------------------------------------ no-allocation variant
  * tpcf_count_auto_noalloc: the auto-count histogram (DD or RR; same

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libtpcf.so")
-SOURCES = ["kernels.cu", "runtime.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "runtime.cpp", "server.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -21,31 +21,16 @@
 #include <string>
 #include <vector>
 
+#include "handles.h"
 #include "plan.h"
 #include "tpcf.h"
 #include "tpcf_internal.h"
 
 using namespace tpcf;
 
-namespace {
+std::atomic<int> tpcf::g_alloc_fail_countdown{-1};
 
-constexpr int kSlots = 16;
-constexpr size_t kHistStride = TPCF_MAX_EDGES + 1;          // words per histogram in a slot
-constexpr size_t kStatOff = 3 * kHistStride;                 // stats words after 3 histograms
-constexpr size_t kSlotWords = ((kStatOff + kStatWords) + 31) / 32 * 32;
-// Guard band g in cos(theta).  The kernel's FP32 screen value of a pair,
-// e = fma(az,bz, fma(ay,by, fma(ax,bx, -T))) on FP32-rounded inputs, is within
-// 8.0003u of d - T (u = 2^-24: 2u from rounding the inputs, 3 roundings of
-// terms bounded by |T| + 1), so any g >= 9u keeps the FP32 classification
-// outside the bands exact.  Default: g = 9u.
-constexpr double kUnit = 5.9604644775390625e-08;             // u = 2^-24
-constexpr double kDefaultGuard = 9.0 * kUnit;
-constexpr double kMinGuard = 9.0 * kUnit;
-constexpr uint32_t kDefaultWaitUs = 2000000;
-
-std::atomic<int> g_alloc_fail_countdown{-1};
-
-cudaError_t dev_malloc(void** p, size_t bytes) {
+cudaError_t tpcf::dev_malloc(void** p, size_t bytes) {
     int c = g_alloc_fail_countdown.load();
     if (c >= 0) {
         if (c == 0) { *p = nullptr; return cudaErrorMemoryAllocation; }
@@ -54,28 +39,14 @@ cudaError_t dev_malloc(void** p, size_t bytes) {
     return cudaMalloc(p, bytes);
 }
 
-}  // namespace
-
-// ====================================================================== handles
-struct tpcf_ctx {
-    tpcf_config cfg;
-    int num_sms = 0;
-    size_t smem_optin = 0;
-    std::mutex err_mu;
-    std::string last_error;
-    struct Slot {
-        unsigned long long* dev = nullptr;
-        cudaEvent_t ev = nullptr;
-        std::mutex mu;
-    };
-    Slot slots[kSlots];
-    std::atomic<uint32_t> slot_rr{0};
-    std::atomic<uint64_t> launches{0};  // kernels of this library launched through the context
-    std::mutex tune_mu;
-    std::map<std::array<int, 5>, Shape> tuned;  // autotuned shapes by workload class
-
-    int fail(int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
-};
+cudaError_t tpcf::dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+    int c = g_alloc_fail_countdown.load();
+    if (c >= 0) {
+        if (c == 0) { *p = nullptr; return cudaErrorMemoryAllocation; }
+        g_alloc_fail_countdown.fetch_sub(1);
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
 
 int tpcf_ctx::fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -87,37 +58,6 @@ int tpcf_ctx::fail(int code, const char* fmt, ...) {
     last_error = buf;
     return code;
 }
-
-struct tpcf_catalog {
-    tpcf_ctx* ctx = nullptr;
-    uint64_t n = 0;
-    uint32_t n_pad = 0;
-    Point64* d64 = nullptr;
-    float4* d32 = nullptr;
-    float4* d32x2 = nullptr;        // (x,x,y,y),(z,z,0,0) per point for the packed screen
-    std::vector<uint64_t> offsets;  // segments (empty = one segment)
-};
-
-struct tpcf_bins {
-    tpcf_ctx* ctx = nullptr;
-    int nedges = 0;
-    std::vector<double> edges, cos_thr;
-    std::vector<float> lo, hi, c32;      // cos-space FP32 bounds (reported by the ABI)
-    std::vector<float> elo, ehi, ec;     // screen-value (e-space) bounds used by the kernel
-    std::vector<uint32_t> lut;
-    std::vector<int> verified;
-    BinsDev host;                  // device pointers, host copy
-    void* dev_buf = nullptr;       // arrays
-    BinsDev* dev_desc = nullptr;   // device copy of `host`
-};
-
-#define CUDA_TRY(ctx, call)                                                                    \
-    do {                                                                                       \
-        cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess)                                                                 \
-            return (ctx)->fail(e_ == cudaErrorMemoryAllocation ? TPCF_ENOMEM : TPCF_ECUDA,     \
-                               "%s failed: %s", #call, cudaGetErrorString(e_));                \
-    } while (0)
 
 // ====================================================================== misc
 extern "C" const char* tpcf_strerror(int s) {
@@ -168,6 +108,7 @@ extern "C" int tpcf_create(tpcf_ctx** out, const tpcf_config* cfg_in) {
     if (!(cfg.guard_band >= kMinGuard && cfg.guard_band < 0.25)) return TPCF_EINVAL;
     if (cfg.precision != TPCF_SCREEN_RECHECK && cfg.precision != TPCF_PLAIN_FP64) return TPCF_EINVAL;
     if (cfg.shard_count > 1 && cfg.shard_index >= cfg.shard_count) return TPCF_EINVAL;
+    if (cfg.server_workers < 0 || cfg.server_workers > 64) return TPCF_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev)
         return TPCF_ECUDA;
@@ -191,6 +132,7 @@ extern "C" int tpcf_create(tpcf_ctx** out, const tpcf_config* cfg_in) {
 
 extern "C" int tpcf_destroy(tpcf_ctx* ctx) {
     if (!ctx) return TPCF_EINVAL;
+    server_shutdown(ctx);
     cudaSetDevice(ctx->cfg.device);
     for (auto& s : ctx->slots) {
         if (s.ev) cudaEventSynchronize(s.ev);
@@ -390,7 +332,8 @@ extern "C" int tpcf_bins_thresholds(const double* edges, int nedges, double guar
     return TPCF_OK;
 }
 
-extern "C" int tpcf_bins_create(tpcf_ctx* ctx, const double* edges, int nedges, tpcf_bins** out) {
+int tpcf::bins_create_impl(tpcf_ctx* ctx, const double* edges, int nedges, cudaStream_t st,
+                           bool stream_ordered, tpcf_bins** out) {
     if (!ctx || !out) return TPCF_EINVAL;
     *out = nullptr;
     if (!edges_valid(edges, nedges))
@@ -400,6 +343,8 @@ extern "C" int tpcf_bins_create(tpcf_ctx* ctx, const double* edges, int nedges, 
     tpcf_bins* b = new tpcf_bins();
     b->ctx = ctx;
     b->nedges = nedges;
+    b->stream_ordered = stream_ordered;
+    b->free_stream = st;
     b->edges.assign(edges, edges + nedges);
     derive_all(edges, nedges, ctx->cfg.guard_band, b->cos_thr, b->lo, b->hi, b->c32, b->verified);
     // screen offset T: the fast test fma(az,bz, fma(ay,by, fma(ax,bx, -T))) has
@@ -410,26 +355,17 @@ extern "C" int tpcf_bins_create(tpcf_ctx* ctx, const double* edges, int nedges, 
     int32_t key0;
     int shift;
     build_lut(b->elo, b->ehi, T, b->lut, &key0, &shift);
-    // one device buffer: C (double), lo, hi, c32 (float), lut (uint32)
+    // one device buffer: C (double), lo, hi, c32 (float), lut (uint32), then the descriptor
     const size_t nd = (size_t)nedges * 8, nf = (size_t)nedges * 4, nl = b->lut.size() * 4;
     const size_t off_lo = (nd + 15) / 16 * 16, off_hi = off_lo + (nf + 15) / 16 * 16,
                  off_c32 = off_hi + (nf + 15) / 16 * 16, off_lut = off_c32 + (nf + 15) / 16 * 16,
-                 total = off_lut + nl;
-    std::vector<unsigned char> host(total, 0);
-    memcpy(host.data(), b->cos_thr.data(), nd);
-    memcpy(host.data() + off_lo, b->elo.data(), nf);
-    memcpy(host.data() + off_hi, b->ehi.data(), nf);
-    memcpy(host.data() + off_c32, b->ec.data(), nf);
-    memcpy(host.data() + off_lut, b->lut.data(), nl);
+                 off_desc = (off_lut + nl + 255) / 256 * 256, total = off_desc + sizeof(BinsDev);
     auto cleanup = [&](int code) {
-        if (b->dev_buf) cudaFree(b->dev_buf);
-        if (b->dev_desc) cudaFree(b->dev_desc);
-        delete b;
+        bins_destroy_impl(b);
         return ctx->fail(code, "bins: device allocation or copy failed");
     };
-    if (dev_malloc(&b->dev_buf, total) != cudaSuccess) return cleanup(TPCF_ENOMEM);
-    if (cudaMemcpy(b->dev_buf, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
-        return cleanup(TPCF_ECUDA);
+    if ((stream_ordered ? dev_malloc_async(&b->dev_buf, total, st) : dev_malloc(&b->dev_buf, total)) != cudaSuccess)
+        return cleanup(TPCF_ENOMEM);
     unsigned char* base = (unsigned char*)b->dev_buf;
     b->host.cos_thr = (const double*)base;
     b->host.lo = (const float*)(base + off_lo);
@@ -443,27 +379,53 @@ extern "C" int tpcf_bins_create(tpcf_ctx* ctx, const double* edges, int nedges, 
     b->host.range_t = b->elo[nedges - 1];
     b->host.fast_t = T;
     b->host.cos_last = b->cos_thr[nedges - 1];
-    if (dev_malloc((void**)&b->dev_desc, sizeof(BinsDev)) != cudaSuccess) return cleanup(TPCF_ENOMEM);
-    if (cudaMemcpy(b->dev_desc, &b->host, sizeof(BinsDev), cudaMemcpyHostToDevice) != cudaSuccess)
-        return cleanup(TPCF_ECUDA);
+    b->dev_desc = (BinsDev*)(base + off_desc);
+    b->staging.assign(total, 0);
+    unsigned char* hs = b->staging.data();
+    memcpy(hs, b->cos_thr.data(), nd);
+    memcpy(hs + off_lo, b->elo.data(), nf);
+    memcpy(hs + off_hi, b->ehi.data(), nf);
+    memcpy(hs + off_c32, b->ec.data(), nf);
+    memcpy(hs + off_lut, b->lut.data(), nl);
+    memcpy(hs + off_desc, &b->host, sizeof(BinsDev));
+    const cudaError_t e = stream_ordered
+                              ? cudaMemcpyAsync(b->dev_buf, hs, total, cudaMemcpyHostToDevice, st)
+                              : cudaMemcpy(b->dev_buf, hs, total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cleanup(TPCF_ECUDA);
     *out = b;
     return TPCF_OK;
 }
 
-extern "C" int tpcf_bins_destroy(tpcf_bins* b) {
+int tpcf::bins_destroy_impl(tpcf_bins* b) {
     if (!b) return TPCF_EINVAL;
     cudaSetDevice(b->ctx->cfg.device);
-    cudaDeviceSynchronize();
-    if (b->dev_buf) cudaFree(b->dev_buf);
-    if (b->dev_desc) cudaFree(b->dev_desc);
+    if (b->dev_buf) {
+        if (b->stream_ordered) {
+            cudaFreeAsync(b->dev_buf, b->free_stream);
+            cudaStreamSynchronize(b->free_stream);  // the staging image may back a pending copy
+        } else {
+            cudaDeviceSynchronize();
+            cudaFree(b->dev_buf);
+        }
+    }
     delete b;
     return TPCF_OK;
 }
 
+extern "C" int tpcf_bins_create(tpcf_ctx* ctx, const double* edges, int nedges, tpcf_bins** out) {
+    return bins_create_impl(ctx, edges, nedges, nullptr, false, out);
+}
+
+extern "C" int tpcf_bins_destroy(tpcf_bins* b) { return bins_destroy_impl(b); }
+
 // ====================================================================== catalogs
-extern "C" int tpcf_catalog_create_segmented(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where,
-                                             const uint64_t* offsets, int nseg, void* stream_v,
-                                             tpcf_catalog** out) {
+size_t tpcf::catalog_bytes(uint64_t n) {
+    const uint64_t n_pad = ((n + kPad - 1) / kPad + 1) * kPad;
+    return (size_t)n_pad * (sizeof(Point64) + 3 * sizeof(float4));
+}
+
+int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where, const uint64_t* offsets,
+                              int nseg, cudaStream_t st, bool stream_ordered, tpcf_catalog** out) {
     if (!ctx || !out) return TPCF_EINVAL;
     *out = nullptr;
     if (n > TPCF_MAX_POINTS) return ctx->fail(TPCF_EOVERFLOW, "catalog: %llu points > limit",
@@ -479,10 +441,11 @@ extern "C" int tpcf_catalog_create_segmented(tpcf_ctx* ctx, const double* xyz, u
         if (nseg > 65535) return ctx->fail(TPCF_EOVERFLOW, "catalog: too many segments");
     }
     cudaSetDevice(ctx->cfg.device);
-    cudaStream_t st = (cudaStream_t)stream_v;
     tpcf_catalog* c = new tpcf_catalog();
     c->ctx = ctx;
     c->n = n;
+    c->stream_ordered = stream_ordered;
+    c->free_stream = st;
     c->n_pad = (uint32_t)(((n + kPad - 1) / kPad) * kPad);
     if (c->n_pad == 0) c->n_pad = kPad;
     // a segment's tiles and i-blocks may run up to one block past its last point
@@ -508,15 +471,15 @@ extern "C" int tpcf_catalog_create_segmented(tpcf_ctx* ctx, const double* xyz, u
     };
     auto fail_with = [&](int code, const char* what) {
         release();
-        if (c->d64) cudaFree(c->d64);
-        if (c->d32) cudaFree(c->d32);
-        if (c->d32x2) cudaFree(c->d32x2);
-        delete c;
+        catalog_destroy_impl(c);
         return ctx->fail(code, "catalog: %s", what);
     };
-    if (dev_malloc((void**)&c->d64, (size_t)c->n_pad * sizeof(Point64)) != cudaSuccess ||
-        dev_malloc((void**)&c->d32, (size_t)c->n_pad * sizeof(float4)) != cudaSuccess ||
-        dev_malloc((void**)&c->d32x2, (size_t)c->n_pad * 2 * sizeof(float4)) != cudaSuccess)
+    auto alloc = [&](void** p, size_t bytes) {
+        return stream_ordered ? dev_malloc_async(p, bytes, st) : dev_malloc(p, bytes);
+    };
+    if (alloc((void**)&c->d64, (size_t)c->n_pad * sizeof(Point64)) != cudaSuccess ||
+        alloc((void**)&c->d32, (size_t)c->n_pad * sizeof(float4)) != cudaSuccess ||
+        alloc((void**)&c->d32x2, (size_t)c->n_pad * 2 * sizeof(float4)) != cudaSuccess)
         return fail_with(TPCF_ENOMEM, "device allocation failed");
     const double* in = xyz;
     if (n > 0 && where == TPCF_HOST) {
@@ -559,21 +522,34 @@ extern "C" int tpcf_catalog_create_segmented(tpcf_ctx* ctx, const double* xyz, u
     return TPCF_OK;
 }
 
-extern "C" int tpcf_catalog_create(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where,
-                                   void* stream, tpcf_catalog** out) {
-    return tpcf_catalog_create_segmented(ctx, xyz, n, where, nullptr, 0, stream, out);
+extern "C" int tpcf_catalog_create_segmented(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where,
+                                             const uint64_t* offsets, int nseg, void* stream,
+                                             tpcf_catalog** out) {
+    return catalog_create_impl(ctx, xyz, n, where, offsets, nseg, (cudaStream_t)stream, false, out);
 }
 
-extern "C" int tpcf_catalog_destroy(tpcf_catalog* c) {
+extern "C" int tpcf_catalog_create(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where,
+                                   void* stream, tpcf_catalog** out) {
+    return catalog_create_impl(ctx, xyz, n, where, nullptr, 0, (cudaStream_t)stream, false, out);
+}
+
+int tpcf::catalog_destroy_impl(tpcf_catalog* c) {
     if (!c) return TPCF_EINVAL;
     cudaSetDevice(c->ctx->cfg.device);
-    cudaDeviceSynchronize();
-    if (c->d64) cudaFree(c->d64);
-    if (c->d32) cudaFree(c->d32);
-    if (c->d32x2) cudaFree(c->d32x2);
+    void* bufs[3] = {c->d64, c->d32, c->d32x2};
+    if (c->stream_ordered) {
+        for (void* p : bufs)
+            if (p) cudaFreeAsync(p, c->free_stream);
+    } else {
+        cudaDeviceSynchronize();
+        for (void* p : bufs)
+            if (p) cudaFree(p);
+    }
     delete c;
     return TPCF_OK;
 }
+
+extern "C" int tpcf_catalog_destroy(tpcf_catalog* c) { return catalog_destroy_impl(c); }
 
 extern "C" uint64_t tpcf_catalog_size(const tpcf_catalog* c) { return c ? c->n : 0; }
 

@@ -51,7 +51,7 @@ class tpcf_config(ctypes.Structure):
                 ("hbm_budget_bytes", ctypes.c_uint64), ("flags", ctypes.c_uint32),
                 ("threads", ctypes.c_int), ("ipt", ctypes.c_int), ("jtile", ctypes.c_int), ("stages", ctypes.c_int),
                 ("shard_index", ctypes.c_uint32), ("shard_count", ctypes.c_uint32),
-                ("wait_timeout_us", ctypes.c_uint32)]
+                ("wait_timeout_us", ctypes.c_uint32), ("server_workers", ctypes.c_int)]
 
 
 class tpcf_stats(ctypes.Structure):
@@ -61,6 +61,20 @@ class tpcf_stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class tpcf_job(ctypes.Structure):
+    _fields_ = [("d_xyz", ctypes.c_void_p), ("nd", ctypes.c_uint64), ("r_xyz", ctypes.c_void_p),
+                ("nr", ctypes.c_uint64), ("edges_rad", ctypes.c_void_p), ("nedges", ctypes.c_int),
+                ("estimator", ctypes.c_int)]
+
+
+class tpcf_result(ctypes.Structure):
+    _fields_ = [("dd", ctypes.c_void_p), ("dr", ctypes.c_void_p), ("rr", ctypes.c_void_p),
+                ("w", ctypes.c_void_p), ("status", ctypes.c_int), ("nedges", ctypes.c_int),
+                ("submit_ms", ctypes.c_double), ("queued_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double), ("pairs", ctypes.c_uint64)]
 
 
 _lib = None
@@ -104,6 +118,9 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_uint32), _u64p]),
     "tpcf_debug_fail_alloc_after": (None, [ctypes.c_int]),
     "tpcf_count_auto_noalloc": (ctypes.c_int, [_vp, _u64, _dp, ctypes.c_int, _vp, _vp]),
+    "tpcf_submit": (ctypes.c_int, [_vp, ctypes.POINTER(tpcf_job), _u64p]),
+    "tpcf_poll": (ctypes.c_int, [_vp, _u64, ctypes.c_int, ctypes.POINTER(tpcf_result)]),
+    "tpcf_cancel": (ctypes.c_int, [_vp, _u64]),
 }
 
 
@@ -398,6 +415,46 @@ def tpcf_count_auto_noalloc(xyz_dev, edges_rad, out_dev, stream=None) -> None:
     _check(rc, "tpcf_count_auto_noalloc")
 
 
+def tpcf_submit(ctx: int, d_xyz, r_xyz, edges_rad, estimator: int = TPCF_LS_EXACT) -> int:
+    """Queue a correlation job (host arrays, copied by the call); returns its id."""
+    d = np.ascontiguousarray(d_xyz, dtype=np.float64).reshape(-1, 3)
+    r = np.ascontiguousarray(r_xyz, dtype=np.float64).reshape(-1, 3)
+    e = np.ascontiguousarray(edges_rad, dtype=np.float64)
+    job = tpcf_job(d.ctypes.data, len(d), r.ctypes.data, len(r), e.ctypes.data, len(e), estimator)
+    jid = ctypes.c_uint64(0)
+    _check(load().tpcf_submit(ctx, ctypes.byref(job), ctypes.byref(jid)), "tpcf_submit", ctx)
+    return int(jid.value)
+
+
+class JobResult(dict):
+    """Result of a finished job: dd, dr, rr, w and the timings of tpcf_result."""
+
+
+def tpcf_poll(ctx: int, job_id: int, nedges: int, timeout_ms: int = -1, raise_on_error: bool = True):
+    """The job's JobResult, or None while it is not finished (TPCF_EAGAIN).
+
+    A finished job that failed raises TpcfError (or, with raise_on_error=False,
+    comes back with its status and no histograms)."""
+    dd, dr, rr = (np.zeros(nedges + 1, np.uint64) for _ in range(3))
+    w = np.full(max(nedges - 1, 0), np.nan)
+    res = tpcf_result(dd.ctypes.data, dr.ctypes.data, rr.ctypes.data, w.ctypes.data)
+    rc = load().tpcf_poll(ctx, job_id, timeout_ms, ctypes.byref(res))
+    if rc == TPCF_EAGAIN:
+        return None
+    if rc == TPCF_ENOTFOUND or (rc != TPCF_OK and raise_on_error):
+        _check(rc, "tpcf_poll", ctx)
+    out = JobResult(status=rc, submit_ms=res.submit_ms, queued_ms=res.queued_ms, run_ms=res.run_ms,
+                    latency_ms=res.latency_ms,
+                    kernel_ms=res.kernel_ms, pairs=int(res.pairs))
+    if rc == TPCF_OK:
+        out.update(dd=dd, dr=dr, rr=rr, w=w)
+    return out
+
+
+def tpcf_cancel(ctx: int, job_id: int) -> None:
+    _check(load().tpcf_cancel(ctx, job_id), "tpcf_cancel", ctx)
+
+
 def tpcf_debug_fail_alloc_after(n: int) -> None:
     load().tpcf_debug_fail_alloc_after(n)
 
@@ -447,6 +504,15 @@ class Context:
 
     def correlate(self, d_xyz, r_xyz, edges_rad, estimator=TPCF_LS_EXACT, stream=None, stats=False):
         return tpcf_correlate(self.handle, d_xyz, r_xyz, edges_rad, estimator, stream, stats)
+
+    def submit(self, d_xyz, r_xyz, edges_rad, estimator=TPCF_LS_EXACT) -> int:
+        return tpcf_submit(self.handle, d_xyz, r_xyz, edges_rad, estimator)
+
+    def poll(self, job_id: int, nedges: int, timeout_ms: int = -1, raise_on_error: bool = True):
+        return tpcf_poll(self.handle, job_id, nedges, timeout_ms, raise_on_error)
+
+    def cancel(self, job_id: int) -> None:
+        tpcf_cancel(self.handle, job_id)
 
     def free(self, obj) -> None:
         kind = "cat" if isinstance(obj, Catalog) else "bins"

@@ -1,6 +1,7 @@
 """Host-side checks of the C-ABI library (no GPU): it loads, exports every
 symbol ``include/tpcf.h`` declares, and its host logic (thresholds, work
 plan, estimator, argument validation) is right."""
+import ctypes
 import math
 import os
 import re
@@ -154,3 +155,13 @@ def test_estimator_rejects_bad_sizes(tpcf):
         tpcf.tpcf_estimate([1], [1], [1], 1, 5)
     with pytest.raises(tpcf.TpcfError):
         tpcf.tpcf_estimate([1], [1], [1], 5, 5, estimator=7)
+
+
+def test_server_entry_points_reject_null_context():
+    from paper_1204_6630_gb300 import tpcf
+    lib = tpcf.load()
+    job = tpcf.tpcf_job()
+    jid = ctypes.c_uint64(0)
+    assert lib.tpcf_submit(None, ctypes.byref(job), ctypes.byref(jid)) == tpcf.TPCF_EINVAL
+    assert lib.tpcf_poll(None, 1, 0, None) == tpcf.TPCF_EINVAL
+    assert lib.tpcf_cancel(None, 1) == tpcf.TPCF_EINVAL
