@@ -16,6 +16,21 @@ operations per pair (FMUL + 2 FFMA), counted as 6 flops, against the FP32
 peak 152 SMs x 128 lanes x 2 flops x 2.07 GHz.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Other workloads (one JSON line each, not the headline line):
+  --workload jackknife  2,000,000 data + 4,000,000 random octant points in 512
+                        patches of lognormal size (1k-200k), 40 linear bins
+                        0-5 deg: per-patch DD/DR/RR as one captured graph
+                        (autotuned shape) against 1,536 separate launches;
+  --workload serving    a Poisson stream of --jobs jobs (N_D log-uniform in
+                        [1e3, 1e6], N_R = 2 N_D, caps of 5-30 deg, 20-80
+                        linear bins over 0-2 deg) through the job server
+                        under a 120 GB budget, against one-at-a-time calls:
+                        p50/p99 latency and throughput;
+  --workload large      4,000,000 clustered data + 8,000,000 random points on
+                        the full sphere, 80 log bins 0.005-2 deg, with exact
+                        counts checked against the oracle on a 100,000-point
+                        random subsample of each catalog.
 """
 from __future__ import annotations
 
@@ -234,6 +249,19 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(w.data.nbytes + w.rand.nbytes + w.edges.nbytes),
                "d2h_bytes_per_step": int(3 * (nbins + 2) * 8 + 8 * 8)}
 
+    # ---- the all-binary64 kernel on the same resident catalogs: one launch
+    fp64 = None
+    if world == 1 and not args.no_fp64:
+        with tpcf.Context(device=local, precision=tpcf.TPCF_PLAIN_FP64) as c64:
+            cd, cr, b = c64.catalog(dev_d, stream), c64.catalog(dev_r, stream), c64.bins(w.edges)
+            (pdd, pdr, prr), st64 = c64.count_all(cd, cr, b, stream, stats=True)
+        same = all(np.array_equal(a, c) for a, c in zip((pdd, pdr, prr), (dd, dr, rr)))
+        fp64 = {"kernel": "count_kernel, all-binary64 mode (fused DD/DR/RR)",
+                "kernel_ms": st64["kernel_ms"], "pairs_per_s": st64["pairs"] / st64["kernel_ms"] * 1e3,
+                "screen_speedup": st64["kernel_ms"] / statistics.mean(kernel_ms),
+                "histograms_identical": same}
+        assert same, "FP32 screen + recheck and all-binary64 kernels disagree"
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
@@ -267,6 +295,7 @@ def run_gpu(args):
                                     "MEASURED_PEAKS.json)"},
         "band": {"pairs": st["band_pairs"], "fraction": st["band_pairs"] / max(1, st["pairs"]),
                  "fp32_mismatch": st["band_mismatch"]},
+        "fp64_plain": fp64,
         "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
@@ -293,6 +322,216 @@ def run_count_only(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- other workloads
+def _quantiles(xs):
+    a = np.sort(np.asarray(xs, dtype=np.float64))
+    return {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)), "max": float(a[-1])}
+
+
+def run_jackknife(args):
+    """Per-patch DD/DR/RR of 512 patches: one captured graph vs separate launches."""
+    import torch
+    from paper_1204_6630_gb300 import synth, tpcf
+    d, r, doff, roff = synth.jackknife_patches(seed=0)
+    edges = synth.linear_edges(0.0, 5.0, 40)
+    nd_p, nr_p = np.diff(doff), np.diff(roff)
+    pairs = int(sum(n * (n - 1) // 2 + m * (m - 1) // 2 + n * m for n, m in zip(nd_p, nr_p)))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    with tpcf.Context(flags=tpcf.TPCF_F_AUTOTUNE) as ctx:
+        cd = ctx.catalog(torch.from_numpy(d).cuda(), stream, offsets=doff)
+        cr = ctx.catalog(torch.from_numpy(r).cuda(), stream, offsets=roff)
+        b = ctx.bins(edges)
+        t0 = time.perf_counter()
+        g = ctx.graph(tpcf.TPCF_GRAPH_PATCHES, cd, cr, b)  # autotunes, then captures
+        torch.cuda.synchronize()
+        create_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            g.launch(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        graph_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            ev[0].record(stream)
+            g.launch(stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            graph_ms.append(ev[0].elapsed_time(ev[1]))
+        st = g.stats()
+        batched = g.out.cpu().numpy().view(np.uint64).copy()
+
+        # separate launches: one catalog pair per patch (prepared beforehand), 3 calls per patch
+        sub = []
+        for p in range(len(nd_p)):
+            sub.append((ctx.catalog(torch.from_numpy(d[doff[p]:doff[p + 1]]).cuda(), stream),
+                        ctx.catalog(torch.from_numpy(r[roff[p]:roff[p + 1]]).cuda(), stream)))
+        sep_out = torch.empty((len(nd_p), 3, len(edges) + 1), dtype=torch.int64, device="cuda")
+
+        def separate():
+            for p, (cdp, crp) in enumerate(sub):
+                ctx.count_auto(cdp, b, stream, out=sep_out[p, 0])
+                ctx.count_cross(cdp, crp, b, stream, out=sep_out[p, 1])
+                ctx.count_auto(crp, b, stream, out=sep_out[p, 2])
+
+        separate()
+        sep_ms = []
+        for _ in range(max(1, args.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            separate()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            sep_ms.append(ev[0].elapsed_time(ev[1]))
+        same = np.array_equal(sep_out.cpu().numpy().view(np.uint64), batched)
+        assert same and st["pairs"] == pairs
+    gm, sm = statistics.median(graph_ms), statistics.median(sep_ms)
+    print(json.dumps({
+        "mode": "jackknife", "metric": METRIC, "value": pairs / gm * 1e3, "unit": UNIT,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": gm, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "octant jackknife: N_D=2,000,000 (1024 clusters sigma 0.2 deg), N_R=4,000,000, "
+                               "512 patches lognormal 1k-200k, 40 linear bins 0-5 deg, seed 0",
+                   "patches": int(len(nd_p)), "pairs_per_step": pairs,
+                   "patch_nd": {"min": int(nd_p.min()), "median": float(np.median(nd_p)), "max": int(nd_p.max())},
+                   "l2": "256 MB buffer rewritten before each timed launch"},
+        "graph": {"ms": gm, "pairs_per_s": pairs / gm * 1e3, "create_s": create_s,
+                  "launches_per_replay": st["launches"], "band_pairs": st["band_pairs"]},
+        "separate": {"ms": sm, "pairs_per_s": pairs / sm * 1e3, "calls": 3 * int(len(nd_p)),
+                     "launches": 3 * 2 * int(len(nd_p))},
+        "speedup_vs_separate": sm / gm, "histograms_identical": same}))
+    return 0
+
+
+def run_serving(args):
+    """Poisson job stream through the job server vs one-at-a-time calls."""
+    import concurrent.futures as cf
+    import torch
+    from paper_1204_6630_gb300 import synth, tpcf
+    specs = synth.serving_jobs(args.jobs, seed=0)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(os.cpu_count() or 4) as ex:
+        jobs = list(ex.map(synth.materialise_job, specs))
+    gen_s = time.perf_counter() - t0
+    pairs = [w.pairs for w in jobs]
+    total_pairs = sum(pairs)
+    budget = 120 << 30
+
+    # serial: one synchronous call per job, in arrival order
+    with tpcf.Context() as ctx:
+        for w in jobs[:3]:
+            ctx.correlate(w.data, w.rand, w.edges)
+        torch.cuda.synchronize()
+        service = []
+        serial_res = []
+        t0 = time.perf_counter()
+        for w in jobs:
+            t1 = time.perf_counter()
+            serial_res.append(ctx.correlate(w.data, w.rand, w.edges))
+            service.append(time.perf_counter() - t1)
+        serial_s = time.perf_counter() - t0
+    rate = 0.8 * len(jobs) / serial_s   # Poisson arrival rate: 80% of the serial job rate
+    gaps = np.random.default_rng(1).exponential(1.0 / rate, len(jobs))
+    arrivals = np.cumsum(gaps) - gaps[0]
+    # the serial system under the same arrivals (FIFO, measured service times)
+    done, serial_lat = 0.0, []
+    for a, sv in zip(arrivals, service):
+        done = max(done, a) + sv
+        serial_lat.append(done - a)
+
+    def serve(at):
+        with tpcf.Context(hbm_budget_bytes=budget, server_workers=args.workers) as ctx:
+            ctx.poll(ctx.submit(jobs[0].data, jobs[0].rand, jobs[0].edges), len(jobs[0].edges))
+            start = time.perf_counter()
+            ids = []
+            for k, w in enumerate(jobs):
+                wait = start + at[k] - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                ids.append((ctx.submit(w.data, w.rand, w.edges), time.perf_counter() - start))
+            res = [ctx.poll(j, len(w.edges)) for (j, _), w in zip(ids, jobs)]
+            span = max(s + x["latency_ms"] / 1e3 for (_, s), x in zip(ids, res))
+        lat = [x["latency_ms"] / 1e3 + (s - at[k]) for k, ((_, s), x) in enumerate(zip(ids, res))]
+        return res, span, lat
+
+    burst_res, burst_span, burst_lat = serve(np.zeros(len(jobs)))
+    pois_res, pois_span, pois_lat = serve(arrivals)
+    same = all(np.array_equal(x[n], y[i]) for x, y in zip(burst_res, serial_res)
+               for i, n in enumerate(("dd", "dr", "rr"))) and \
+        all(np.array_equal(x[n], y[i]) for x, y in zip(pois_res, serial_res)
+            for i, n in enumerate(("dd", "dr", "rr")))
+    assert same, "served results differ from lone calls"
+    nd = np.array([len(w.data) for w in jobs])
+    print(json.dumps({
+        "mode": "serving", "metric": "jobs/s and pairs/s; p50/p99 job latency", "value": total_pairs / burst_span,
+        "unit": UNIT, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serving: {len(jobs)} jobs, N_D log-uniform [1e3, 1e6], N_R = 2 N_D, caps 5-30 deg, "
+                               "128 clusters sigma 0.5 deg, 20-80 linear bins 0-2 deg, seed 0",
+                   "jobs": len(jobs), "pairs_total": total_pairs, "nd_median": float(np.median(nd)),
+                   "hbm_budget_gb": budget / 2**30, "workers": args.workers, "generation_s": gen_s,
+                   "arrival_rate_hz": rate, "arrivals": "Poisson at 0.8 x the serial job rate"},
+        "serial": {"s": serial_s, "jobs_per_s": len(jobs) / serial_s, "pairs_per_s": total_pairs / serial_s,
+                   "latency_s_at_poisson": _quantiles(serial_lat)},
+        "served_burst": {"s": burst_span, "jobs_per_s": len(jobs) / burst_span,
+                         "pairs_per_s": total_pairs / burst_span, "latency_s": _quantiles(burst_lat)},
+        "served_poisson": {"s": pois_span, "jobs_per_s": len(jobs) / pois_span,
+                           "pairs_per_s": total_pairs / pois_span, "latency_s": _quantiles(pois_lat)},
+        "throughput_vs_serial": serial_s / burst_span, "results_identical_to_lone_calls": same}))
+    return 0
+
+
+def run_large(args):
+    """4M + 8M full-sphere points: timed fused launch, oracle check on a subsample."""
+    import torch
+    import oracle
+    from paper_1204_6630_gb300 import synth, tpcf
+    w = synth.sphere_large(seed=0)
+    nd, nr = len(w.data), len(w.rand)
+    pairs = w.pairs
+    stream = torch.cuda.current_stream()
+    with tpcf.Context() as ctx:
+        cd = ctx.catalog(torch.from_numpy(w.data).cuda(), stream)
+        cr = ctx.catalog(torch.from_numpy(w.rand).cuda(), stream)
+        b = ctx.bins(w.edges)
+        for _ in range(args.warmup):
+            ctx.count_all(cd, cr, b, stream)
+        kms = []
+        with ClockSampler(0) as clocks:
+            for _ in range(args.steps):
+                (dd, dr, rr), st = ctx.count_all(cd, cr, b, stream, stats=True)
+                kms.append(st["kernel_ms"])
+        assert int(dd.sum()) == nd * (nd - 1) // 2 and int(dr.sum()) == nd * nr and int(rr.sum()) == nr * (nr - 1) // 2
+        # subsample parity
+        g = np.random.default_rng(7)
+        ds = w.data[np.sort(g.choice(nd, args.sub, replace=False))]
+        rs = w.rand[np.sort(g.choice(nr, args.sub, replace=False))]
+        sdd, sdr, srr = ctx.count_all(ctx.catalog(ds), ctx.catalog(rs), b)
+    t0 = time.perf_counter()
+    cores = os.cpu_count() or 1
+    odd = oracle.count_auto(ds, w.edges, cores)
+    odr = oracle.count_cross(ds, rs, w.edges, cores)
+    orr = oracle.count_auto(rs, w.edges, cores)
+    oracle_s = time.perf_counter() - t0
+    same = np.array_equal(odd, sdd) and np.array_equal(odr, sdr) and np.array_equal(orr, srr)
+    km = statistics.mean(kms)
+    ach = pairs * FLOPS_PER_PAIR / (km / 1e3) / 1e12
+    print(json.dumps({
+        "mode": "large", "metric": METRIC, "value": pairs / km * 1e3, "unit": UNIT, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": km, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "sphere_large: N_D=4,000,000 (4096 clusters sigma 0.1 deg), N_R=8,000,000 uniform, "
+                               "full sphere, 80 log bins 0.005-2 deg, seed 0", "pairs_per_step": pairs,
+                   "timed": "fused DD/DR/RR counting launch + finalize on resident catalogs (CUDA events)"},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP32_PEAK_TFLOPS},
+        "band": {"pairs": st["band_pairs"], "fraction": st["band_pairs"] / pairs,
+                 "fp32_mismatch": st["band_mismatch"]},
+        "subsample_parity": {"points_per_catalog": args.sub, "identical_to_oracle": same,
+                             "oracle_s": oracle_s, "oracle_threads": cores},
+        "clocks": clocks.summary()}))
+    assert same, "subsample histograms differ from the oracle"
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,6 +542,12 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=40_000, help="points per catalog for the oracle timing")
     ap.add_argument("--ref-sample", type=int, default=16_000, help="points per catalog per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the all-binary64 kernel comparison")
+    ap.add_argument("--workload", default="octant_precision",
+                    choices=["octant_precision", "jackknife", "serving", "large"])
+    ap.add_argument("--jobs", type=int, default=2000, help="serving: number of jobs")
+    ap.add_argument("--workers", type=int, default=4, help="serving: jobs in flight")
+    ap.add_argument("--sub", type=int, default=100_000, help="large: subsample points per catalog")
     ap.add_argument("--count-only", type=int, default=0, metavar="N",
                     help="profiling helper: one fused counting launch on the N-point octant workload")
     args = ap.parse_args()
@@ -310,6 +555,8 @@ def main():
         return run_count_only(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "octant_precision":
+        return {"jackknife": run_jackknife, "serving": run_serving, "large": run_large}[args.workload](args)
     return run_gpu(args)
 
 

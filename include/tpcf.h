@@ -222,6 +222,38 @@ int tpcf_count_patches(tpcf_ctx *ctx, const tpcf_catalog *d, const tpcf_catalog 
                        const tpcf_bins *bins, void *stream, uint64_t *hists, int where,
                        tpcf_stats *st);
 
+/* ------------------------------------------------------------------ captured graphs
+ * A counting call prepared once and replayed: tpcf_graph_create does the host
+ * work of a count (kernel shape, autotuning when TPCF_F_AUTOTUNE is set, work
+ * description, pair totals, uploads) and captures the device sequence
+ * (accumulator clear, the one persistent counting launch, the finalize
+ * launch) into a CUDA graph; tpcf_graph_launch replays it in `stream` with
+ * one cudaGraphLaunch.  The paper has no counterpart; it serves repeated
+ * counts over resident catalogs (jackknife patches, serving).
+ *   kind TPCF_GRAPH_AUTO:    hist of d (r unused), out_dev = B + 2 uint64;
+ *   kind TPCF_GRAPH_CROSS:   d x r, out_dev = B + 2 uint64;
+ *   kind TPCF_GRAPH_ALL:     out_dev = DD | DR | RR, 3 (B + 2) uint64;
+ *   kind TPCF_GRAPH_PATCHES: segmented d and r, out_dev laid out as in
+ *                            tpcf_count_patches, P * 3 * (B + 2) uint64.
+ * out_dev is device memory; each launch overwrites it in stream order.  The
+ * catalogs, bins and out_dev must stay alive until tpcf_graph_destroy.
+ * Launches of one graph are ordered one after another by CUDA whatever their
+ * streams.  tpcf_graph_stats waits for the last launch and returns its
+ * statistics (kernel_ms = device time of the whole graph) and status
+ * (TPCF_ETIMEOUT / TPCF_ECUDA from the device error word); TPCF_ESTATE before
+ * the first launch.  Errors: TPCF_EINVAL (NULL, unknown kind, unsegmented
+ * catalogs for patches), TPCF_ENOMEM, TPCF_ECUDA. */
+#define TPCF_GRAPH_AUTO 0
+#define TPCF_GRAPH_CROSS 1
+#define TPCF_GRAPH_ALL 2
+#define TPCF_GRAPH_PATCHES 3
+typedef struct tpcf_graph tpcf_graph;
+int tpcf_graph_create(tpcf_ctx *ctx, int kind, const tpcf_catalog *d, const tpcf_catalog *r,
+                      const tpcf_bins *bins, uint64_t *out_dev, tpcf_graph **out);
+int tpcf_graph_launch(tpcf_graph *graph, void *stream);
+int tpcf_graph_stats(tpcf_graph *graph, tpcf_stats *st);
+int tpcf_graph_destroy(tpcf_graph *graph);
+
 /* ------------------------------------------------------------------ estimator
  * Landy-Szalay w(theta) (Eq. 1) for nbins bins.  dd, dr, rr: the per-bin
  * counts WITHOUT underflow/overflow (host arrays of nbins); nd, nr >= 2 the

@@ -1029,10 +1029,17 @@ static cudaError_t launch_t(const WorkDesc& wd, const Shape& sh, cudaStream_t st
     return cudaGetLastError();
 }
 
+// The limit is raised to the device's opt-in maximum rather than to `bytes`:
+// the attribute belongs to the kernel, not to a launch, so a smaller value set
+// by one host thread could otherwise undercut a concurrent launch of another.
 template <int T, int R, int MODE>
 static cudaError_t set_smem_t(size_t bytes) {
-    return cudaFuncSetAttribute(count_kernel<T, R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bytes);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > (size_t)optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(count_kernel<T, R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
 #define TPCF_SHAPES(X) X(128, 8) X(256, 8) X(512, 8) X(256, 16)

@@ -663,10 +663,21 @@ uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bi
 
 int ilog2_u64(uint64_t v) { int k = 0; while (v > 1) { v >>= 1; ++k; } return k; }
 
+// What run_counts leaves behind when it captures the counting sequence into a
+// CUDA graph instead of running it.
+struct GraphOut {
+    cudaGraphExec_t exec = nullptr;
+    void* buf = nullptr;                     // accumulators, sub-problems, totals (owned)
+    unsigned long long* stat_w = nullptr;    // kStatWords statistics words inside buf
+    uint32_t launches = 0;                   // kernels per graph launch
+};
+
 int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* bins,
                cudaStream_t st, unsigned long long* const* outs, int where, tpcf_stats* stats,
-               bool force_idx = false) {
+               bool force_idx = false, GraphOut* gout = nullptr) {
     if (where != TPCF_HOST && where != TPCF_DEVICE) return ctx->fail(TPCF_EINVAL, "bad where");
+    const bool capture = gout != nullptr;
+    if (capture && (where != TPCF_DEVICE || stats)) return ctx->fail(TPCF_EINVAL, "graph capture needs device outputs");
     if (where == TPCF_DEVICE && stats) return ctx->fail(TPCF_EINVAL, "stats need where = TPCF_HOST");
     if (!bins || bins->ctx != ctx) return ctx->fail(TPCF_EINVAL, "bins missing or from another context");
     if (nsub < 1) return ctx->fail(TPCF_EINVAL, "no histogram to count");
@@ -694,8 +705,9 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
                          ctx->cfg.threads, ctx->cfg.ipt, ctx->cfg.jtile);
 
     // ---- accumulators and statistics: a context slot for up to 3 histograms,
-    // otherwise one stream-ordered allocation for this call
-    const bool use_slot = nsub <= 3;
+    // otherwise one stream-ordered allocation for this call (a plain allocation
+    // owned by the graph when capturing)
+    const bool use_slot = nsub <= 3 && !capture;
     tpcf_ctx::Slot* slot = nullptr;
     std::unique_lock<std::mutex> slot_lock;
     unsigned long long* acc = nullptr;
@@ -718,7 +730,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         acc_stride = (size_t)ne + 1;
         acc_words = (size_t)nsub * acc_stride + kStatWords;
         const size_t bytes = acc_words * 8 + sub_bytes + (size_t)nsub * 8;
-        if (cudaMallocAsync(&call_buf, bytes, st) != cudaSuccess)
+        if ((capture ? dev_malloc(&call_buf, bytes) : cudaMallocAsync(&call_buf, bytes, st)) != cudaSuccess)
             return ctx->fail(TPCF_ENOMEM, "accumulator allocation failed (%zu bytes)", bytes);
         acc = (unsigned long long*)call_buf;
         stat_w = acc + (size_t)nsub * acc_stride;
@@ -726,7 +738,12 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         dev_totals = (unsigned long long*)((char*)dev_subs + sub_bytes);
     }
     auto release = [&](int rc) {
-        if (call_buf) cudaFreeAsync(call_buf, st);
+        if (call_buf && capture) {
+            cudaStreamSynchronize(st);
+            cudaFree(call_buf);
+        } else if (call_buf) {
+            cudaFreeAsync(call_buf, st);
+        }
         if (slot) cudaEventRecord(slot->ev, st);
         return rc;
     };
@@ -769,8 +786,10 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         Shape sl = shp;
         const uint64_t n_launch_items = wd.item_hi - wd.item_lo;
         if ((uint64_t)sl.blocks > n_launch_items) sl.blocks = (int)n_launch_items;
-        cudaError_t e = count_set_smem_limit(mode, shp.threads, shp.ipt, shp.smem);
-        if (e != cudaSuccess) return e;
+        if (!capture) {  // when capturing, set before the capture begins
+            cudaError_t e = count_set_smem_limit(mode, shp.threads, shp.ipt, shp.smem);
+            if (e != cudaSuccess) return e;
+        }
         return launch_count(wd, sl, mode, ne, st);
     };
 
@@ -795,6 +814,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
                     if (!shape_for(ctx, mode, ne, cand_t[ti], 8, cand_j[ji], 0, &c)) continue;
                     if (setup(c) != TPCF_OK) continue;
                     cudaMemsetAsync(acc, 0, acc_words * 8, st);
+                    if (capture && count_set_smem_limit(mode, c.threads, c.ipt, c.smem) != cudaSuccess) continue;
                     cudaEventRecord(a0, st);
                     if (launch(c) != cudaSuccess) continue;
                     cudaEventRecord(a1, st);
@@ -814,8 +834,30 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         const int rc = setup(sh);
         if (rc != TPCF_OK) return release(ctx->fail(rc, "work description failed"));
     }
+    // ---- per-histogram pair totals (the finalize step derives overflow from them)
+    std::vector<unsigned long long> totals(nsub);
+    for (int s2 = 0; s2 < nsub; ++s2)
+        totals[s2] = ctx->cfg.shard_count > 1 ? range_pairs(subs[s2], wd.item_lo, wd.item_hi, wd.I, wd.Jc, wd.J)
+                                              : full_pairs(specs[s2]);
+    if (!use_slot &&
+        cudaMemcpyAsync(dev_totals, totals.data(), (size_t)nsub * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return release(ctx->fail(TPCF_ECUDA, "totals upload failed"));
+    if (capture) {
+        if (count_set_smem_limit(mode, sh.threads, sh.ipt, sh.smem) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess ||
+            cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return release(ctx->fail(TPCF_ECUDA, "graph capture could not start"));
+    }
+    auto abort_capture = [&](int rc) {
+        if (capture) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(st, &g);
+            if (g) cudaGraphDestroy(g);
+        }
+        return release(rc);
+    };
     if (cudaMemsetAsync(acc, 0, acc_words * 8, st) != cudaSuccess)
-        return release(ctx->fail(TPCF_ECUDA, "memset failed"));
+        return abort_capture(ctx->fail(TPCF_ECUDA, "memset failed"));
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (stats) {
         cudaEventCreate(&t0);
@@ -825,17 +867,13 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     uint32_t launches = 0;
     {
         const cudaError_t e = launch(sh);
-        if (e != cudaSuccess) return release(ctx->fail(TPCF_ECUDA, "count launch failed: %s", cudaGetErrorString(e)));
+        if (e != cudaSuccess)
+            return abort_capture(ctx->fail(TPCF_ECUDA, "count launch failed: %s", cudaGetErrorString(e)));
         if (wd.item_hi > wd.item_lo) ++launches;
     }
     if (stats) cudaEventRecord(t1, st);
 
     // ---- finalize: overflow of each histogram = its pair total - sum of the other entries
-    const uint32_t I = wd.I, J = wd.J, Jc = wd.Jc;
-    std::vector<unsigned long long> totals(nsub);
-    for (int s2 = 0; s2 < nsub; ++s2)
-        totals[s2] = ctx->cfg.shard_count > 1 ? range_pairs(subs[s2], wd.item_lo, wd.item_hi, I, Jc, J)
-                                              : full_pairs(specs[s2]);
     if (use_slot) {
         for (int s2 = 0; s2 < nsub; ++s2) {
             unsigned long long* a = acc + (size_t)s2 * acc_stride;
@@ -845,14 +883,24 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
             ++launches;
         }
     } else {
-        if (cudaMemcpyAsync(dev_totals, totals.data(), (size_t)nsub * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
-            return release(ctx->fail(TPCF_ECUDA, "totals upload failed"));
         // device outputs must be one contiguous array (outs[s] = outs[0] + s * (ne + 1))
         unsigned long long* dst = where == TPCF_DEVICE ? outs[0] : acc;
         if (launch_finalize_batch(acc, (int)acc_stride, ne, dst, ne + 1, dev_totals, nsub, stat_w + kStatError, st) !=
             cudaSuccess)
-            return release(ctx->fail(TPCF_ECUDA, "finalize launch failed"));
+            return abort_capture(ctx->fail(TPCF_ECUDA, "finalize launch failed"));
         ++launches;
+    }
+    if (capture) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamEndCapture(st, &g) != cudaSuccess || !g)
+            return release(ctx->fail(TPCF_ECUDA, "graph capture failed"));
+        const cudaError_t e = cudaGraphInstantiate(&gout->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return release(ctx->fail(TPCF_ECUDA, "graph instantiation failed"));
+        gout->buf = call_buf;
+        gout->stat_w = stat_w;
+        gout->launches = launches;
+        return TPCF_OK;  // the graph owns call_buf
     }
     int rc = TPCF_OK;
     if (where == TPCF_HOST) {
@@ -937,6 +985,126 @@ extern "C" int tpcf_count_patches(tpcf_ctx* ctx, const tpcf_catalog* d, const tp
         for (int k = 0; k < 3; ++k) outs[3 * p + k] = (unsigned long long*)hists + (3 * (size_t)p + k) * hs;
     }
     return run_counts(ctx, specs.data(), 3 * np, bins, (cudaStream_t)stream, outs.data(), where, st, true);
+}
+
+// ====================================================================== captured counting graphs
+struct tpcf_graph {
+    tpcf_ctx* ctx = nullptr;
+    GraphOut g;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaStream_t copy_st = nullptr;
+    bool launched = false;
+};
+
+extern "C" int tpcf_graph_create(tpcf_ctx* ctx, int kind, const tpcf_catalog* d, const tpcf_catalog* r,
+                                 const tpcf_bins* bins, uint64_t* out_dev, tpcf_graph** out) {
+    if (!ctx || !out) return TPCF_EINVAL;
+    *out = nullptr;
+    if (!d || !bins || !out_dev || (kind != TPCF_GRAPH_AUTO && !r))
+        return ctx->fail(TPCF_EINVAL, "graph: NULL argument");
+    const size_t hs = (size_t)bins->nedges + 1;
+    std::vector<SubSpec> specs;
+    bool force_idx = false;
+    switch (kind) {
+        case TPCF_GRAPH_AUTO:
+            specs.push_back(SubSpec{d, d, true, (uint32_t)d->n, (uint32_t)d->n, 0, 0});
+            break;
+        case TPCF_GRAPH_CROSS:
+            specs.push_back(SubSpec{d, r, false, (uint32_t)d->n, (uint32_t)r->n, 0, 0});
+            break;
+        case TPCF_GRAPH_ALL:
+            specs.push_back(SubSpec{d, d, true, (uint32_t)d->n, (uint32_t)d->n, 0, 0});
+            specs.push_back(SubSpec{d, r, false, (uint32_t)d->n, (uint32_t)r->n, 0, 0});
+            specs.push_back(SubSpec{r, r, true, (uint32_t)r->n, (uint32_t)r->n, 0, 0});
+            break;
+        case TPCF_GRAPH_PATCHES: {
+            if (d->offsets.empty() || r->offsets.empty() || d->offsets.size() != r->offsets.size())
+                return ctx->fail(TPCF_EINVAL, "graph: patches need two segmented catalogs with the same count");
+            const int np = (int)d->offsets.size() - 1;
+            for (int p = 0; p < np; ++p) {
+                const uint32_t d0 = (uint32_t)d->offsets[p], dn = (uint32_t)(d->offsets[p + 1] - d->offsets[p]);
+                const uint32_t r0 = (uint32_t)r->offsets[p], rn = (uint32_t)(r->offsets[p + 1] - r->offsets[p]);
+                specs.push_back(SubSpec{d, d, true, dn, dn, d0, d0});
+                specs.push_back(SubSpec{d, r, false, dn, rn, d0, r0});
+                specs.push_back(SubSpec{r, r, true, rn, rn, r0, r0});
+            }
+            force_idx = true;
+            break;
+        }
+        default:
+            return ctx->fail(TPCF_EINVAL, "graph: unknown kind %d", kind);
+    }
+    std::vector<unsigned long long*> outs(specs.size());
+    for (size_t k = 0; k < specs.size(); ++k) outs[k] = (unsigned long long*)out_dev + k * hs;
+    tpcf_graph* gr = new (std::nothrow) tpcf_graph();
+    if (!gr) return ctx->fail(TPCF_ENOMEM, "graph: host allocation failed");
+    gr->ctx = ctx;
+    cudaSetDevice(ctx->cfg.device);
+    if (cudaStreamCreateWithFlags(&gr->copy_st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&gr->t0) != cudaSuccess || cudaEventCreate(&gr->t1) != cudaSuccess) {
+        tpcf_graph_destroy(gr);
+        return ctx->fail(TPCF_ECUDA, "graph: stream or event creation failed");
+    }
+    // captured on the graph's own stream (capture needs a stream other than the legacy default one)
+    const int rc = run_counts(ctx, specs.data(), (int)specs.size(), bins, gr->copy_st, outs.data(), TPCF_DEVICE,
+                              nullptr, force_idx, &gr->g);
+    if (rc != TPCF_OK) {
+        tpcf_graph_destroy(gr);
+        return rc;
+    }
+    *out = gr;
+    return TPCF_OK;
+}
+
+extern "C" int tpcf_graph_launch(tpcf_graph* g, void* stream) {
+    if (!g || !g->g.exec) return TPCF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(g->ctx->cfg.device);
+    if (cudaEventRecord(g->t0, st) != cudaSuccess || cudaGraphLaunch(g->g.exec, st) != cudaSuccess ||
+        cudaEventRecord(g->t1, st) != cudaSuccess)
+        return g->ctx->fail(TPCF_ECUDA, "graph launch failed");
+    g->launched = true;
+    g->ctx->launches.fetch_add(g->g.launches);
+    return TPCF_OK;
+}
+
+extern "C" int tpcf_graph_stats(tpcf_graph* g, tpcf_stats* st) {
+    if (!g || !g->g.exec) return TPCF_EINVAL;
+    if (!g->launched) return g->ctx->fail(TPCF_ESTATE, "graph: not launched yet");
+    tpcf_ctx* ctx = g->ctx;
+    cudaSetDevice(ctx->cfg.device);
+    unsigned long long h[kStatWords];
+    if (cudaStreamWaitEvent(g->copy_st, g->t1, 0) != cudaSuccess ||
+        cudaMemcpyAsync(h, g->g.stat_w, sizeof h, cudaMemcpyDeviceToHost, g->copy_st) != cudaSuccess ||
+        cudaStreamSynchronize(g->copy_st) != cudaSuccess)
+        return ctx->fail(TPCF_ECUDA, "graph: statistics copy failed");
+    if (st) {
+        memset(st, 0, sizeof *st);
+        st->pairs = h[kStatPairs];
+        st->band_pairs = h[kStatBand];
+        st->band_mismatch = h[kStatMismatch];
+        st->device_error = (uint32_t)h[kStatError];
+        st->launches = g->g.launches;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g->t0, g->t1);
+        st->kernel_ms = ms;
+    }
+    if (h[kStatError] & kErrWaitTimeout) return ctx->fail(TPCF_ETIMEOUT, "a bounded device wait timed out");
+    if (h[kStatError]) return ctx->fail(TPCF_ECUDA, "device error word 0x%llx", h[kStatError]);
+    return TPCF_OK;
+}
+
+extern "C" int tpcf_graph_destroy(tpcf_graph* g) {
+    if (!g) return TPCF_EINVAL;
+    if (g->ctx) cudaSetDevice(g->ctx->cfg.device);
+    if (g->launched && g->t1) cudaEventSynchronize(g->t1);
+    if (g->g.exec) cudaGraphExecDestroy(g->g.exec);
+    if (g->g.buf) cudaFree(g->g.buf);
+    if (g->t0) cudaEventDestroy(g->t0);
+    if (g->t1) cudaEventDestroy(g->t1);
+    if (g->copy_st) cudaStreamDestroy(g->copy_st);
+    delete g;
+    return TPCF_OK;
 }
 
 // ====================================================================== estimator

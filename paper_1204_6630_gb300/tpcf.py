@@ -35,6 +35,7 @@ TPCF_F_PACKED_FMA = 0x4
 TPCF_F_AUTOTUNE = 0x8
 TPCF_F_TEST_WAIT_TIMEOUT = 0x100
 TPCF_MAX_EDGES = 321
+TPCF_GRAPH_AUTO, TPCF_GRAPH_CROSS, TPCF_GRAPH_ALL, TPCF_GRAPH_PATCHES = 0, 1, 2, 3
 
 
 class TpcfError(RuntimeError):
@@ -121,6 +122,10 @@ _SIGS = {
     "tpcf_submit": (ctypes.c_int, [_vp, ctypes.POINTER(tpcf_job), _u64p]),
     "tpcf_poll": (ctypes.c_int, [_vp, _u64, ctypes.c_int, ctypes.POINTER(tpcf_result)]),
     "tpcf_cancel": (ctypes.c_int, [_vp, _u64]),
+    "tpcf_graph_create": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "tpcf_graph_launch": (ctypes.c_int, [_vp, _vp]),
+    "tpcf_graph_stats": (ctypes.c_int, [_vp, ctypes.POINTER(tpcf_stats)]),
+    "tpcf_graph_destroy": (ctypes.c_int, [_vp]),
 }
 
 
@@ -455,6 +460,30 @@ def tpcf_cancel(ctx: int, job_id: int) -> None:
     _check(load().tpcf_cancel(ctx, job_id), "tpcf_cancel", ctx)
 
 
+def tpcf_graph_create(ctx: int, kind: int, d: int, r: int | None, bins: int, out_dev) -> int:
+    """Capture a counting call into a CUDA graph writing the CUDA tensor out_dev."""
+    if not (_is_torch(out_dev) and out_dev.is_cuda and out_dev.is_contiguous()):
+        raise ValueError("out_dev must be a contiguous CUDA tensor")
+    h = _vp()
+    _check(load().tpcf_graph_create(ctx, kind, d, r, bins, out_dev.data_ptr(), ctypes.byref(h)),
+           "tpcf_graph_create", ctx)
+    return h.value
+
+
+def tpcf_graph_launch(graph: int, stream=None, ctx: int | None = None) -> None:
+    _check(load().tpcf_graph_launch(graph, _stream_ptr(stream)), "tpcf_graph_launch", ctx)
+
+
+def tpcf_graph_stats(graph: int, ctx: int | None = None) -> dict:
+    st = tpcf_stats()
+    _check(load().tpcf_graph_stats(graph, ctypes.byref(st)), "tpcf_graph_stats", ctx)
+    return st.as_dict()
+
+
+def tpcf_graph_destroy(graph: int) -> None:
+    _check(load().tpcf_graph_destroy(graph), "tpcf_graph_destroy")
+
+
 def tpcf_debug_fail_alloc_after(n: int) -> None:
     load().tpcf_debug_fail_alloc_after(n)
 
@@ -514,16 +543,31 @@ class Context:
     def cancel(self, job_id: int) -> None:
         tpcf_cancel(self.handle, job_id)
 
+    def graph(self, kind: int, d: "Catalog", r: "Catalog | None", bins: "Bins", out_dev=None) -> "Graph":
+        """A captured counting graph (see include/tpcf.h); out_dev is allocated when None."""
+        hs = bins.nedges + 1
+        if out_dev is None:
+            import torch
+            shape = {TPCF_GRAPH_AUTO: (hs,), TPCF_GRAPH_CROSS: (hs,), TPCF_GRAPH_ALL: (3, hs),
+                     TPCF_GRAPH_PATCHES: (d.npatch, 3, hs)}[kind]
+            out_dev = torch.empty(shape, dtype=torch.int64, device="cuda")
+        h = tpcf_graph_create(self.handle, kind, d.handle, r.handle if r is not None else None, bins.handle, out_dev)
+        g = Graph(self, h, out_dev)
+        self._owned.append(("graph", h))
+        return g
+
+    _DESTROY = {"cat": "tpcf_catalog_destroy", "bins": "tpcf_bins_destroy", "graph": "tpcf_graph_destroy"}
+
     def free(self, obj) -> None:
-        kind = "cat" if isinstance(obj, Catalog) else "bins"
+        kind = "cat" if isinstance(obj, Catalog) else ("graph" if isinstance(obj, Graph) else "bins")
         if (kind, obj.handle) in self._owned:
             self._owned.remove((kind, obj.handle))
-            (tpcf_catalog_destroy if kind == "cat" else tpcf_bins_destroy)(obj.handle)
+            globals()[self._DESTROY[kind]](obj.handle)
 
     def close(self) -> None:
         if self.handle:
             for kind, h in reversed(self._owned):
-                (tpcf_catalog_destroy if kind == "cat" else tpcf_bins_destroy)(h)
+                globals()[self._DESTROY[kind]](h)
             self._owned.clear()
             tpcf_destroy(self.handle)
             self.handle = 0
@@ -549,3 +593,14 @@ class Catalog:
 class Bins:
     def __init__(self, ctx: Context, handle: int, nedges: int):
         self.ctx, self.handle, self.nedges = ctx, handle, nedges
+
+
+class Graph:
+    def __init__(self, ctx: Context, handle: int, out):
+        self.ctx, self.handle, self.out = ctx, handle, out
+
+    def launch(self, stream=None) -> None:
+        tpcf_graph_launch(self.handle, stream, self.ctx.handle)
+
+    def stats(self) -> dict:
+        return tpcf_graph_stats(self.handle, self.ctx.handle)

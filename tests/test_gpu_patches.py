@@ -91,3 +91,53 @@ def test_patches_reject_mismatched_segments(T):
         cr = ctx.catalog(r)  # not segmented
         with pytest.raises(T.TpcfError):
             ctx.count_patches(cd, cr, ctx.bins(synth.linear_edges(0.0, 5.0, 10)))
+
+
+@pytest.mark.parametrize("flags", [0, 0x8])
+def test_patch_graph_replays_equal_direct_call(T, flags):
+    import torch
+    rng = np.random.default_rng(9)
+    sizes = [0, 1] + list(rng.integers(200, 9000, 30))
+    d, r, doff, roff = patch_set(sizes, seed=9)
+    edges = synth.linear_edges(0.0, 5.0, 40)
+    with T.Context(flags=flags) as ctx:
+        cd, cr, b = ctx.catalog(d, offsets=doff), ctx.catalog(r, offsets=roff), ctx.bins(edges)
+        want = ctx.count_patches(cd, cr, b)
+        g = ctx.graph(T.TPCF_GRAPH_PATCHES, cd, cr, b)
+        s = torch.cuda.current_stream()
+        for _ in range(3):  # each replay clears and recounts
+            g.launch(s)
+        st = g.stats()
+        np.testing.assert_array_equal(g.out.cpu().numpy().view(np.uint64), want)
+        assert st["device_error"] == 0 and st["launches"] == 2
+        want_pairs = sum(n * (n - 1) // 2 + (2 * n) * (2 * n - 1) // 2 + 2 * n * n for n in sizes)
+        assert st["pairs"] == want_pairs
+
+
+def test_graph_kinds_equal_direct_calls(T):
+    import torch
+    d = synth.clustered(30000, 64, 0.3, synth.Footprint("octant"), 21)
+    r = synth.randoms(45000, synth.Footprint("octant"), 22)
+    edges = synth.log_edges(0.01, 10.0, 64)
+    with T.Context() as ctx:
+        cd, cr, b = ctx.catalog(d), ctx.catalog(r), ctx.bins(edges)
+        dd, dr, rr = ctx.count_all(cd, cr, b)
+        s = torch.cuda.current_stream()
+        ga = ctx.graph(T.TPCF_GRAPH_AUTO, cd, None, b)
+        gc = ctx.graph(T.TPCF_GRAPH_CROSS, cd, cr, b)
+        gall = ctx.graph(T.TPCF_GRAPH_ALL, cd, cr, b)
+        for g in (ga, gc, gall):
+            g.launch(s)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ga.out.cpu().numpy().view(np.uint64), dd)
+        np.testing.assert_array_equal(gc.out.cpu().numpy().view(np.uint64), dr)
+        np.testing.assert_array_equal(gall.out.cpu().numpy().view(np.uint64), np.stack([dd, dr, rr]))
+        assert gall.stats()["pairs"] == int(dd.sum() + dr.sum() + rr.sum())
+        ctx.free(ga)
+        with pytest.raises(T.TpcfError) as e:
+            ctx.graph(T.TPCF_GRAPH_PATCHES, cd, cr, b)  # not segmented
+        assert e.value.status == T.TPCF_EINVAL
+        g_new = ctx.graph(T.TPCF_GRAPH_AUTO, cr, None, b)
+        with pytest.raises(T.TpcfError) as e:
+            g_new.stats()  # never launched
+        assert e.value.status == T.TPCF_ESTATE

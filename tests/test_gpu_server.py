@@ -182,3 +182,19 @@ def test_destroy_with_queued_jobs(T):
     for _ in range(4):
         ctx.submit(d, r, edges)
     ctx.close()  # waits for the running job, drops the queued ones
+
+
+def test_mixed_sizes_and_bin_sets(T):
+    """Serving-style jobs (cap footprints, 20-80 bins, sizes over two decades) in
+    flight together use different kernel shapes and shared-memory sizes; each
+    result must still equal its lone call."""
+    specs = synth.serving_jobs(24, seed=3, nd_min=1e3, nd_max=1.5e5)
+    jobs = [synth.materialise_job(s) for s in specs]
+    with T.Context() as ctx:
+        alone = [ctx.correlate(w.data, w.rand, w.edges) for w in jobs]
+    with T.Context(server_workers=6) as ctx:
+        ids = [ctx.submit(w.data, w.rand, w.edges) for w in jobs]
+        for k, (jid, w) in enumerate(zip(ids, jobs)):
+            res = ctx.poll(jid, len(w.edges))
+            for name, want in zip(("dd", "dr", "rr", "w"), alone[k]):
+                np.testing.assert_array_equal(res[name], want, err_msg=f"job {k} {name}")

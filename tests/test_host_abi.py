@@ -165,3 +165,13 @@ def test_server_entry_points_reject_null_context():
     assert lib.tpcf_submit(None, ctypes.byref(job), ctypes.byref(jid)) == tpcf.TPCF_EINVAL
     assert lib.tpcf_poll(None, 1, 0, None) == tpcf.TPCF_EINVAL
     assert lib.tpcf_cancel(None, 1) == tpcf.TPCF_EINVAL
+
+
+def test_graph_entry_points_reject_null():
+    from paper_1204_6630_gb300 import tpcf
+    lib = tpcf.load()
+    h = ctypes.c_void_p()
+    assert lib.tpcf_graph_create(None, 0, None, None, None, None, ctypes.byref(h)) == tpcf.TPCF_EINVAL
+    assert lib.tpcf_graph_launch(None, None) == tpcf.TPCF_EINVAL
+    assert lib.tpcf_graph_stats(None, None) == tpcf.TPCF_EINVAL
+    assert lib.tpcf_graph_destroy(None) == tpcf.TPCF_EINVAL
