@@ -70,6 +70,7 @@ struct tpcf_catalog {
     float4* d32 = nullptr;
     float4* d32x2 = nullptr;        // (x,x,y,y),(z,z,0,0) per point for the packed screen
     std::vector<uint64_t> offsets;  // segments (empty = one segment)
+    double eps_max = 0.0;           // bound on | |v|^2 - 1 | over the points
     cudaStream_t free_stream = nullptr;  // stream-ordered buffers: freed in this stream's order
     bool stream_ordered = false;
 };
@@ -80,6 +81,7 @@ struct tpcf_bins {
     std::vector<double> edges, cos_thr;
     std::vector<float> lo, hi, c32;      // cos-space FP32 bounds (reported by the ABI)
     std::vector<float> elo, ehi, ec;     // screen-value (e-space) bounds used by the kernel
+    std::vector<float> zlo, zhi;         // chord-space bounds (refinement of unsettled pairs)
     std::vector<uint32_t> lut;
     std::vector<int> verified;
     tpcf::BinsDev host;                  // device pointers, host copy

@@ -122,6 +122,16 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     return d;
 }
 
+// AND of the bit patterns of N floats as a balanced tree (depth log N).
+template <int N>
+__device__ __forceinline__ int and_tree(const float* v) {
+    if constexpr (N == 1) {
+        return __float_as_int(v[0]);
+    } else {
+        return and_tree<N / 2>(v) & and_tree<N - N / 2>(v + N / 2);
+    }
+}
+
 // ============================================================== work cursor
 // Enumerates (item, tile) pairs of one block in processing order.  The
 // consumer (all threads) and the producer (thread 0, S tiles ahead) each
@@ -188,16 +198,17 @@ enum Ctl { kCtlAbort = 0, kCtlWarpsDone = 1, kCtlIssued = 2, kCtlRelease = 8, kC
            kCtlWords = 64 };
 constexpr int kMaxStages = 16;   // release counters live at kCtlRelease + stage
 constexpr int kQueuePerWarp = 64;   // band pairs per warp awaiting the binary64 recheck
+constexpr uint32_t kCursorBytes = 32;  // one producer cursor slot
 
 struct SmemLayout {
     uint32_t bars;      // S full mbarriers
     uint32_t ctl;       // control words
     uint32_t stage;     // S * J * pt_bytes
-    uint32_t hist;      // ceil((nedges + 1) / 2) * T uint32: rows 2w, 2w+1 as 16-bit halves, column tid
+    uint32_t hist;      // (nedges + 1) * T / 2 uint32: row h, column c at word h * T/2 + c (see HistCol)
     uint32_t cos_thr;   // nedges doubles
-    uint32_t lo, hi, cos32;  // nedges floats each
-    uint32_t lut;       // kLutMax uint32 (screen only)
-    uint32_t queue;     // W * kQueuePerWarp band pairs (uint4, screen only)
+    uint32_t lo, hi, cos32, zlo, zhi;  // nedges floats each
+    uint32_t lut;       // kLutCells uint32 (screen only)
+    uint32_t queue;     // W * kQueuePerWarp unsettled pairs (i, j) (uint2, screen only)
     uint32_t prod;      // W producer cursors (one per warp, used by its lane 0)
     uint32_t total;
 };
@@ -213,84 +224,110 @@ __host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S,
     L.ctl = off; off += kCtlWords * 4;
     off = align_up(off, 128);
     L.stage = off; off += (uint32_t)S * J * pt;
-    L.hist = off; off += (uint32_t)((nedges + 2) / 2) * T * 4;
+    L.hist = off; off += (uint32_t)(nedges + 1) * (uint32_t)(T / 2) * 4;
     off = align_up(off, 16);
     L.cos_thr = off; off += (uint32_t)nedges * 8;
     L.lo = off; off += (uint32_t)nedges * 4;
     L.hi = off; off += (uint32_t)nedges * 4;
     L.cos32 = off; off += (uint32_t)nedges * 4;
+    L.zlo = off; off += (uint32_t)nedges * 4;
+    L.zhi = off; off += (uint32_t)nedges * 4;
     off = align_up(off, 16);
-    L.lut = off; off += plain ? 0u : (uint32_t)kLutMax * 4;
+    L.lut = off; off += plain ? 0u : (uint32_t)kLutCells * 4;
     off = align_up(off, 16);
-    L.queue = off; off += plain ? 0u : (uint32_t)(T / 32) * kQueuePerWarp * 16;
+    L.queue = off; off += plain ? 0u : (uint32_t)(T / 32) * kQueuePerWarp * 8;
     off = align_up(off, 16);
-    L.prod = off; off += (uint32_t)(T / 32) * (uint32_t)align_up(sizeof(Cursor), 16);
+    L.prod = off; off += (uint32_t)(T / 32) * kCursorBytes;
     L.total = off;
     return L;
 }
 
 // ============================================================== block helpers
+// Block constants live in the kernel parameter (constant bank): the host fills
+// the shared-memory offsets and the bin scalars of WorkDesc, so the kernel
+// spends no registers on them.
 template <int T>
-__device__ void load_bins(const BinsDev* bd, unsigned char* smem, const SmemLayout& L, bool plain) {
-    const int ne = bd->nedges;
-    double* c = (double*)(smem + L.cos_thr);
-    float* lo = (float*)(smem + L.lo);
-    float* hi = (float*)(smem + L.hi);
-    float* c32 = (float*)(smem + L.cos32);
+__device__ void load_bins(const BinsDev* bd, const WorkDesc& wd, bool plain) {
+    const int ne = wd.ne;
+    double* c = sptr<double>(wd.off_cthr);
+    float* lo = sptr<float>(wd.off_lo);
+    float* hi = sptr<float>(wd.off_hi);
+    float* c32 = sptr<float>(wd.off_c32);
+    float* zlo = sptr<float>(wd.off_zlo);
+    float* zhi = sptr<float>(wd.off_zhi);
     for (int k = threadIdx.x; k < ne; k += T) {
         c[k] = bd->cos_thr[k];
         lo[k] = bd->lo[k];
         hi[k] = bd->hi[k];
         c32[k] = bd->cos32[k];
+        zlo[k] = bd->zlo[k];
+        zhi[k] = bd->zhi[k];
     }
     if (!plain) {
         // Shared copy of the LUT re-encoded for this block shape: a settled entry
-        // (P == Q) holds the word offset (P / 2) * T of the thread's histogram
-        // word in bits 0..15 and the 16-bit half (P & 1) in bit 16; an
-        // unsettled entry has bit 31 set and P, Q in bits 0..11, 12..23.
-        uint32_t* lut = (uint32_t*)(smem + L.lut);
-        for (int k = threadIdx.x; k < bd->nlut; k += T) {
+        // (P == Q) holds the byte offset P * (T/2) * 4 of row P from a thread's
+        // column (non-negative); an unsettled entry has bit 31 set and P, Q in
+        // bits 0..11, 12..23.
+        uint32_t* lut = sptr<uint32_t>(wd.off_lut);
+        for (int k = threadIdx.x; k < kLutCells; k += T) {
             const uint32_t e = bd->lut[k];
             const uint32_t P = e & 0xffffu, Q = e >> 16;
-            lut[k] = (P == Q) ? ((P >> 1) * (uint32_t)T) | ((P & 1u) << 16)
-                              : 0x80000000u | P | (Q << 12);
+            lut[k] = (P == Q) ? P * (uint32_t)(T / 2) * 4u : 0x80000000u | P | (Q << 12);
         }
     }
 }
 
-// One warp merges its 32 private histogram columns into the global uint64
-// bins and zeroes them.  Each 32-bit word holds two 16-bit counters (rows 2w
-// and 2w + 1).  Rows 0..nedges-1 (underflow and the B bins) are merged; row
-// nedges (pairs found beyond the last edge) is dropped: overflow is derived
-// from the pair total by the finalize kernel.
+// Thread-private 16-bit histogram counters, two per 32-bit shared word:
+// thread t < T/2 owns the low halves of column t, thread t + T/2 the high
+// halves of the same column, so every thread adds one fixed increment (1 or
+// 2^16) and the LUT can hold a plain byte offset of the row.  A counter has a
+// single writer; the word's atomic add keeps the partner's half intact.
+struct HistCol {
+    uint32_t addr;  // shared byte address of the thread's word in row 0
+    uint32_t inc;   // 1 (low half) or 65536 (high half)
+};
+
 template <int T>
-__device__ void warp_flush_hist(uint32_t* hist, int nedges, unsigned long long* out) {
+__device__ __forceinline__ HistCol hist_col(const WorkDesc& wd) {
+    const uint32_t t = threadIdx.x;
+    return HistCol{smem_addr(dyn_smem) + wd.off_hist + (t % (T / 2)) * 4u, t < T / 2 ? 1u : 65536u};
+}
+
+__device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+__device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+// Histogram row h of the thread's column, one increment.
+template <int T>
+__device__ __forceinline__ void hist_inc(const HistCol& hc, int h) {
+    red_add_shared(hc.addr + (uint32_t)h * (uint32_t)(T / 2) * 4u, hc.inc);
+}
+
+// One warp merges its 32 counters of every row into the global uint64 bins
+// and clears them.  Rows 0..nedges-1 (underflow and the B bins) are merged;
+// row nedges (pairs beyond the last edge) is only cleared: overflow is
+// derived from the pair total by the finalize kernel.  Each thread takes its
+// own half out of the shared word with an atomic subtract, since the partner
+// warp may be adding to the other half at the same time.
+template <int T>
+__device__ void warp_flush_hist(const HistCol& hc, int nedges, unsigned long long* out) {
     const int lane = threadIdx.x & 31;
-    const int words = (nedges + 2) / 2;
-    for (int w = 0; w < words; ++w) {
-        uint32_t* p = hist + w * T + threadIdx.x;
-        const uint32_t v = *p;
-        *p = 0;
-        uint32_t lo = v & 0xffffu, hi = v >> 16;
+    const uint32_t sh = hc.inc == 1u ? 0u : 16u;
+    for (int h = 0; h <= nedges; ++h) {
+        const uint32_t a = hc.addr + (uint32_t)h * (uint32_t)(T / 2) * 4u;
+        uint32_t mine = (ld_shared_u32(a) >> sh) & 0xffffu;
+        if (mine) red_add_shared(a, 0u - (mine << sh));
+        if (h == nedges) break;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo += __shfl_down_sync(0xffffffffu, lo, o);
-            hi += __shfl_down_sync(0xffffffffu, hi, o);
-        }
-        if (lane == 0) {
-            if (lo != 0 && 2 * w < nedges) atomicAdd(out + 2 * w, (unsigned long long)lo);
-            if (hi != 0 && 2 * w + 1 < nedges) atomicAdd(out + 2 * w + 1, (unsigned long long)hi);
-        }
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+        if (lane == 0 && mine != 0) atomicAdd(out + h, (unsigned long long)mine);
     }
-}
-
-// Thread-private histogram increment of row h (one shared-memory reduction
-// instruction on the 16-bit half of the row pair's word).
-template <int T>
-__device__ __forceinline__ void hist_inc(uint32_t* hcol, int h) {
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_addr(hcol + (h >> 1) * T)),
-                 "r"(1u << ((h & 1) << 4))
-                 : "memory");
 }
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
@@ -313,44 +350,34 @@ __device__ __forceinline__ double dot64(const Point64& a, const Point64& b) {
     return __dadd_rn(__dadd_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)), __dmul_rn(a.z, b.z));
 }
 
-struct BandStats {
-    unsigned long long band;
-    unsigned long long mismatch;
-};
-
 // Exact histogram index of a band pair: h = nbv + #{m in [nbv, nav) : d <= C_m}
 // with d the binary64 dot product (the edges below nbv are certainly crossed,
-// those from nav on certainly not).  h32 is the FP32-only index, kept for the
-// mismatch statistic.
-__device__ __forceinline__ int band_index(const Point64* a64, const Point64* b64, uint32_t ig,
-                                          uint32_t jg, int nbv, int nav, int h32,
-                                          uint32_t cthr_o, BandStats& bs) {
-    const double* cthr = sptr<const double>(cthr_o);
-    const double d = dot64(ldg_point(a64 + ig), ldg_point(b64 + jg));
+// those from nav on certainly not).  h32 is the FP32-only index; *mismatch
+// is set when it differs (statistics).
+__device__ __forceinline__ int band_index(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg, int nbv, int nav,
+                                          int h32, uint32_t* mismatch) {
+    const SubProblem& sp = sub_of(wd, sub);
+    const double* cthr = sptr<const double>(wd.off_cthr);
+    const double d = dot64(ldg_point(sp.a64 + ig), ldg_point(sp.b64 + jg));
     int h = nbv;
     for (int m = nbv; m < nav; ++m) h += (d <= cthr[m]);
-    bs.band += 1;
-    bs.mismatch += (h != h32);
+    *mismatch = (h != h32) ? 1u : 0u;
     return h;
 }
 
-// FP32 classification of a pair with FP32 cosine c >= lo_B.  The LUT entry of
-// c's key range holds P = nb(c_max) and Q = na(c_min), where
-// nb(c) = #{m : c < lo_m} (edges certainly crossed) and
-// na(c) = #{m : c <= hi_m} (edges possibly crossed); P == Q settles the index.
-// resolve_f32: for an unsettled entry, compare c with the few edges in [P, Q).
-// Returns h >= 0 when settled; otherwise h = -1 with the band range
-// [nbv, nav) and the FP32-only index h32.  Arguments and result are plain
-// values so that no local object's address escapes into this rare call.
+// FP32 classification of a pair whose LUT entry left edges [P, Q) open:
+// nb(c) = #{m : c < lo_m} (edges certainly crossed), na(c) = #{m : c <= hi_m}
+// (edges possibly crossed); nb == na settles the index.  Otherwise h = -1
+// with the band range [nbv, nav) and the FP32-only index h32.  Plain values in
+// and out so that no local object's address escapes into this rare call.
 struct Resolved {
     int h, nbv, nav, h32;
 };
 
-__device__ __forceinline__ Resolved resolve_f32(float c, int P, int Q, uint32_t lo_o, uint32_t hi_o,
-                                               uint32_t c32_o) {
-    const float* lo = sptr<const float>(lo_o);
-    const float* hi = sptr<const float>(hi_o);
-    const float* c32 = sptr<const float>(c32_o);
+__device__ __forceinline__ Resolved resolve_f32(const WorkDesc& wd, float c, int P, int Q) {
+    const float* lo = sptr<const float>(wd.off_lo);
+    const float* hi = sptr<const float>(wd.off_hi);
+    const float* c32 = sptr<const float>(wd.off_c32);
     int nb_ = P, na_ = P;
     for (int m = P; m < Q; ++m) {
         nb_ += (c < lo[m]);
@@ -362,134 +389,184 @@ __device__ __forceinline__ Resolved resolve_f32(float c, int P, int Q, uint32_t 
     return Resolved{-1, nb_, na_, h};
 }
 
-// One warp classifies its queued pairs.  Two kinds of entry (i, j, z, w):
-// unsettled pairs with w = their LUT entry (bit 31 set) and z = the screen
-// value's bits, first compared with the edges the entry leaves open; and band
-// pairs with z = nbv | nav << 16, w = h32.  Pairs inside a guard band are
-// recomputed in binary64.  Each lane adds to its own histogram column; ends
-// with the warp's queue empty.  Returns the lane's band statistics so that no
-// local object's address escapes.
+__device__ __forceinline__ uint32_t queue_off(const WorkDesc& wd, int warp) {
+    return wd.off_queue + (uint32_t)warp * kQueuePerWarp * 8;
+}
+
+__device__ __forceinline__ uint32_t queue_count_off(const WorkDesc& wd, int warp) {
+    return wd.off_ctl + (uint32_t)(kCtlQueue + warp) * 4;
+}
+
+// Screen value of pair (ig, jg) recomputed from the FP32 copies with the
+// fast loop's operation order (bit-identical: fma.rn.f32x2 rounds each half
+// as fmaf does).
+__device__ __forceinline__ float screen_value(const WorkDesc& wd, const SubProblem& sp, uint32_t ig, uint32_t jg) {
+    const float4 a = __ldg(sp.a32 + ig), b = __ldg(sp.b32 + jg);
+    return fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, wd.neg_fast_t)));
+}
+
+// LUT entry of screen value e (see slow_j).
+__device__ __forceinline__ uint32_t lut_entry(const WorkDesc& wd, float e) {
+    const float v = __saturatef(e * wd.lut_scale);
+    const float f = fmaf(v, 16384.0f, 8388608.0f);
+    return ld_shared_u32(smem_addr(dyn_smem) + wd.off_lut + (__float_as_uint(f) - 0x4B000000u) * 4u);
+}
+
+// Histogram index of an unsettled pair: the FP32 comparison with the edges
+// its LUT entry leaves open, else (inside a guard band) the binary64
+// recomputation.  Band statistics are added to *band, *mism.
+__device__ __forceinline__ int classify_unsettled(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg,
+                                                  uint32_t* band, uint32_t* mism) {
+    const SubProblem& sp = sub_of(wd, sub);
+    const float e = screen_value(wd, sp, ig, jg);
+    const uint32_t ent = lut_entry(wd, e);
+    if ((int)ent >= 0) return (int)(ent / (uint32_t)(4 * (blockDim.x / 2)));  // settled (not expected)
+    const Resolved rs = resolve_f32(wd, e, (int)(ent & 0xfffu), (int)((ent >> 12) & 0xfffu));
+    if (rs.h >= 0) return rs.h;
+    uint32_t mm;
+    const int h = band_index(wd, sub, ig, jg, rs.nbv, rs.nav, rs.h32, &mm);
+    *band += 1;
+    *mism += mm;
+    return h;
+}
+
+// One warp classifies its queued pairs (i, j) and adds each to the lane's
+// own histogram column; the warp's band statistics go to the call's
+// statistics words; ends with the warp's queue empty.
 template <int T>
-__device__ __forceinline__ BandStats warp_drain_queue(uint32_t wq_o, uint32_t wqc_o, const Point64* a64,
-                                                      const Point64* b64, uint32_t cthr_o, uint32_t lo_o,
-                                                      uint32_t hi_o, uint32_t c32_o, uint32_t* hcol) {
-    const uint4* wq = sptr<const uint4>(wq_o);
-    volatile int* wq_count = sptr<volatile int>(wqc_o);
-    BandStats bs = {0ull, 0ull};
+__device__ __noinline__ void warp_drain_queue(const WorkDesc& wd, int sub, HistCol hc) {
+    const int warp = (int)(threadIdx.x >> 5);
+    const uint2* wq = sptr<const uint2>(queue_off(wd, warp));
+    volatile int* wq_count = sptr<volatile int>(queue_count_off(wd, warp));
+    uint32_t band = 0, mism = 0;
     __syncwarp();
     const int n = min(*wq_count, kQueuePerWarp);
     for (int k = (int)(threadIdx.x & 31); k < n; k += 32) {
-        const uint4 q = wq[k];
-        int h, nbv, nav, h32;
-        if (q.w >> 31) {
-            const Resolved rs = resolve_f32(__uint_as_float(q.z), (int)(q.w & 0xfffu),
-                                            (int)((q.w >> 12) & 0xfffu), lo_o, hi_o, c32_o);
-            h = rs.h;
-            nbv = rs.nbv;
-            nav = rs.nav;
-            h32 = rs.h32;
-        } else {
-            h = -1;
-            nbv = (int)(q.z & 0xffffu);
-            nav = (int)(q.z >> 16);
-            h32 = (int)q.w;
+        const uint2 q = wq[k];
+        hist_inc<T>(hc, classify_unsettled(wd, sub, q.x, q.y, &band, &mism));
+    }
+    const unsigned long long b = warp_sum(band), m = warp_sum(mism);
+    if ((threadIdx.x & 31) == 0) {
+        if (b) atomicAdd(wd.stats + kStatBand, b);
+        if (m) atomicAdd(wd.stats + kStatMismatch, m);
+        *wq_count = 0;
+    }
+    __syncwarp();
+}
+
+// An unsettled pair (divergent: executed by the lanes holding one): queued
+// for the warp's drain, one shared atomic for all active lanes; when the
+// queue is full the pair is classified at once (rare, out of line).
+template <int T>
+__device__ __noinline__ void classify_now(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg, HistCol hc) {
+    uint32_t band = 0, mism = 0;
+    hist_inc<T>(hc, classify_unsettled(wd, sub, ig, jg, &band, &mism));
+    if (band) atomicAdd(wd.stats + kStatBand, 1ull);
+    if (mism) atomicAdd(wd.stats + kStatMismatch, 1ull);
+}
+
+template <int T>
+__device__ __forceinline__ void queue_pair(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg, const HistCol& hc) {
+    const uint32_t act = __activemask();
+    const uint32_t lane = threadIdx.x & 31u;
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(sptr<int>(queue_count_off(wd, (int)(threadIdx.x >> 5))), __popc(act));
+    base = __shfl_sync(act, base, leader);
+    const int pos = base + __popc(act & ((1u << lane) - 1u));
+    if (pos < kQueuePerWarp)
+        sptr<uint2>(queue_off(wd, (int)(threadIdx.x >> 5)))[pos] = make_uint2(ig, jg);
+    else
+        classify_now<T>(wd, sub, ig, jg, hc);
+}
+
+// An unsettled pair of the slow path: its screen value and LUT entry are
+// recomputed from the FP32 points (bit-identical; cheaper than indexing the
+// caller's register arrays), then the chord refinement decides the edges
+// the entry leaves open: z = fl32(|a' - b'|^2) is within 4u|a - b| + O(u
+// |a-b|^2) of 2 (1 - d) (bounds zlo, zhi: runtime.cpp), far tighter than the
+// screen value at the small and moderate angles of a histogram range.
+// Z-space bounds increase with the edge index, so a binary search over
+// [P, Q) finds nb = #{crossed}; the pair is settled when z is also below
+// zlo[nb].  Pairs left in a chord band (or catalogs outside the chord
+// bound's norm tolerance) are queued for the binary64 recheck.
+template <int T>
+__device__ __forceinline__ void unsettled_pair(const WorkDesc& wd, int sub, const float4 a, const float4& b,
+                                               uint32_t ig, uint32_t jg, const HistCol& hc) {
+    if (wd.chord_ok) {
+        const float e = fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, wd.neg_fast_t)));
+        const uint32_t ent = lut_entry(wd, e);
+        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        const float z = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float* zlo = sptr<const float>(wd.off_zlo);
+        const float* zhi = sptr<const float>(wd.off_zhi);
+        int lo = (int)(ent & 0xfffu), hi = (int)((ent >> 12) & 0xfffu);
+        const int Q = hi;
+        while (lo < hi) {  // first m in [P, Q) with z < zhi[m]
+            const int mid = (lo + hi) >> 1;
+            if (z >= zhi[mid]) lo = mid + 1; else hi = mid;
         }
-        if (h < 0) h = band_index(a64, b64, q.x, q.y, nbv, nav, h32, cthr_o, bs);
-        hist_inc<T>(hcol, h);
+        if (lo == Q || z < zlo[lo]) {
+            hist_inc<T>(hc, lo);
+            return;
+        }
     }
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) *wq_count = 0;
-    __syncwarp();
-    return bs;
+    queue_pair<T>(wd, sub, ig, jg, hc);
 }
 
-// Slow path for one j (warp-uniform).  Branch-free over the R pairs of each
-// lane: every in-range pair's LUT entry is loaded (G independent shared loads
-// in flight) and pairs with a settled entry increment the thread's own
-// histogram word directly from the entry (predicated red.shared).  The rare
-// unsettled pairs are compared with the edges left open (resolve_f32); pairs
-// inside a guard band go to the warp's queue for the binary64 recheck.
-struct SlowCtx {
-    uint32_t lut_o, lo_o, hi_o, c32_o, cthr_o;  // shared-memory byte offsets
-    uint32_t wq_o, wqc_o;                       // this warp's queue and its count
-    int32_t key0;
-    int shift, nlut;
-    bool need_idx;
-    uint32_t na;
-    const Point64* a64;
-    const Point64* b64;
-};
-
-template <int T>
-__device__ __forceinline__ void drain(const SlowCtx& sc, uint32_t* hcol, BandStats& bs) {
-    const BandStats d = warp_drain_queue<T>(sc.wq_o, sc.wqc_o, sc.a64, sc.b64, sc.cthr_o, sc.lo_o, sc.hi_o,
-                                            sc.c32_o, hcol);
-    bs.band += d.band;
-    bs.mismatch += d.mismatch;
-}
-
-// An unsettled pair: queued for the warp's drain when there is room, else
-// classified at once.
-template <int T>
-__device__ __forceinline__ void resolve_pair(float e, uint32_t ent, uint32_t ig, uint32_t jg,
-                                             const SlowCtx& sc, uint32_t* hcol, BandStats& bs) {
-    const int pos = atomicAdd(sptr<int>(sc.wqc_o), 1);
-    if (pos < kQueuePerWarp) {
-        sptr<uint4>(sc.wq_o)[pos] = make_uint4(ig, jg, __float_as_uint(e), ent);
-        return;
-    }
-    const Resolved rs = resolve_f32(e, (int)(ent & 0xfffu), (int)((ent >> 12) & 0xfffu), sc.lo_o, sc.hi_o,
-                                    sc.c32_o);
-    const int h = rs.h >= 0 ? rs.h : band_index(sc.a64, sc.b64, ig, jg, rs.nbv, rs.nav, rs.h32, sc.cthr_o, bs);
-    hist_inc<T>(hcol, h);
-}
-
+// Slow path for one j (warp-uniform), all R pairs of every lane, branch-free:
+// the LUT cell of e is k = rne(sat(e * 2^-q) * 2^14), read as the low bits of
+// fma(v, 2^14, 2^23); a settled entry is the byte offset of the pair's row,
+// so the pair costs one shared load and one shared reduction.  All R loads are
+// issued before the first reduction (shared loads and reductions stay in
+// program order, so interleaving them would expose the load latency once per
+// pair).  Pairs beyond the range (e < 0 or in cell 0) land in the overflow
+// row, which is never merged; pairs that must not be counted (padding, j <= i
+// on the diagonal) are given e = -1 first.  Unsettled entries (bit 31) go
+// through unsettled_pair, one pair per iteration.
 template <int T, int R>
-__device__ __forceinline__ void slow_e(const float (&e)[R], uint32_t ibase, uint32_t jg, bool j_ok,
-                                       bool masked, const SlowCtx& sc, uint32_t* hcol, BandStats& bs) {
-    constexpr int G = 4;  // pairs per batch: G LUT loads in flight per lane
-    const uint32_t hbase = smem_addr(hcol);
-    // pairs that may be counted: all, unless indices need checking (padding
-    // inside the range) or the tile straddles the diagonal (j > i only)
-    uint32_t valid = (1u << R) - 1u;
-    if (sc.need_idx || masked) {
-        valid = 0;
+__device__ __forceinline__ void slow_j(const WorkDesc& wd, int sub, float (&e)[R], const float4& b, uint32_t ibase,
+                                       uint32_t jg, bool masked, const HistCol& hc) {
+    if (wd.need_idx || masked) {
+        const uint32_t na = sub_of(wd, sub).na, nb = sub_of(wd, sub).nb;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const uint32_t ig = ibase + 32u * r;
-            const bool ok = (!sc.need_idx || (j_ok && ig < sc.na)) && (!masked || jg > ig);
-            valid |= ok ? (1u << r) : 0u;
+            const bool ok = (!wd.need_idx || (jg < nb && ig < na)) && (!masked || jg > ig);
+            if (!ok) e[r] = -1.0f;
         }
     }
+    const uint32_t lut_adj = smem_addr(dyn_smem) + wd.off_lut - 0x4B000000u * 4u;  // + 4 bits(f): entry
+    uint32_t ent[R];
 #pragma unroll
-    for (int r0 = 0; r0 < R; r0 += G) {
-        uint32_t ent[G];
-        uint32_t amb = 0;
+    for (int r = 0; r < R; ++r) {
+        const float v = __saturatef(e[r] * wd.lut_scale);
+        const float f = fmaf(v, 16384.0f, 8388608.0f);
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(ent[r]) : "r"(__float_as_uint(f) * 4u + lut_adj));
+    }
+    uint32_t um = 0;  // unsettled pairs of this lane, bit r
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const int r = r0 + g;
-            const bool in = e[r] >= 0.f && (valid & (1u << r));
-            // LUT index from the bits of RN(1 + e): linear in e on [0, 1)
-            int idx = (__float_as_int(__fadd_rn(1.0f, e[r])) - sc.key0) >> sc.shift;
-            idx = in ? min(idx, sc.nlut - 1) : 0;
-            ent[g] = sptr<const uint32_t>(sc.lut_o)[idx];
-            const bool settled = (int)ent[g] >= 0;
-            if (in && settled) {
-                asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hbase + ((ent[g] & 0xffffu) << 2)),
-                             "r"(1u << ((ent[g] >> 12) & 16u))
-                             : "memory");
-            }
-            amb |= (in && !settled) ? (1u << g) : 0u;
-        }
-        if (amb) {
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-                if (amb & (1u << g))
-                    resolve_pair<T>(e[r0 + g], ent[g], ibase + 32u * (r0 + g), jg, sc, hcol, bs);
+    for (int r = 0; r < R; ++r) {
+        if ((int)ent[r] >= 0) red_add_shared(hc.addr + ent[r], hc.inc);
+        um |= (ent[r] >> 31) << r;
+    }
+    if (__any_sync(0xffffffffu, um != 0u)) {
+        const float4* a32 = sub_of(wd, sub).a32;
+        while (um) {  // one iteration per unsettled pair of the lane
+            const int r = __ffs(um) - 1;
+            um &= um - 1;
+            const uint32_t ig = ibase + 32u * (uint32_t)r;
+            unsettled_pair<T>(wd, sub, __ldg(a32 + ig), b, ig, jg, hc);
         }
     }
+}
+
+// After a group of slow j: drain the warp's queue once it is half full.
+template <int T>
+__device__ __forceinline__ void maybe_drain(const WorkDesc& wd, int sub, const HistCol& hc) {
     __syncwarp();
-    if (*sptr<volatile int>(sc.wqc_o) >= kQueuePerWarp / 2) drain<T>(sc, hcol, bs);
+    if (*sptr<volatile int>(queue_count_off(wd, (int)(threadIdx.x >> 5))) >= kQueuePerWarp / 2)
+        warp_drain_queue<T>(wd, sub, hc);
 }
 
 // ============================================================== the counting kernel
@@ -507,21 +584,11 @@ template <int T, int R, int MODE>
 __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ WorkDesc wd) {
     constexpr bool PLAIN = MODE == kModePlain;
     constexpr bool PACKED = MODE == kModeScreen2;
-    unsigned char* smem = dyn_smem;
     constexpr int W = T / 32;
-    const int S = (int)wd.stages;
-    const int J = (int)wd.J;
-    const int I = T * R;
-    const int nedges = wd.nedges_max;
-    const SmemLayout L = smem_layout(MODE, T, J, S, nedges);
-    uint64_t* bars = (uint64_t*)(smem + L.bars);
-    volatile int* ctl = (volatile int*)(smem + L.ctl);
-    uint32_t* hist = (uint32_t*)(smem + L.hist);
-    constexpr uint32_t PT = MODE == kModeScreen ? 16u : 32u;
-    const uint32_t stage_bytes = (uint32_t)J * PT;
+    const uint32_t S = wd.stages;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t* hcol = hist + tid;
-    const double* cthr = (const double*)(smem + L.cos_thr);
+    uint64_t* bars = sptr<uint64_t>(wd.off_bars);
+    volatile int* ctl = sptr<volatile int>(wd.off_ctl);
 
     Cursor cons;
     cursor_begin(wd, cons);
@@ -529,84 +596,52 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
 
     // ---- set up: barriers, control words, histogram, bins (all sub-problems share them)
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        for (uint32_t s = 0; s < S; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     for (int k = tid; k < kCtlWords; k += T) ctl[k] = 0;
-    for (int k = tid; k < ((nedges + 2) / 2) * T; k += T) hist[k] = 0;
-    const BinsDev* bd = sub_of(wd, cons.sub).bins;
-    load_bins<T>(bd, smem, L, PLAIN);
-    const int ne = bd->nedges;
-    const float neg_fast_t = -bd->fast_t;
-    const double cos_last = bd->cos_last;
-    const int32_t key0 = bd->lut_key0;
-    const int lut_shift = bd->lut_shift, nlut = bd->nlut;
-    // zero-vector padding has screen value e = -T: it can look in range only when
-    // T <= 0; sub-ranges of segmented catalogs are followed by real points
-    const bool need_idx = wd.force_idx || !(bd->fast_t > 0.f);
+    {
+        uint32_t* hist = sptr<uint32_t>(wd.off_hist);
+        for (int k = tid; k < (wd.nedges_max + 1) * (T / 2); k += T) hist[k] = 0;
+    }
+    load_bins<T>(sub_of(wd, cons.sub).bins, wd, PLAIN);
     __syncthreads();
-    SlowCtx sctx;
-    sctx.lut_o = L.lut;
-    sctx.lo_o = L.lo;
-    sctx.hi_o = L.hi;
-    sctx.c32_o = L.cos32;
-    sctx.cthr_o = L.cos_thr;
-    sctx.key0 = key0;
-    sctx.shift = lut_shift;
-    sctx.nlut = nlut;
-    sctx.need_idx = need_idx;
-    sctx.na = 0;
-    sctx.a64 = nullptr;
-    sctx.b64 = nullptr;
-    sctx.wq_o = L.queue + (uint32_t)warp * kQueuePerWarp * 16;
-    sctx.wqc_o = L.ctl + (kCtlQueue + warp) * 4;
-
+    const HistCol hc = hist_col<T>(wd);
 
     auto issue = [&](uint32_t seq, const Cursor& pc) {
         const SubProblem& sp = sub_of(wd, pc.sub);
-        const uint32_t jbase = pc.g.j0 + pc.t * (uint32_t)J;
-        unsigned char* dst = smem + L.stage + (seq % (uint32_t)S) * stage_bytes;
+        const uint32_t jbase = pc.g.j0 + pc.t * wd.J;
+        unsigned char* dst = sptr<unsigned char>(wd.off_stage + (seq % S) * wd.stage_bytes);
         if ((wd.flags & TPCF_F_TEST_WAIT_TIMEOUT) && seq == 0) return;  // test hook: never issued
-        mbar_expect_tx(&bars[seq % (uint32_t)S], stage_bytes);
+        mbar_expect_tx(&bars[seq % S], wd.stage_bytes);
         const void* src = PLAIN ? (const void*)(sp.b64 + jbase)
                                 : PACKED ? (const void*)(sp.b32x2 + 2ull * jbase) : (const void*)(sp.b32 + jbase);
-        bulk_copy_g2s(dst, src, stage_bytes, &bars[seq % (uint32_t)S]);
+        bulk_copy_g2s(dst, src, wd.stage_bytes, &bars[seq % S]);
     };
 
     // ---- prologue: thread 0 issues the first S tiles; lane 0 of every warp
     // keeps a producer cursor S tiles ahead (in shared memory) for its refill
     // turns.
-    Cursor* prod = (Cursor*)(smem + L.prod + (uint32_t)warp * align_up(sizeof(Cursor), 16));
     if (lane == 0) {
         Cursor pc = cons;
-        int k = 0;
+        uint32_t k = 0;
         for (; k < S && pc.valid; ++k) {
-            if (tid == 0) issue((uint32_t)k, pc);
+            if (tid == 0) issue(k, pc);
             cursor_next(wd, pc);
         }
-        *prod = pc;
-        if (tid == 0) ctl[kCtlIssued] = k;
+        *sptr<Cursor>(wd.off_prod + (uint32_t)warp * kCursorBytes) = pc;
+        if (tid == 0) ctl[kCtlIssued] = (int)k;
     }
     __syncwarp();
 
     // ---- consumer state
     int cur_sub = -1;
-    unsigned long long* cur_hist = nullptr;
-    uint64_t j_since_flush = 0;
-    // 16-bit counters: a lane adds at most R per j to one row plus at most 2 per
-    // queue drain (one drain per 4 j), so merging every 65535 / (R + 1) - J
-    // j-points keeps every counter below 2^16
-    const uint64_t flush_limit = (0xffffull / (R + 1)) - (uint64_t)J;
+    uint32_t j_since_flush = 0;
     float ax[MODE == kModeScreen ? R : 1], ay[MODE == kModeScreen ? R : 1], az[MODE == kModeScreen ? R : 1];
     unsigned long long px[PACKED ? R / 2 : 1], py[PACKED ? R / 2 : 1], pz[PACKED ? R / 2 : 1];
     double dx[PLAIN ? R : 1], dy[PLAIN ? R : 1], dz[PLAIN ? R : 1];
     uint32_t ibase = 0;
-    unsigned long long pairs = 0;
-    BandStats bs = {0ull, 0ull};
-    bool auto_mode = false, aborted = false;
-    uint32_t na = 0, nb = 0;
-    const Point64* a64 = nullptr;
-    const Point64* b64 = nullptr;
+    bool aborted = false;
 
     uint32_t seq = 0;
     while (cons.valid) {
@@ -614,32 +649,25 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             // ---- new item (warp-uniform: every warp walks the same tiles)
             const SubProblem& sp = sub_of(wd, cons.sub);
             if (cons.sub != cur_sub) {
-                if (cur_hist != nullptr) {
-                    if constexpr (!PLAIN) drain<T>(sctx, hcol, bs);
-                    if (sp.hist != cur_hist) {
-                        warp_flush_hist<T>(hist, ne, cur_hist);
+                if (cur_sub >= 0) {
+                    if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
+                    if (sp.hist != sub_of(wd, cur_sub).hist) {
+                        warp_flush_hist<T>(hc, wd.ne, sub_of(wd, cur_sub).hist);
                         j_since_flush = 0;
                     }
                 }
                 cur_sub = cons.sub;
-                cur_hist = sp.hist;
-                auto_mode = sp.auto_mode != 0;
-                na = sp.na;
-                nb = sp.nb;
-                a64 = sp.a64;
-                b64 = sp.b64;
-                sctx.na = na;
-                sctx.a64 = a64;
-                sctx.b64 = b64;
             }
-            const uint64_t item_j = (uint64_t)(cons.g.t_end - cons.g.t_first) * J;
-            if (j_since_flush + item_j > flush_limit) {
-                if constexpr (!PLAIN) drain<T>(sctx, hcol, bs);
-                warp_flush_hist<T>(hist, ne, cur_hist);
+            const uint32_t item_j = (cons.g.t_end - cons.g.t_first) * wd.J;
+            if (j_since_flush + item_j > wd.flush_limit) {
+                if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
+                warp_flush_hist<T>(hc, wd.ne, sp.hist);
                 j_since_flush = 0;
             }
             j_since_flush += item_j;
-            if (tid == 0) pairs += item_pairs(cons.g, na, nb, auto_mode, (uint32_t)I, wd.Jc);
+            if (tid == 0)
+                atomicAdd(wd.stats + kStatPairs,
+                          (unsigned long long)item_pairs(cons.g, sp.na, sp.nb, sp.auto_mode != 0, wd.I, wd.Jc));
             ibase = cons.g.i0 + (uint32_t)warp * (32u * R) + (uint32_t)lane;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -671,8 +699,8 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         }
 
         // ---- wait for this tile
-        const uint32_t stage = seq % (uint32_t)S;
-        const bool ok = mbar_wait_bounded(&bars[stage], (seq / (uint32_t)S) & 1u, wd.wait_limit_ns);
+        const uint32_t stage = seq % S;
+        const bool ok = mbar_wait_bounded(&bars[stage], (seq / S) & 1u, wd.wait_limit_ns);
         if (__any_sync(0xffffffffu, !ok)) {
             if (lane == 0) {
                 ctl[kCtlAbort] = 1;
@@ -683,76 +711,70 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         }
         if (ctl[kCtlAbort]) { aborted = true; break; }
 
-        const uint32_t jbase = cons.g.j0 + cons.t * (uint32_t)J;
-        const bool masked = auto_mode && (jbase < cons.g.i0 + (uint32_t)I);
+        const uint32_t jbase = cons.g.j0 + cons.t * wd.J;
+        const bool masked = sub_of(wd, cur_sub).auto_mode != 0 && (jbase < cons.g.i0 + wd.I);
+        const int J = (int)wd.J;
         if constexpr (PACKED) {
-            const float4* sj = (const float4*)(smem + L.stage + stage * stage_bytes);  // 2 per point
-            const unsigned long long nt2 = pack2(neg_fast_t, neg_fast_t);
-            // Fast loop with packed FMA: e for i-points (r, r + 1) in one fma.rn.f32x2;
-            // a j with some e >= 0 in the warp takes the inline slow path.
-#pragma unroll 1
-            for (int jj = 0; jj < J; ++jj) {
-                const ulonglong2 bxy = *reinterpret_cast<const ulonglong2*>(sj + 2 * jj);
-                const unsigned long long bz = *reinterpret_cast<const unsigned long long*>(sj + 2 * jj + 1);
-                float e[R];
-                int acc = -1;
-#pragma unroll
-                for (int p = 0; p < R / 2; ++p) {
-                    const unsigned long long v = ffma2(pz[p], bz, ffma2(py[p], bxy.y, ffma2(px[p], bxy.x, nt2)));
-                    e[2 * p] = lo_of(v);
-                    e[2 * p + 1] = hi_of(v);
-                    acc &= (int)(uint32_t)v & (int)(uint32_t)(v >> 32);
-                }
-                if (__any_sync(0xffffffffu, acc >= 0)) {
-                    const uint32_t jg = jbase + (uint32_t)jj;
-                    slow_e<T, R>(e, ibase, jg, !need_idx || jg < nb, masked, sctx, hcol, bs);
-                }
-            }
-        } else if constexpr (MODE == kModeScreen) {
-            const float4* sj = (const float4*)(smem + L.stage + stage * stage_bytes);
-            // Fast loop: e = FP32 dot minus the range offset T for R i-points; the AND
-            // of the R sign bits is negative when every pair is certainly overflow.
-            // A j with some e >= 0 in the warp takes the inline slow path.
-            // j-points per group: the group's screen values stay in registers until
-            // the slow path has used them (2 x R at 512 threads, 4 x R below)
-            constexpr int U = T >= 512 ? 2 : 4;
+            // Fast loop with packed FMA: one fma.rn.f32x2 gives the screen values of
+            // i-points (r, r + 1); j-points are staged as (x,x,y,y),(z,z,0,0).
+            // Groups of U j as in the scalar loop.
+            const float4* sj = sptr<const float4>(wd.off_stage + stage * wd.stage_bytes);  // 2 per point
+            const unsigned long long nt2 = pack2(wd.neg_fast_t, wd.neg_fast_t);
+            constexpr int U = 4;
 #pragma unroll 1
             for (int jj = 0; jj < J; jj += U) {
                 float eu[U][R];
-                uint32_t skip = 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const ulonglong2 bxy = *reinterpret_cast<const ulonglong2*>(sj + 2 * (jj + u));
+                    const unsigned long long bz = *reinterpret_cast<const unsigned long long*>(sj + 2 * (jj + u) + 1);
+#pragma unroll
+                    for (int p = 0; p < R / 2; ++p) {
+                        const unsigned long long v = ffma2(pz[p], bz, ffma2(py[p], bxy.y, ffma2(px[p], bxy.x, nt2)));
+                        eu[u][2 * p] = lo_of(v);
+                        eu[u][2 * p + 1] = hi_of(v);
+                    }
+                }
+                if (!__any_sync(0xffffffffu, and_tree<U * R>(&eu[0][0]) >= 0)) continue;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float4 bxy = sj[2 * (jj + u)], bzz = sj[2 * (jj + u) + 1];
+                    slow_j<T, R>(wd, cur_sub, eu[u], make_float4(bxy.x, bxy.z, bzz.x, 0.f), ibase,
+                                 jbase + (uint32_t)(jj + u), masked, hc);
+                }
+                maybe_drain<T>(wd, cur_sub, hc);
+            }
+        } else if constexpr (MODE == kModeScreen) {
+            const float4* sj = sptr<const float4>(wd.off_stage + stage * wd.stage_bytes);
+            // Fast loop: e = FP32 dot minus the range offset T for R i-points; the AND
+            // of the group's sign bits is negative when every pair is certainly
+            // overflow.  A group with some e >= 0 in the warp takes the slow path.
+            // j-points per group: the group's screen values stay in registers until
+            // the slow path has used them (2 x R at 512 threads, 4 x R below)
+            constexpr int U = R >= 16 ? 2 : 4;
+#pragma unroll 1
+            for (int jj = 0; jj < J; jj += U) {
+                float eu[U][R];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const float4 b = sj[jj + u];
-                    int acc = -1;
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        eu[u][r] = fmaf(az[r], b.z, fmaf(ay[r], b.y, fmaf(ax[r], b.x, neg_fast_t)));
-                        acc &= __float_as_int(eu[u][r]);
-                    }
-                    skip = __funnelshift_l((uint32_t)acc, skip, 1);  // (skip << 1) | sign(acc)
+                    for (int r = 0; r < R; ++r)
+                        eu[u][r] = fmaf(az[r], b.z, fmaf(ay[r], b.y, fmaf(ax[r], b.x, wd.neg_fast_t)));
                 }
-                const uint32_t need = ~skip & ((1u << U) - 1u);
-                if (!__any_sync(0xffffffffu, need != 0u)) continue;
-                uint32_t todo = __reduce_or_sync(0xffffffffu, need);
-                do {
-                    // bit U-1-u stands for j = jj + u; u is warp-uniform
-                    const int bit = 31 - __clz(todo);
-                    todo &= ~(1u << bit);
-                    const int u = U - 1 - bit;
-                    float e[R];
+                // AND of the group's screen values (a balanced tree, not a serial
+                // chain in front of the vote): negative when every pair is overflow
+                if (!__any_sync(0xffffffffu, and_tree<U * R>(&eu[0][0]) >= 0)) continue;
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        e[r] = eu[0][r];
-#pragma unroll
-                        for (int uu = 1; uu < U; ++uu)
-                            if (u == uu) e[r] = eu[uu][r];
-                    }
-                    const uint32_t jg = jbase + (uint32_t)(jj + u);
-                    slow_e<T, R>(e, ibase, jg, !need_idx || jg < nb, masked, sctx, hcol, bs);
-                } while (todo);
+                for (int u = 0; u < U; ++u)
+                    slow_j<T, R>(wd, cur_sub, eu[u], sj[jj + u], ibase, jbase + (uint32_t)(jj + u), masked, hc);
+                maybe_drain<T>(wd, cur_sub, hc);
             }
         } else {
-            const Point64* sj = (const Point64*)(smem + L.stage + stage * stage_bytes);
+            const Point64* sj = sptr<const Point64>(wd.off_stage + stage * wd.stage_bytes);
+            const double* cthr = sptr<const double>(wd.off_cthr);
+            const uint32_t na = sub_of(wd, cur_sub).na, nb = sub_of(wd, cur_sub).nb;
+            const int ne = wd.ne;
             for (int jj = 0; jj < J; ++jj) {
                 const Point64 b = sj[jj];
                 const uint32_t jg = jbase + (uint32_t)jj;
@@ -760,7 +782,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                 for (int r = 0; r < R; ++r) {
                     const double d = __dadd_rn(__dadd_rn(__dmul_rn(dx[r], b.x), __dmul_rn(dy[r], b.y)),
                                                __dmul_rn(dz[r], b.z));
-                    if (d > cos_last) {
+                    if (d > wd.cos_last) {
                         const uint32_t ig = ibase + 32u * r;
                         if (ig < na && jg < nb && (!masked || jg > ig)) {
                             // h = number of edges m with d <= C_m (C decreasing)
@@ -769,7 +791,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                                 const int mid = (lo + hi) >> 1;
                                 if (cthr[mid] >= d) lo = mid + 1; else hi = mid;
                             }
-                            hist_inc<T>(hcol, lo);
+                            hist_inc<T>(hc, lo);
                         }
                     }
                 }
@@ -779,6 +801,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         // ---- release the stage; the last warp to release refills it with tile seq + S
         __syncwarp();
         if (lane == 0) {
+            Cursor* prod = sptr<Cursor>(wd.off_prod + (uint32_t)warp * kCursorBytes);
             __threadfence_block();
             const int old = atomicAdd((int*)&ctl[kCtlRelease + stage], 1);
             if (old == W - 1) {
@@ -786,28 +809,20 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                 ctl[kCtlRelease + stage] = 0;
                 if (prod->valid && !ctl[kCtlAbort]) {
                     fence_proxy_async_smem();
-                    issue(seq + (uint32_t)S, *prod);
+                    issue(seq + S, *prod);
                     atomicAdd((int*)&ctl[kCtlIssued], 1);
                 }
             }
+            cursor_next(wd, *prod);
         }
         ++seq;
         cursor_next(wd, cons);
-        if (lane == 0) cursor_next(wd, *prod);
     }
 
     // ---- merge this warp's columns (skipped after an abort: outputs are invalid)
-    if (!aborted && cur_hist != nullptr) {
-        if constexpr (!PLAIN) drain<T>(sctx, hcol, bs);
-        warp_flush_hist<T>(hist, ne, cur_hist);
-        if constexpr (!PLAIN) {
-            const unsigned long long b = warp_sum(bs.band), m = warp_sum(bs.mismatch);
-            if (lane == 0) {
-                if (b) atomicAdd(wd.stats + kStatBand, b);
-                if (m) atomicAdd(wd.stats + kStatMismatch, m);
-            }
-        }
-        if (tid == 0) atomicAdd(wd.stats + kStatPairs, pairs);
+    if (!aborted && cur_sub >= 0) {
+        if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
+        warp_flush_hist<T>(hc, wd.ne, sub_of(wd, cur_sub).hist);
     }
     __syncwarp();
     if (lane == 0) {
@@ -822,10 +837,10 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         __threadfence_block();
         if (ctl[kCtlAbort]) {
             const uint32_t issued = (uint32_t)ctl[kCtlIssued];
-            const uint32_t first = issued > (uint32_t)S ? issued - (uint32_t)S : 0u;
+            const uint32_t first = issued > S ? issued - S : 0u;
             for (uint32_t s2 = first; s2 < issued; ++s2) {
                 if ((wd.flags & TPCF_F_TEST_WAIT_TIMEOUT) && s2 == 0) continue;
-                (void)mbar_wait_bounded(&bars[s2 % (uint32_t)S], (s2 / (uint32_t)S) & 1u, wd.wait_limit_ns);
+                (void)mbar_wait_bounded(&bars[s2 % S], (s2 / S) & 1u, wd.wait_limit_ns);
             }
         }
     }
@@ -919,28 +934,40 @@ __device__ __forceinline__ uint32_t cell_key(double x, double y, double z) {
     return (face << 28) | (spread14((uint32_t)qu) << 1) | spread14((uint32_t)qv);
 }
 
+// Sort keys and validation; eps_word receives the largest | |v|^2 - 1 | (as
+// the bits of a non-negative double, whose order is that of the integers).
 __global__ void prep_keys_kernel(const double* __restrict__ xyz, uint32_t n,
                                  const uint32_t* __restrict__ seg_of_point, int sort,
                                  unsigned long long* keys, uint32_t* vals, uint32_t n_pow2,
-                                 unsigned long long* err_word) {
+                                 unsigned long long* err_word, unsigned long long* eps_word) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_pow2) return;
+    if (i >= n_pow2) return;  // n_pow2 is a multiple of the block size: whole warps leave
+    double eps = 0.0;
     if (i >= n) {
         keys[i] = ~0ull;
         vals[i] = 0xffffffffu;
-        return;
+    } else {
+        const double x = xyz[3ull * i], y = xyz[3ull * i + 1], z = xyz[3ull * i + 2];
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+        const bool finite = isfinite(x) && isfinite(y) && isfinite(z);
+        // | |v| - 1 | <= 1e-6  <=>  r2 in [(1 - 1e-6)^2, (1 + 1e-6)^2]
+        if (!finite || !(r2 >= 0.999998000001 && r2 <= 1.000002000001)) {
+            atomicOr(err_word, (unsigned long long)kErrBadPoint);
+        } else {
+            eps = fabs(r2 - 1.0);
+        }
+        const unsigned long long seg = seg_of_point ? seg_of_point[i] : 0u;
+        const uint32_t ck = (sort && finite) ? cell_key(x, y, z) : 0u;
+        keys[i] = (seg << 32) | ck;
+        vals[i] = i;
     }
-    const double x = xyz[3ull * i], y = xyz[3ull * i + 1], z = xyz[3ull * i + 2];
-    const double r2 = x * x + y * y + z * z;
-    const bool finite = isfinite(x) && isfinite(y) && isfinite(z);
-    // | |v| - 1 | <= 1e-6  <=>  r2 in [(1 - 1e-6)^2, (1 + 1e-6)^2]
-    if (!finite || !(r2 >= 0.999998000001 && r2 <= 1.000002000001)) {
-        atomicOr(err_word, (unsigned long long)kErrBadPoint);
+    unsigned long long eb = (unsigned long long)__double_as_longlong(eps);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, eb, o);
+        eb = v > eb ? v : eb;
     }
-    const unsigned long long seg = seg_of_point ? seg_of_point[i] : 0u;
-    const uint32_t ck = (sort && finite) ? cell_key(x, y, z) : 0u;
-    keys[i] = (seg << 32) | ck;
-    vals[i] = i;
+    if ((threadIdx.x & 31) == 0 && eb != 0) atomicMax(eps_word, eb);
 }
 
 __device__ __forceinline__ bool kv_greater(unsigned long long ka, uint32_t va, unsigned long long kb,
@@ -1023,8 +1050,31 @@ __global__ void prep_gather_kernel(const double* __restrict__ xyz, uint32_t n,
 }
 
 // ============================================================== launchers
+// Fills the block constants of the work description (shared-memory offsets of
+// the shape, merge interval) and launches.
 template <int T, int R, int MODE>
-static cudaError_t launch_t(const WorkDesc& wd, const Shape& sh, cudaStream_t stream) {
+static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t stream) {
+    WorkDesc wd = wd_in;
+    const SmemLayout L = smem_layout(MODE, T, (int)wd.J, (int)wd.stages, wd.nedges_max);
+    wd.off_bars = L.bars;
+    wd.off_ctl = L.ctl;
+    wd.off_stage = L.stage;
+    wd.off_hist = L.hist;
+    wd.off_cthr = L.cos_thr;
+    wd.off_lo = L.lo;
+    wd.off_hi = L.hi;
+    wd.off_c32 = L.cos32;
+    wd.off_zlo = L.zlo;
+    wd.off_zhi = L.zhi;
+    wd.off_lut = L.lut;
+    wd.off_queue = L.queue;
+    wd.off_prod = L.prod;
+    wd.stage_bytes = wd.J * (MODE == kModeScreen ? 16u : 32u);
+    // 16-bit counters: a lane adds at most R per j to one row plus at most 2 per
+    // queue drain (at most one drain per slow j), so merging every
+    // 65535 / (R + 2) - J j-points keeps every counter below 2^16
+    wd.flush_limit = 0xffffu / (uint32_t)(R + 2) - wd.J;
+    if (L.total > sh.smem) return cudaErrorInvalidValue;
     count_kernel<T, R, MODE><<<sh.blocks, T, sh.smem, stream>>>(wd);
     return cudaGetLastError();
 }
@@ -1092,12 +1142,13 @@ cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long l
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
                            int sort, Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
                            unsigned long long* keys, uint32_t* vals, uint32_t n_pow2,
-                           unsigned long long* err_word, cudaStream_t stream, uint32_t* launches) {
+                           unsigned long long* err_word, unsigned long long* eps_word, cudaStream_t stream,
+                           uint32_t* launches) {
     cudaError_t e;
     uint32_t nl = 0;
     if (n > 0) {
         prep_keys_kernel<<<(n_pow2 + 255) / 256, 256, 0, stream>>>(xyz_in, n, seg_of_point, sort,
-                                                                    keys, vals, n_pow2, err_word);
+                                                                    keys, vals, n_pow2, err_word, eps_word);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

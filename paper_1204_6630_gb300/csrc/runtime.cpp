@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <string>
@@ -159,18 +160,6 @@ double dfromkey(int64_t k) {
     return d;
 }
 
-int32_t fkey(float v) {
-    int32_t b;
-    memcpy(&b, &v, 4);
-    return b >= 0 ? b : -(b & 0x7fffffff);
-}
-
-float ffromkey(int64_t k) {
-    uint32_t b = k >= 0 ? (uint32_t)k : ((uint32_t)(-k) | 0x80000000u);
-    float f;
-    memcpy(&f, &b, 4);
-    return f;
-}
 
 // The oracle's predicate for one pair and one edge: theta >= t with
 // theta = acos(clamp(d, -1, 1)) from the host C library.
@@ -265,40 +254,75 @@ void derive_e_space(const std::vector<double>& C, float T, double g, std::vector
     }
 }
 
-// LUT over e >= 0, indexed by the bits of RN(1 + e): idx = (bits(1 + e) -
-// bits(1)) >> shift, at most kLutMax entries.  Entry k covers keys
-// [key0 + (k << shift), key0 + ((k + 1) << shift) - 1]; the e values that round
-// into that range lie within one ulp of (value - 1), so the entry stores
-// P = #{m : e_max < elo_m} and Q = #{m : e_min <= ehi_m} for the widened range.
-// The last entry also covers every larger e and stores P = 0.
-void build_lut(const std::vector<float>& elo, const std::vector<float>& ehi, float T,
-               std::vector<uint32_t>& lut, int32_t* key0_out, int* shift_out) {
+// Chord-space bounds for the refinement of unsettled pairs.  The kernel
+// computes z = fl32(|a' - b'|^2) from the FP32 copies a', b' (differences,
+// then fl(fma(dz,dz, fma(dy,dy, dx*dx)))).  With Z = 2 (1 - d) (d the binary64
+// dot product) and | |v|^2 - 1 | <= eps for every point:
+//   |z - Z| <= delta(Z) = 4u(1 + 1e-6) s + (5u + 10u^2)(s + 2.01u)^2 + 4.1u^2
+//                         + 2 eps + 6.7e-16,   s = sqrt(Z + 2 eps + 7e-16):
+// input rounding moves a - b by at most 2u(1 + eps) (so |a-b|^2 by 4u|a-b| +
+// 4u^2), the subtractions and the three roundings of the non-negative sum
+// give a relative 5u, |a - b|^2 = Z + eps_a + eps_b - 2 (D - d), and the
+// binary64 dot d is within 3.4e-16 of the exact D.  Edge k is crossed
+// (theta >= t_k) iff Z >= Z_k = 2 (1 - C_k); with g_k >= delta(Z_k),
+// z >= zhi_k = RU(Z_k + g_k) proves Z >= Z_k (else z <= Z + delta(Z) <
+// Z_k + g_k), and z < zlo_k = RD(Z_k - g_k) proves Z < Z_k (Z - delta(Z) is
+// increasing for Z >= 1e-12; smaller Z_k get no lower bound).
+void derive_chord_space(const std::vector<double>& C, std::vector<float>& zlo, std::vector<float>& zhi) {
+    const int ne = (int)C.size();
+    const double u = kUnit, eps = kChordEpsRef;
+    zlo.resize(ne); zhi.resize(ne);
+    auto delta = [&](double Z) {
+        const double sq = std::sqrt(Z + 2.0 * eps + 7e-16) * (1.0 + 1e-15);
+        const double t = sq + 2.01 * u;
+        return 4.0 * u * (1.0 + 1e-6) * sq + (5.0 * u + 10.0 * u * u) * t * t + 4.1 * u * u + 2.0 * eps + 6.7e-16;
+    };
+    for (int k = 0; k < ne; ++k) {
+        if (std::isinf(C[k])) {  // t_k = 0: every pair crosses it
+            zlo[k] = zhi[k] = -INFINITY;
+            continue;
+        }
+        double Zd = 2.0 * (1.0 - C[k]), Zu = Zd;
+        if (C[k] < 0.5) {  // 1 - C may round (it is exact by Sterbenz's lemma for C >= 1/2)
+            Zd = std::nextafter(Zd, -INFINITY);
+            Zu = std::nextafter(Zu, INFINITY);
+        }
+        const double g = delta(Zu) * (1.0 + 1e-9);
+        zhi[k] = round_up_f32(Zu + g);
+        zlo[k] = Zd < 1e-12 ? -1.0f : round_down_f32(Zd - g);
+    }
+}
+
+// Exponent q of the LUT span: the smallest q with 2^q >= e_top, where e_top
+// bounds every screen value: |d| <= (1 + 1e-6)^2 for validated points, plus
+// the screen error and the offset margin.
+int lut_span_exponent(double e_top) {
+    int q = -30;
+    while (std::ldexp(1.0, q) < e_top) ++q;
+    return q;
+}
+
+// LUT over the screen value e.  The kernel computes
+//   k = rne(sat(e * 2^-q) * 2^14)       (exact scaling by powers of two)
+// so cell k holds every e in [(k - 1/2) w, (k + 1/2) w] with w = 2^(q - 14),
+// cell 0 also every e <= 0 (saturation; also NaN) and the last cell every
+// e >= 2^q.  Entry k stores P = #{m : e_max < elo_m} (edges certainly
+// crossed by every e of the cell) and Q = #{m : e_min <= ehi_m} (edges
+// possibly crossed); P == Q settles the histogram index of the whole cell.
+void build_lut(const std::vector<float>& elo, const std::vector<float>& ehi, int q, std::vector<uint32_t>& lut) {
     const int ne = (int)elo.size();
-    const int64_t key0 = fkey(1.0f);
-    const double e_top = (1.0 + 1e-6) - (double)T;  // d <= 1 + 1e-15, plus the error bound
-    const int64_t key_hi = (int64_t)fkey(round_up_f32(1.0 + e_top)) + 64;
-    const int64_t span = key_hi - key0 + 1;
-    int shift = 0;
-    while (((span - 1) >> shift) + 1 > kLutMax) ++shift;
-    const int nlut = (int)(((span - 1) >> shift) + 1);
-    lut.assign(nlut, 0);
-    auto ulp_above = [](float v) { return (double)nextafterf(v, INFINITY) - (double)v; };
-    for (int e = 0; e < nlut; ++e) {
-        const int64_t ka = key0 + ((int64_t)e << shift);
-        const int64_t kb = std::min(key0 + (((int64_t)e + 1) << shift) - 1, key_hi);
-        const float va = ffromkey(ka), vb = ffromkey(kb);
-        const double e_min = ((double)va - 1.0) - ulp_above(va);
-        const double e_max = ((double)vb - 1.0) + ulp_above(vb);
+    const double w = std::ldexp(1.0, q - kLutBits);
+    lut.assign(kLutCells, 0);
+    for (int k = 0; k < kLutCells; ++k) {
+        const double e_min = k == 0 ? -INFINITY : (k - 0.5) * w;
+        const double e_max = k == kLutCells - 1 ? INFINITY : (k + 0.5) * w;
         uint32_t P = 0, Q = 0;
         for (int m = 0; m < ne; ++m) {
             P += (e_max < (double)elo[m]);
             Q += (e_min <= (double)ehi[m]);
         }
-        if (e == nlut - 1) P = 0;
-        lut[e] = P | (Q << 16);
+        lut[k] = P | (Q << 16);
     }
-    *key0_out = (int32_t)key0;
-    *shift_out = shift;
 }
 
 }  // namespace
@@ -347,18 +371,29 @@ int tpcf::bins_create_impl(tpcf_ctx* ctx, const double* edges, int nedges, cudaS
     b->free_stream = st;
     b->edges.assign(edges, edges + nedges);
     derive_all(edges, nedges, ctx->cfg.guard_band, b->cos_thr, b->lo, b->hi, b->c32, b->verified);
-    // screen offset T: the fast test fma(az,bz, fma(ay,by, fma(ax,bx, -T))) has
-    // error <= 8.0003u against d - T (2u input rounding, 3 roundings of terms
-    // bounded by |T| + 1), so a negative value means d < T + 8.0003u <= C_B.
-    const float T = round_down_f32(b->cos_thr[nedges - 1] - 10.0 * kUnit);
+    // Screen offset T: the fast test fma(az,bz, fma(ay,by, fma(ax,bx, -T))) has
+    // error <= 8.0003u + 3u (|T| - 1)+ against d - T (2u input rounding, three
+    // roundings of terms bounded by |T| + 1), below the guard band g >= 9u, so
+    // a negative value means d < T + g <= C_B.  T = RD(C_B - g - u - w) sits
+    // one LUT cell w below that bound so that LUT cell 0, which also receives
+    // every e < 0, lies wholly beyond the last edge (e_max of cell 0 = w / 2 <
+    // w <= elo_B = RD(C_B - T - g)) and settles as overflow.
+    const double C_B = b->cos_thr[nedges - 1];
+    const double g = ctx->cfg.guard_band;
+    int q = lut_span_exponent(1.0 + 3e-6 - C_B + g + 2.0 * kUnit);
+    float T = 0.f;
+    for (;; ++q) {
+        T = round_down_f32(C_B - g - kUnit - std::ldexp(1.0, q - kLutBits));
+        if (std::ldexp(1.0, q) >= 1.0 + 3e-6 + 12.0 * kUnit - (double)T) break;
+    }
     derive_e_space(b->cos_thr, T, ctx->cfg.guard_band, b->elo, b->ehi, b->ec);
-    int32_t key0;
-    int shift;
-    build_lut(b->elo, b->ehi, T, b->lut, &key0, &shift);
-    // one device buffer: C (double), lo, hi, c32 (float), lut (uint32), then the descriptor
+    build_lut(b->elo, b->ehi, q, b->lut);
+    derive_chord_space(b->cos_thr, b->zlo, b->zhi);
+    // one device buffer: C (double), lo, hi, c32, zlo, zhi (float), lut (uint32), then the descriptor
     const size_t nd = (size_t)nedges * 8, nf = (size_t)nedges * 4, nl = b->lut.size() * 4;
-    const size_t off_lo = (nd + 15) / 16 * 16, off_hi = off_lo + (nf + 15) / 16 * 16,
-                 off_c32 = off_hi + (nf + 15) / 16 * 16, off_lut = off_c32 + (nf + 15) / 16 * 16,
+    const size_t nf16 = (nf + 15) / 16 * 16;
+    const size_t off_lo = (nd + 15) / 16 * 16, off_hi = off_lo + nf16, off_c32 = off_hi + nf16,
+                 off_zlo = off_c32 + nf16, off_zhi = off_zlo + nf16, off_lut = off_zhi + nf16,
                  off_desc = (off_lut + nl + 255) / 256 * 256, total = off_desc + sizeof(BinsDev);
     auto cleanup = [&](int code) {
         bins_destroy_impl(b);
@@ -372,10 +407,10 @@ int tpcf::bins_create_impl(tpcf_ctx* ctx, const double* edges, int nedges, cudaS
     b->host.hi = (const float*)(base + off_hi);
     b->host.cos32 = (const float*)(base + off_c32);
     b->host.lut = (const uint32_t*)(base + off_lut);
+    b->host.zlo = (const float*)(base + off_zlo);
+    b->host.zhi = (const float*)(base + off_zhi);
     b->host.nedges = nedges;
-    b->host.nlut = (int)b->lut.size();
-    b->host.lut_shift = shift;
-    b->host.lut_key0 = key0;
+    b->host.lut_scale = (float)std::ldexp(1.0, -q);
     b->host.range_t = b->elo[nedges - 1];
     b->host.fast_t = T;
     b->host.cos_last = b->cos_thr[nedges - 1];
@@ -386,6 +421,8 @@ int tpcf::bins_create_impl(tpcf_ctx* ctx, const double* edges, int nedges, cudaS
     memcpy(hs + off_lo, b->elo.data(), nf);
     memcpy(hs + off_hi, b->ehi.data(), nf);
     memcpy(hs + off_c32, b->ec.data(), nf);
+    memcpy(hs + off_zlo, b->zlo.data(), nf);
+    memcpy(hs + off_zhi, b->zhi.data(), nf);
     memcpy(hs + off_lut, b->lut.data(), nl);
     memcpy(hs + off_desc, &b->host, sizeof(BinsDev));
     const cudaError_t e = stream_ordered
@@ -489,11 +526,11 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
             return fail_with(TPCF_ECUDA, "host-to-device copy failed");
         in = (const double*)tmp_in;
     }
-    if (cudaMallocAsync((void**)&err, 8, st) != cudaSuccess ||
+    if (cudaMallocAsync((void**)&err, 16, st) != cudaSuccess ||
         cudaMallocAsync((void**)&keys, (size_t)n_pow2 * 8, st) != cudaSuccess ||
         cudaMallocAsync((void**)&vals, (size_t)n_pow2 * 4, st) != cudaSuccess)
         return fail_with(TPCF_ENOMEM, "scratch allocation failed");
-    if (cudaMemsetAsync(err, 0, 8, st) != cudaSuccess) return fail_with(TPCF_ECUDA, "memset failed");
+    if (cudaMemsetAsync(err, 0, 16, st) != cudaSuccess) return fail_with(TPCF_ECUDA, "memset failed");
     if (nseg > 0 && n > 0) {
         std::vector<uint32_t> hs(n);
         for (int s = 0; s < nseg; ++s)
@@ -506,13 +543,17 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
     }
     uint32_t nl = 0;
     cudaError_t e = launch_prepare(in, (uint32_t)n, seg, sort ? 1 : 0, c->d64, c->d32, c->d32x2, c->n_pad, keys,
-                                   vals, n_pow2, err, st, &nl);
+                                   vals, n_pow2, err, err + 1, st, &nl);
     ctx->launches.fetch_add(nl);
     if (e != cudaSuccess) return fail_with(TPCF_ECUDA, cudaGetErrorString(e));
-    unsigned long long herr = 0;
-    if (cudaMemcpyAsync(&herr, err, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    unsigned long long hw[2] = {0, 0};
+    if (cudaMemcpyAsync(hw, err, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail_with(TPCF_ECUDA, "preparation failed");
+    const unsigned long long herr = hw[0];
+    double eps_dev;
+    memcpy(&eps_dev, &hw[1], 8);
+    c->eps_max = eps_dev + 4e-16;  // the device sum of squares is within 3.4e-16 of |v|^2
     if (herr & kErrBadPoint) {
         rc = TPCF_EINVAL;
         return fail_with(rc, "a point is not finite or not a unit vector (| |v| - 1 | > 1e-6)");
@@ -778,6 +819,16 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         wd.flags = ctx->cfg.flags;
         wd.force_idx = force_idx ? 1u : 0u;
         wd.nedges_max = ne;
+        wd.ne = ne;
+        wd.neg_fast_t = -bins->host.fast_t;
+        wd.lut_scale = bins->host.lut_scale;
+        wd.cos_last = bins->host.cos_last;
+        // zero-vector padding has screen value e = -T: it can look in range only
+        // when T <= 0; sub-ranges of segmented catalogs are followed by real points
+        wd.need_idx = (force_idx || !(bins->host.fast_t > 0.f)) ? 1u : 0u;
+        wd.chord_ok = 1u;
+        for (int s2 = 0; s2 < nsub; ++s2)
+            if (!(specs[s2].a->eps_max <= kChordEpsRef && specs[s2].b->eps_max <= kChordEpsRef)) wd.chord_ok = 0u;
         wd.wait_limit_ns = (uint64_t)ctx->cfg.wait_timeout_us * 1000ull;
         return TPCF_OK;
     };

@@ -11,8 +11,14 @@ namespace tpcf {
 // points; points past n are zero vectors (never counted, see kernels.cu).
 constexpr uint32_t kPad = 4096;
 
-// Lookup table from FP32 cosine to the candidate histogram index range.
-constexpr int kLutMax = 16384;
+// Lookup table from the FP32 screen value to the candidate histogram index
+// range: cell k = rne(sat(e * lut_scale) * 2^14), k = 0 .. 2^14.
+constexpr int kLutBits = 14;
+constexpr int kLutCells = (1 << kLutBits) + 1;
+
+// The chord refinement of unsettled pairs (kernels.cu, slow_j) is proven for
+// catalogs whose points satisfy | |v|^2 - 1 | <= kChordEpsRef.
+constexpr double kChordEpsRef = 0x1p-40;
 
 // Binary64 point (x, y, z, 0), 32-byte aligned for two 16-byte loads.
 struct __align__(32) Point64 {
@@ -29,11 +35,11 @@ struct BinsDev {
     const float* lo;        // [nedges] RD(C_k - T - g)   (e-space)
     const float* hi;        // [nedges] RU(C_k - T + g)   (e-space)
     const float* cos32;     // [nedges] RN(C_k - T): FP32-only classification (statistics)
-    const uint32_t* lut;    // [nlut] (P | Q << 16), indexed by bits(RN(1 + e)): see runtime.cpp
+    const uint32_t* lut;    // [kLutCells] (P | Q << 16) per cell of e: see runtime.cpp
+    const float* zlo;       // [nedges] chord-space bounds of Z_k = 2 (1 - C_k): z < zlo_k => not crossed
+    const float* zhi;       // [nedges]                                          z >= zhi_k => crossed
     int nedges;             // B + 1
-    int nlut;
-    int lut_shift;
-    int32_t lut_key0;       // bits(1.0f)
+    float lut_scale;        // 2^-q with 2^q >= every in-range e: cell width 2^(q - 14)
     float range_t;          // lo[B] in e-space
     float fast_t;           // T = RD(C_B - 10u): a screen value e < 0 is certainly overflow
     double cos_last;        // C_B (binary64 range limit, plain kernel)
@@ -81,6 +87,20 @@ struct WorkDesc {
     uint32_t force_idx;              // 1: always check indices (sub-ranges of segmented catalogs)
     int nedges_max;                  // largest B + 1 over the sub-problems (shared-memory sizing)
     uint64_t wait_limit_ns;          // bounded waits
+    // Block constants, read by the kernel straight from its parameter (no
+    // registers).  Bin scalars of the one bin set all sub-problems share
+    // (set by the runtime) ...
+    int ne;                          // B + 1
+    float neg_fast_t;                // -T (screen offset)
+    float lut_scale;                 // 2^-q (LUT span)
+    uint32_t need_idx;               // 1: check i < na, j < nb for every slow pair
+    uint32_t chord_ok;               // 1: every catalog of the launch has | |v|^2 - 1 | <= kChordEpsRef
+    double cos_last;                 // C_B (all-binary64 kernel)
+    // ... and the shared-memory layout of the shape (set by the launcher).
+    uint32_t off_bars, off_ctl, off_stage, off_hist, off_cthr, off_lo, off_hi, off_c32, off_zlo, off_zhi,
+        off_lut, off_queue, off_prod;
+    uint32_t stage_bytes;            // J * bytes per staged point
+    uint32_t flush_limit;            // j-points between merges of the 16-bit counters
 };
 
 // Kernel shape selected on the host.
@@ -111,8 +131,8 @@ cudaError_t launch_finalize_batch(const unsigned long long* acc, int acc_stride,
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
                            int sort, Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
                            unsigned long long* key_scratch, uint32_t* val_scratch,
-                           uint32_t n_pow2, unsigned long long* err_word, cudaStream_t stream,
-                           uint32_t* launches);
+                           uint32_t n_pow2, unsigned long long* err_word, unsigned long long* eps_word,
+                           cudaStream_t stream, uint32_t* launches);
 size_t count_smem_bytes(int mode, int threads, int ipt, int jtile, int stages, int nedges);
 bool count_shape_supported(int threads, int ipt);
 bool derive_cos_thresholds(const double* edges, int nedges, double* cos_thr);
