@@ -405,7 +405,7 @@ __device__ __forceinline__ float screen_value(const WorkDesc& wd, const SubProbl
     return fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, wd.neg_fast_t)));
 }
 
-// LUT entry of screen value e (see slow_j).
+// LUT entry of screen value e (see slow_group).
 __device__ __forceinline__ uint32_t lut_entry(const WorkDesc& wd, float e) {
     const float v = __saturatef(e * wd.lut_scale);
     const float f = fmaf(v, 16384.0f, 8388608.0f);
@@ -480,23 +480,23 @@ __device__ __forceinline__ void queue_pair(const WorkDesc& wd, int sub, uint32_t
         classify_now<T>(wd, sub, ig, jg, hc);
 }
 
-// An unsettled pair of the slow path: its screen value and LUT entry are
-// recomputed from the FP32 points (bit-identical; cheaper than indexing the
-// caller's register arrays), then the chord refinement decides the edges
-// the entry leaves open: z = fl32(|a' - b'|^2) is within 4u|a - b| + O(u
-// |a-b|^2) of 2 (1 - d) (bounds zlo, zhi: runtime.cpp), far tighter than the
-// screen value at the small and moderate angles of a histogram range.
-// Z-space bounds increase with the edge index, so a binary search over
-// [P, Q) finds nb = #{crossed}; the pair is settled when z is also below
-// zlo[nb].  Pairs left in a chord band (or catalogs outside the chord
-// bound's norm tolerance) are queued for the binary64 recheck.
+// An unsettled pair of the slow path (a = the i-point, b = the j-point, FP32):
+// its screen value and LUT entry are recomputed (bit-identical to the fast
+// loop's), then the chord refinement decides the edges the entry leaves
+// open: z = fl32(|a' - b'|^2) is within 4u|a - b| + O(u |a-b|^2) of
+// 2 (1 - d) (bounds zlo, zhi: runtime.cpp), far tighter than the screen
+// value at the small and moderate angles of a histogram range.  Z-space
+// bounds increase with the edge index, so a binary search over [P, Q) finds
+// nb = #{crossed}; the pair is settled when z is also below zlo[nb].  Pairs
+// left in a chord band (or catalogs outside the chord bound's norm
+// tolerance) are queued for the binary64 recheck.
 template <int T>
-__device__ __forceinline__ void unsettled_pair(const WorkDesc& wd, int sub, const float4 a, const float4& b,
-                                               uint32_t ig, uint32_t jg, const HistCol& hc) {
+__device__ __forceinline__ void unsettled_pair(const WorkDesc& wd, int sub, float ax, float ay, float az,
+                                               const float4& b, uint32_t ig, uint32_t jg, const HistCol& hc) {
     if (wd.chord_ok) {
-        const float e = fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, wd.neg_fast_t)));
+        const float e = fmaf(az, b.z, fmaf(ay, b.y, fmaf(ax, b.x, wd.neg_fast_t)));
         const uint32_t ent = lut_entry(wd, e);
-        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        const float dx = ax - b.x, dy = ay - b.y, dz = az - b.z;
         const float z = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float* zlo = sptr<const float>(wd.off_zlo);
         const float* zhi = sptr<const float>(wd.off_zhi);
@@ -514,49 +514,72 @@ __device__ __forceinline__ void unsettled_pair(const WorkDesc& wd, int sub, cons
     queue_pair<T>(wd, sub, ig, jg, hc);
 }
 
-// Slow path for one j (warp-uniform), all R pairs of every lane, branch-free:
-// the LUT cell of e is k = rne(sat(e * 2^-q) * 2^14), read as the low bits of
-// fma(v, 2^14, 2^23); a settled entry is the byte offset of the pair's row,
-// so the pair costs one shared load and one shared reduction.  All R loads are
-// issued before the first reduction (shared loads and reductions stay in
-// program order, so interleaving them would expose the load latency once per
-// pair).  Pairs beyond the range (e < 0 or in cell 0) land in the overflow
-// row, which is never merged; pairs that must not be counted (padding, j <= i
-// on the diagonal) are given e = -1 first.  Unsettled entries (bit 31) go
-// through unsettled_pair, one pair per iteration.
-template <int T, int R>
-__device__ __forceinline__ void slow_j(const WorkDesc& wd, int sub, float (&e)[R], const float4& b, uint32_t ibase,
-                                       uint32_t jg, bool masked, const HistCol& hc) {
+// Element k of a register array without dynamic indexing (no local memory).
+template <int R>
+__device__ __forceinline__ float pick(const float (&v)[R], int k) {
+    float x = v[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) x = (k == r) ? v[r] : x;
+    return x;
+}
+
+// Slow path for a group of U j (warp-uniform), all R pairs of every lane,
+// branch-free: the LUT cell of e is k = rne(sat(e * 2^-q) * 2^14), read as
+// the low bits of fma(v, 2^14, 2^23); a settled entry is the byte offset of
+// the pair's row, so the pair costs one shared load and one shared reduction.
+// Shared loads and reductions stay in program order, so the loads of j u + 1
+// are issued before the reductions of j u (software pipelining) to keep the
+// load latency off the critical path.  Pairs beyond the range (e < 0 or in
+// cell 0) land in the overflow row, which is never merged; pairs that must
+// not be counted (padding, j <= i on the diagonal) are given e = -1 first.
+// Unsettled entries (bit 31) go through unsettled_pair, one per iteration.
+template <int T, int R, int U, class JPoint>
+__device__ __forceinline__ void slow_group(const WorkDesc& wd, int sub, float (&e)[U][R], const float (&ax)[R],
+                                           const float (&ay)[R], const float (&az)[R], const JPoint& j_point, int jj,
+                                           uint32_t ibase, uint32_t jbase, bool masked, const HistCol& hc) {
+    static_assert(U * R <= 32, "one bit per pair of the group");
     if (wd.need_idx || masked) {
         const uint32_t na = sub_of(wd, sub).na, nb = sub_of(wd, sub).nb;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t ig = ibase + 32u * r;
-            const bool ok = (!wd.need_idx || (jg < nb && ig < na)) && (!masked || jg > ig);
-            if (!ok) e[r] = -1.0f;
+        for (int u = 0; u < U; ++u) {
+            const uint32_t jg = jbase + (uint32_t)(jj + u);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t ig = ibase + 32u * r;
+                const bool ok = (!wd.need_idx || (jg < nb && ig < na)) && (!masked || jg > ig);
+                if (!ok) e[u][r] = -1.0f;
+            }
         }
     }
     const uint32_t lut_adj = smem_addr(dyn_smem) + wd.off_lut - 0x4B000000u * 4u;  // + 4 bits(f): entry
-    uint32_t ent[R];
+    uint32_t ent[2][R];
+    uint32_t um = 0;  // unsettled pairs of this lane, bit u * R + r
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const float v = __saturatef(e[r] * wd.lut_scale);
-        const float f = fmaf(v, 16384.0f, 8388608.0f);
-        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(ent[r]) : "r"(__float_as_uint(f) * 4u + lut_adj));
-    }
-    uint32_t um = 0;  // unsettled pairs of this lane, bit r
+    for (int u = 0; u <= U; ++u) {
+        if (u < U) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if ((int)ent[r] >= 0) red_add_shared(hc.addr + ent[r], hc.inc);
-        um |= (ent[r] >> 31) << r;
+            for (int r = 0; r < R; ++r) {
+                const float v = __saturatef(e[u][r] * wd.lut_scale);
+                const float f = fmaf(v, 16384.0f, 8388608.0f);
+                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(ent[u & 1][r]) : "r"(__float_as_uint(f) * 4u + lut_adj));
+            }
+        }
+        if (u > 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t x = ent[(u - 1) & 1][r];
+                if ((int)x >= 0) red_add_shared(hc.addr + x, hc.inc);
+                um |= (x >> 31) << ((u - 1) * R + r);
+            }
+        }
     }
     if (__any_sync(0xffffffffu, um != 0u)) {
-        const float4* a32 = sub_of(wd, sub).a32;
         while (um) {  // one iteration per unsettled pair of the lane
-            const int r = __ffs(um) - 1;
+            const int k = __ffs(um) - 1;
             um &= um - 1;
-            const uint32_t ig = ibase + 32u * (uint32_t)r;
-            unsettled_pair<T>(wd, sub, __ldg(a32 + ig), b, ig, jg, hc);
+            const int u = k / R, r = k % R;
+            unsettled_pair<T>(wd, sub, pick(ax, r), pick(ay, r), pick(az, r), j_point(jj + u),
+                              ibase + 32u * (uint32_t)r, jbase + (uint32_t)(jj + u), hc);
         }
     }
 }
@@ -720,7 +743,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             // Groups of U j as in the scalar loop.
             const float4* sj = sptr<const float4>(wd.off_stage + stage * wd.stage_bytes);  // 2 per point
             const unsigned long long nt2 = pack2(wd.neg_fast_t, wd.neg_fast_t);
-            constexpr int U = 4;
+            constexpr int U = 32 / R;
 #pragma unroll 1
             for (int jj = 0; jj < J; jj += U) {
                 float eu[U][R];
@@ -736,12 +759,19 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                     }
                 }
                 if (!__any_sync(0xffffffffu, and_tree<U * R>(&eu[0][0]) >= 0)) continue;
+                float qx[R], qy[R], qz[R];  // the packed i-points as scalars (register halves)
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const float4 bxy = sj[2 * (jj + u)], bzz = sj[2 * (jj + u) + 1];
-                    slow_j<T, R>(wd, cur_sub, eu[u], make_float4(bxy.x, bxy.z, bzz.x, 0.f), ibase,
-                                 jbase + (uint32_t)(jj + u), masked, hc);
+                for (int p = 0; p < R / 2; ++p) {
+                    qx[2 * p] = lo_of(px[p]); qx[2 * p + 1] = hi_of(px[p]);
+                    qy[2 * p] = lo_of(py[p]); qy[2 * p + 1] = hi_of(py[p]);
+                    qz[2 * p] = lo_of(pz[p]); qz[2 * p + 1] = hi_of(pz[p]);
                 }
+                slow_group<T, R, U>(wd, cur_sub, eu, qx, qy, qz,
+                                    [&](int j) {
+                                        const float4 bxy = sj[2 * j], bzz = sj[2 * j + 1];
+                                        return make_float4(bxy.x, bxy.z, bzz.x, 0.f);
+                                    },
+                                    jj, ibase, jbase, masked, hc);
                 maybe_drain<T>(wd, cur_sub, hc);
             }
         } else if constexpr (MODE == kModeScreen) {
@@ -765,9 +795,8 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                 // AND of the group's screen values (a balanced tree, not a serial
                 // chain in front of the vote): negative when every pair is overflow
                 if (!__any_sync(0xffffffffu, and_tree<U * R>(&eu[0][0]) >= 0)) continue;
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    slow_j<T, R>(wd, cur_sub, eu[u], sj[jj + u], ibase, jbase + (uint32_t)(jj + u), masked, hc);
+                slow_group<T, R, U>(wd, cur_sub, eu, ax, ay, az, [&](int j) { return sj[j]; }, jj, ibase, jbase, masked,
+                                    hc);
                 maybe_drain<T>(wd, cur_sub, hc);
             }
         } else {
