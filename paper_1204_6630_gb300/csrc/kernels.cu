@@ -198,6 +198,7 @@ enum Ctl { kCtlAbort = 0, kCtlWarpsDone = 1, kCtlIssued = 2, kCtlRelease = 8, kC
            kCtlWords = 64 };
 constexpr int kMaxStages = 16;   // release counters live at kCtlRelease + stage
 constexpr int kQueuePerWarp = 64;   // band pairs per warp awaiting the binary64 recheck
+constexpr int kSlowPipe = 2;        // slow path: j-points whose LUT loads are in flight
 constexpr uint32_t kCursorBytes = 32;  // one producer cursor slot
 
 struct SmemLayout {
@@ -551,32 +552,33 @@ __device__ __forceinline__ void slow_group(const WorkDesc& wd, int sub, float (&
             }
         }
     }
+    constexpr int D = kSlowPipe;  // loads run D - 1 j ahead of the reductions
     const uint32_t lut_adj = smem_addr(dyn_smem) + wd.off_lut - 0x4B000000u * 4u;  // + 4 bits(f): entry
-    uint32_t ent[2][R];
-    uint32_t um = 0;  // unsettled pairs of this lane, bit u * R + r
+    uint32_t ent[D][R];
+    uint32_t um = 0;  // unsettled pairs of this lane: pair k = u * R + r at bit U * R - 1 - k
 #pragma unroll
-    for (int u = 0; u <= U; ++u) {
+    for (int u = 0; u < U + D - 1; ++u) {
         if (u < U) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const float v = __saturatef(e[u][r] * wd.lut_scale);
                 const float f = fmaf(v, 16384.0f, 8388608.0f);
-                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(ent[u & 1][r]) : "r"(__float_as_uint(f) * 4u + lut_adj));
+                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(ent[u % D][r]) : "r"(__float_as_uint(f) * 4u + lut_adj));
             }
         }
-        if (u > 0) {
+        if (u >= D - 1) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const uint32_t x = ent[(u - 1) & 1][r];
+                const uint32_t x = ent[(u - (D - 1)) % D][r];
                 if ((int)x >= 0) red_add_shared(hc.addr + x, hc.inc);
-                um |= (x >> 31) << ((u - 1) * R + r);
+                um = __funnelshift_l(x, um, 1);  // (um << 1) | (x >> 31)
             }
         }
     }
     if (__any_sync(0xffffffffu, um != 0u)) {
         while (um) {  // one iteration per unsettled pair of the lane
-            const int k = __ffs(um) - 1;
-            um &= um - 1;
+            const int k = U * R - 1 - (31 - __clz(um));
+            um &= ~(1u << (U * R - 1 - k));
             const int u = k / R, r = k % R;
             unsettled_pair<T>(wd, sub, pick(ax, r), pick(ay, r), pick(az, r), j_point(jj + u),
                               ibase + 32u * (uint32_t)r, jbase + (uint32_t)(jj + u), hc);
