@@ -274,8 +274,14 @@ def run_gpu(args):
     traffic = None
     prof = os.path.join(ROOT, "profiles", "count_kernel_traffic.json")
     if os.path.exists(prof):
+        # the recorded DRAM bytes count only while the kernel source is the one they were taken from
         try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+            import hashlib
+            rec = json.load(open(prof))
+            src = os.path.join(ROOT, "paper_1204_6630_gb300", "csrc", "kernels.cu")
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            if rec.get("kernel_source_sha256_16") == sha and args.n == 1_000_000:
+                traffic = rec.get("dram_bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
     cfg = workload_config(args.n, nbins)
