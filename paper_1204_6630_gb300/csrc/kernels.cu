@@ -122,14 +122,30 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     return d;
 }
 
-// AND of the bit patterns of N floats as a balanced tree (depth log N).
+// a & b & c in one three-input logic instruction.
+__device__ __forceinline__ uint32_t and3(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0x80;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// AND of the bit patterns of N floats as a tree of three-input ANDs.
+template <int N>
+__device__ __forceinline__ uint32_t and_tree3(const float* v) {
+    if constexpr (N == 1) {
+        return __float_as_uint(v[0]);
+    } else if constexpr (N == 2) {
+        return __float_as_uint(v[0]) & __float_as_uint(v[1]);
+    } else {
+        constexpr int A = N / 3, B = (N - A) / 2;
+        return and3(and_tree3<A>(v), and_tree3<B>(v + A), and_tree3<N - A - B>(v + A + B));
+    }
+}
+
+// Negative when every one of the N floats is negative (AND of the sign bits).
 template <int N>
 __device__ __forceinline__ int and_tree(const float* v) {
-    if constexpr (N == 1) {
-        return __float_as_int(v[0]);
-    } else {
-        return and_tree<N / 2>(v) & and_tree<N - N / 2>(v + N / 2);
-    }
+    return (int)and_tree3<N>(v);
 }
 
 // ============================================================== work cursor
