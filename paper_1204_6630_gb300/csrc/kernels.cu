@@ -805,7 +805,9 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             // j-points per group: the group's screen values stay in registers until
             // the slow path has used them (2 x R at 512 threads, 4 x R below)
             constexpr int U = R >= 16 ? 2 : 4;
-#pragma unroll 1
+            // two groups per iteration: the loop's own compare and branch once per
+            // 2U j (measured: more unrolling copies the slow path and loses)
+#pragma unroll 2
             for (int jj = 0; jj < J; jj += U) {
                 float eu[U][R];
 #pragma unroll
