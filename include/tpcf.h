@@ -86,7 +86,6 @@ extern "C" {
 
 /* configuration flags */
 #define TPCF_F_NO_SORT 0x1u          /* keep catalog order (no spatial sort on the device) */
-#define TPCF_F_DYNAMIC_SCHED 0x2u    /* persistent blocks take work from an atomic counter */
 #define TPCF_F_PACKED_FMA 0x4u       /* FP32 screen with packed FP32x2 FMA (fma.rn.f32x2) instead of scalar FMA */
 #define TPCF_F_AUTOTUNE 0x8u         /* the first counting call of a workload class times every kernel
                                         shape that fits and the context keeps the fastest */

@@ -411,7 +411,6 @@ int tpcf::bins_create_impl(tpcf_ctx* ctx, const double* edges, int nedges, cudaS
     b->host.zhi = (const float*)(base + off_zhi);
     b->host.nedges = nedges;
     b->host.lut_scale = (float)std::ldexp(1.0, -q);
-    b->host.range_t = b->elo[nedges - 1];
     b->host.fast_t = T;
     b->host.cos_last = b->cos_thr[nedges - 1];
     b->dev_desc = (BinsDev*)(base + off_desc);

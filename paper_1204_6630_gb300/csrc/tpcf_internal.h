@@ -40,7 +40,6 @@ struct BinsDev {
     const float* zhi;       // [nedges]                                          z >= zhi_k => crossed
     int nedges;             // B + 1
     float lut_scale;        // 2^-q with 2^q >= every in-range e: cell width 2^(q - 14)
-    float range_t;          // lo[B] in e-space
     float fast_t;           // T = RD(C_B - 10u): a screen value e < 0 is certainly overflow
     double cos_last;        // C_B (binary64 range limit, plain kernel)
 };
@@ -70,7 +69,7 @@ constexpr int kMaxInlineSub = 3;
 
 // Device statistics words (per call, in the scratch slot after the histograms).
 enum StatWord { kStatPairs = 0, kStatBand = 1, kStatMismatch = 2, kStatError = 3,
-                kStatWork = 4, kStatWords = 8 };
+                kStatWords = 8 };
 
 // Device error word bits.
 enum : uint32_t { kErrWaitTimeout = 1u, kErrBadHist = 2u, kErrBadPoint = 4u, kErrSortOverflow = 8u };

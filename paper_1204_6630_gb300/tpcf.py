@@ -30,7 +30,6 @@ TPCF_HOST, TPCF_DEVICE = 0, 1
 TPCF_SCREEN_RECHECK, TPCF_PLAIN_FP64 = 0, 1
 TPCF_LS_EXACT, TPCF_LS_PAPER = 0, 1
 TPCF_F_NO_SORT = 0x1
-TPCF_F_DYNAMIC_SCHED = 0x2
 TPCF_F_PACKED_FMA = 0x4
 TPCF_F_AUTOTUNE = 0x8
 TPCF_F_TEST_WAIT_TIMEOUT = 0x100
