@@ -253,6 +253,30 @@ int tpcf_graph_launch(tpcf_graph *graph, void *stream);
 int tpcf_graph_stats(tpcf_graph *graph, tpcf_stats *st);
 int tpcf_graph_destroy(tpcf_graph *graph);
 
+/* Leave-one-out jackknife over the P segments (sky patches) of two segmented
+ * catalogs with the same P: for each p the DD, DR and RR histograms of the
+ * catalogs with segment p removed (delete-one jackknife resampling of Eq. 1's
+ * counts; the paper gives no error estimate, this is the standard one built on
+ * its three histograms).  One persistent launch counts every pair of the full
+ * catalogs once more in each direction, attributing it to the patch of its
+ * first point, together with the per-patch counts of tpcf_count_patches;
+ * pairs touching patch p follow exactly, and X_{-p} = X - (pairs touching p).
+ *   loo:   P * 3 * (B + 2) host uint64, histogram (p, k) at (3 p + k) (B + 2),
+ *          k = 0 DD, 1 DR, 2 RR (layout above);
+ *   w_loo: P * B host doubles (may be NULL): w(theta) of each resampling with
+ *          N_D - n_p and N_R - m_p points (NaN where RR = 0 or fewer than 2
+ *          points remain), estimator as tpcf_estimate;
+ *   cov:   B * B host doubles (may be NULL): C_ab = (P - 1)/P sum_p
+ *          (w_pa - wbar_a)(w_pb - wbar_b), wbar the mean over p, sums in
+ *          patch order (NaN propagates).
+ * Synchronous in `stream`; st (may be NULL) gets the statistics of the launch
+ * with pairs = the real pairs counted.  Errors: TPCF_EINVAL for unsegmented
+ * catalogs or different P, cov with P < 2, an unknown estimator, or a last
+ * edge too close to 90 degrees or above it (the aligned catalog layout holds
+ * zero vectors that must stay outside the histogram range). */
+int tpcf_jackknife(tpcf_ctx *ctx, const tpcf_catalog *d, const tpcf_catalog *r, const tpcf_bins *bins,
+                   void *stream, int estimator, uint64_t *loo, double *w_loo, double *cov, tpcf_stats *st);
+
 /* ------------------------------------------------------------------ estimator
  * Landy-Szalay w(theta) (Eq. 1) for nbins bins.  dd, dr, rr: the per-bin
  * counts WITHOUT underflow/overflow (host arrays of nbins); nd, nr >= 2 the

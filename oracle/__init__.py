@@ -167,3 +167,50 @@ def correlation(data, rand, edges, estimator: int = LS_EXACT, threads: int = 1):
     dr = count_cross(data, rand, edges, threads)
     w = estimate(dd[1:-1], dr[1:-1], rr[1:-1], len(data), len(rand), estimator)
     return dd, dr, rr, w
+
+
+def jackknife(data, rand, data_offsets, rand_offsets, edges, estimator: int = LS_EXACT, threads: int = 1):
+    """Delete-one jackknife of the three histograms over the patches of a segmented catalog pair.
+
+    Patch p holds ``data[data_offsets[p]:data_offsets[p+1]]`` and likewise for
+    the randoms.  For each p the patch is removed and DD, DR and RR are counted
+    again from scratch on what remains (the definition of the resampling, no
+    shortcut); w of each resampling follows from ``estimate`` with the remaining
+    point counts (NaN when fewer than 2 points remain), and the covariance is
+    C_ab = (P - 1)/P sum_p (w_pa - mean_a)(w_pb - mean_b), the sums taken in
+    patch order.
+
+    Returns ``(loo, w, cov)``: loo (P, 3, B + 2) uint64, w (P, B), cov (B, B).
+    """
+    data, rand = _as_xyz(data), _as_xyz(rand)
+    doff = [int(x) for x in data_offsets]
+    roff = [int(x) for x in rand_offsets]
+    P = len(doff) - 1
+    nb = len(edges) - 1
+    loo = np.zeros((P, 3, nb + 2), dtype=np.uint64)
+    w = np.full((P, nb), np.nan)
+    for p in range(P):
+        d = np.concatenate([data[:doff[p]], data[doff[p + 1]:]])
+        r = np.concatenate([rand[:roff[p]], rand[roff[p + 1]:]])
+        loo[p, 0] = count_auto(d, edges, threads)
+        loo[p, 1] = count_cross(d, r, edges, threads)
+        loo[p, 2] = count_auto(r, edges, threads)
+        if len(d) >= 2 and len(r) >= 2:
+            w[p] = estimate(loo[p, 0, 1:-1], loo[p, 1, 1:-1], loo[p, 2, 1:-1], len(d), len(r), estimator)
+    cov = None
+    if P >= 2:
+        mean = [0.0] * nb
+        for a in range(nb):
+            s = 0.0
+            for p in range(P):
+                s += float(w[p, a])
+            mean[a] = s / P
+        f = (P - 1) / P
+        cov = np.empty((nb, nb))
+        for a in range(nb):
+            for b in range(nb):
+                s = 0.0
+                for p in range(P):
+                    s += (float(w[p, a]) - mean[a]) * (float(w[p, b]) - mean[b])
+                cov[a, b] = f * s
+    return loo, w, cov

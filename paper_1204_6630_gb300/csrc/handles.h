@@ -69,7 +69,10 @@ struct tpcf_catalog {
     tpcf::Point64* d64 = nullptr;
     float4* d32 = nullptr;
     float4* d32x2 = nullptr;        // (x,x,y,y),(z,z,0,0) per point for the packed screen
-    std::vector<uint64_t> offsets;  // segments (empty = one segment)
+    std::vector<uint64_t> offsets;  // segments (empty = one segment), input order
+    std::vector<uint64_t> seg_start;  // device position of each segment's first point (multiples of
+                                      // kSegAlign; zero vectors fill the gaps), size nseg + 1
+    uint32_t* seg_of_block = nullptr;  // device: segment of each kSegAlign-point block (segmented only)
     double eps_max = 0.0;           // bound on | |v|^2 - 1 | over the points
     cudaStream_t free_stream = nullptr;  // stream-ordered buffers: freed in this stream's order
     bool stream_ordered = false;

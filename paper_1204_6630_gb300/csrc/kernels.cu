@@ -561,14 +561,17 @@ __device__ __forceinline__ void slow_group(const WorkDesc& wd, int sub, float (&
                                            uint32_t ibase, uint32_t jbase, bool masked, const HistCol& hc) {
     static_assert(U * R <= 32, "one bit per pair of the group");
     if (wd.need_idx || masked) {
-        const uint32_t na = sub_of(wd, sub).na, nb = sub_of(wd, sub).nb;
+        const SubProblem& sp = sub_of(wd, sub);
+        const uint32_t na = sp.na, nb = sp.nb;
+        const bool no_self = sp.no_self != 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t jg = jbase + (uint32_t)(jj + u);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const uint32_t ig = ibase + 32u * r;
-                const bool ok = (!wd.need_idx || (jg < nb && ig < na)) && (!masked || jg > ig);
+                const bool diag_ok = no_self ? jg != ig : jg > ig;
+                const bool ok = (!wd.need_idx || (jg < nb && ig < na)) && (!masked || diag_ok);
                 if (!ok) e[u][r] = -1.0f;
             }
         }
@@ -682,6 +685,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
 
     // ---- consumer state
     int cur_sub = -1;
+    unsigned long long* cur_hist = nullptr;  // the histogram this warp's counters belong to
     uint32_t j_since_flush = 0;
     float ax[MODE == kModeScreen ? R : 1], ay[MODE == kModeScreen ? R : 1], az[MODE == kModeScreen ? R : 1];
     unsigned long long px[PACKED ? R / 2 : 1], py[PACKED ? R / 2 : 1], pz[PACKED ? R / 2 : 1];
@@ -694,20 +698,25 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         if (cons.t == cons.g.t_first) {
             // ---- new item (warp-uniform: every warp walks the same tiles)
             const SubProblem& sp = sub_of(wd, cons.sub);
-            if (cons.sub != cur_sub) {
+            unsigned long long* tgt = sp.hist;
+            if (sp.row_seg)
+                tgt += (size_t)__ldg(sp.row_seg + (cons.g.i0 + (uint32_t)warp * (32u * R)) / kSegAlign) * sp.row_stride;
+            if (cons.sub != cur_sub || tgt != cur_hist) {
                 if (cur_sub >= 0) {
+                    // queued pairs belong to the previous sub-problem and histogram
                     if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
-                    if (sp.hist != sub_of(wd, cur_sub).hist) {
-                        warp_flush_hist<T>(hc, wd.ne, sub_of(wd, cur_sub).hist);
+                    if (tgt != cur_hist) {
+                        warp_flush_hist<T>(hc, wd.ne, cur_hist);
                         j_since_flush = 0;
                     }
                 }
                 cur_sub = cons.sub;
+                cur_hist = tgt;
             }
             const uint32_t item_j = (cons.g.t_end - cons.g.t_first) * wd.J;
             if (j_since_flush + item_j > wd.flush_limit) {
                 if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
-                warp_flush_hist<T>(hc, wd.ne, sp.hist);
+                warp_flush_hist<T>(hc, wd.ne, cur_hist);
                 j_since_flush = 0;
             }
             j_since_flush += item_j;
@@ -758,7 +767,9 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         if (ctl[kCtlAbort]) { aborted = true; break; }
 
         const uint32_t jbase = cons.g.j0 + cons.t * wd.J;
-        const bool masked = sub_of(wd, cur_sub).auto_mode != 0 && (jbase < cons.g.i0 + wd.I);
+        // tiles that meet the diagonal: j > i (auto counts) or j != i (full square without self pairs)
+        const bool masked = (sub_of(wd, cur_sub).auto_mode != 0 && jbase < cons.g.i0 + wd.I) ||
+                            (sub_of(wd, cur_sub).no_self != 0 && jbase < cons.g.i0 + wd.I && jbase + wd.J > cons.g.i0);
         const int J = (int)wd.J;
         if constexpr (PACKED) {
             // Fast loop with packed FMA: one fma.rn.f32x2 gives the screen values of
@@ -828,6 +839,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             const Point64* sj = sptr<const Point64>(wd.off_stage + stage * wd.stage_bytes);
             const double* cthr = sptr<const double>(wd.off_cthr);
             const uint32_t na = sub_of(wd, cur_sub).na, nb = sub_of(wd, cur_sub).nb;
+            const bool no_self = sub_of(wd, cur_sub).no_self != 0;
             const int ne = wd.ne;
             for (int jj = 0; jj < J; ++jj) {
                 const Point64 b = sj[jj];
@@ -838,7 +850,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                                                __dmul_rn(dz[r], b.z));
                     if (d > wd.cos_last) {
                         const uint32_t ig = ibase + 32u * r;
-                        if (ig < na && jg < nb && (!masked || jg > ig)) {
+                        if (ig < na && jg < nb && (!masked || (no_self ? jg != ig : jg > ig))) {
                             // h = number of edges m with d <= C_m (C decreasing)
                             int lo = 0, hi = ne;
                             while (lo < hi) {
@@ -876,7 +888,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     // ---- merge this warp's columns (skipped after an abort: outputs are invalid)
     if (!aborted && cur_sub >= 0) {
         if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
-        warp_flush_hist<T>(hc, wd.ne, sub_of(wd, cur_sub).hist);
+        warp_flush_hist<T>(hc, wd.ne, cur_hist);
     }
     __syncwarp();
     if (lane == 0) {
@@ -1080,27 +1092,24 @@ __global__ void __launch_bounds__(1024) bitonic_local_kernel(unsigned long long*
     vals[base + t + 1024] = sv[t + 1024];
 }
 
-// Gather points in sorted order into the binary64 and FP32 device copies;
-// zero the padding.
+// Gather points in sorted order into the binary64 and FP32 device copies (the
+// outputs are zeroed beforehand: padding and segment gaps hold zero vectors).
+// Sorted point p of segment s goes to position p + seg_delta[s] (segments of a
+// segmented catalog start on aligned positions; seg_delta = NULL: no shift).
 __global__ void prep_gather_kernel(const double* __restrict__ xyz, uint32_t n,
-                                   const uint32_t* __restrict__ order, Point64* out64,
-                                   float4* out32, float4* out32x2, uint32_t n_pad) {
+                                   const uint32_t* __restrict__ order, const uint32_t* __restrict__ seg_of_point,
+                                   const uint32_t* __restrict__ seg_delta, Point64* out64, float4* out32,
+                                   float4* out32x2) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pad) return;
-    if (p >= n) {
-        out64[p] = Point64{0.0, 0.0, 0.0, 0.0};
-        out32[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-        out32x2[2ull * p] = make_float4(0.f, 0.f, 0.f, 0.f);
-        out32x2[2ull * p + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
+    if (p >= n) return;
     const uint32_t s = order ? order[p] : p;
+    const uint32_t q = seg_delta ? p + seg_delta[seg_of_point[s]] : p;
     const double x = xyz[3ull * s], y = xyz[3ull * s + 1], z = xyz[3ull * s + 2];
     const float fx = __double2float_rn(x), fy = __double2float_rn(y), fz = __double2float_rn(z);
-    out64[p] = Point64{x, y, z, 0.0};
-    out32[p] = make_float4(fx, fy, fz, 0.f);
-    out32x2[2ull * p] = make_float4(fx, fx, fy, fy);
-    out32x2[2ull * p + 1] = make_float4(fz, fz, 0.f, 0.f);
+    out64[q] = Point64{x, y, z, 0.0};
+    out32[q] = make_float4(fx, fy, fz, 0.f);
+    out32x2[2ull * q] = make_float4(fx, fx, fy, fy);
+    out32x2[2ull * q + 1] = make_float4(fz, fz, 0.f, 0.f);
 }
 
 // ============================================================== launchers
@@ -1194,7 +1203,8 @@ cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long l
 }
 
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
-                           int sort, Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
+                           const uint32_t* seg_delta, int sort, Point64* out64, float4* out32, float4* out32x2,
+                           uint32_t n_pad,
                            unsigned long long* keys, uint32_t* vals, uint32_t n_pow2,
                            unsigned long long* err_word, unsigned long long* eps_word, cudaStream_t stream,
                            uint32_t* launches) {
@@ -1226,8 +1236,14 @@ cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg
         }
     }
     if (n_pad > 0) {
-        prep_gather_kernel<<<(n_pad + 255) / 256, 256, 0, stream>>>(xyz_in, n, do_sort ? vals : nullptr,
-                                                                   out64, out32, out32x2, n_pad);
+        if ((e = cudaMemsetAsync(out64, 0, (size_t)n_pad * sizeof(Point64), stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(out32, 0, (size_t)n_pad * sizeof(float4), stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(out32x2, 0, (size_t)n_pad * 2 * sizeof(float4), stream)) != cudaSuccess)
+            return e;
+    }
+    if (n > 0) {
+        prep_gather_kernel<<<(n + 255) / 256, 256, 0, stream>>>(xyz_in, n, do_sort ? vals : nullptr, seg_of_point,
+                                                               seg_delta, out64, out32, out32x2);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -482,11 +482,22 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
     c->n = n;
     c->stream_ordered = stream_ordered;
     c->free_stream = st;
-    c->n_pad = (uint32_t)(((n + kPad - 1) / kPad) * kPad);
+    uint64_t n_layout = n;  // device positions in use (segments are aligned: gaps of zero vectors)
+    if (nseg > 0) {
+        c->offsets.assign(offsets, offsets + nseg + 1);
+        c->seg_start.assign(nseg + 1, 0);
+        for (int s = 0; s < nseg; ++s)
+            c->seg_start[s + 1] = (c->seg_start[s] + (offsets[s + 1] - offsets[s]) + kSegAlign - 1) / kSegAlign * kSegAlign;
+        n_layout = c->seg_start[nseg];
+        if (n_layout > TPCF_MAX_POINTS) {
+            catalog_destroy_impl(c);
+            return ctx->fail(TPCF_EOVERFLOW, "catalog: aligned segments exceed the point limit");
+        }
+    }
+    c->n_pad = (uint32_t)(((n_layout + kPad - 1) / kPad) * kPad);
     if (c->n_pad == 0) c->n_pad = kPad;
     // a segment's tiles and i-blocks may run up to one block past its last point
     if (nseg > 0) c->n_pad += kPad;
-    if (nseg > 0) c->offsets.assign(offsets, offsets + nseg + 1);
     const bool sort = !(ctx->cfg.flags & TPCF_F_NO_SORT);
     uint32_t n_pow2 = 2048;
     while (n_pow2 < n) n_pow2 <<= 1;
@@ -495,6 +506,7 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
     unsigned long long* keys = nullptr;
     uint32_t* vals = nullptr;
     uint32_t* seg = nullptr;
+    uint32_t* seg_delta = nullptr;
     unsigned long long* err = nullptr;
     int rc = TPCF_OK;
     auto release = [&]() {
@@ -502,6 +514,7 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
         if (keys) cudaFreeAsync(keys, st);
         if (vals) cudaFreeAsync(vals, st);
         if (seg) cudaFreeAsync(seg, st);
+        if (seg_delta) cudaFreeAsync(seg_delta, st);
         if (err) cudaFreeAsync(err, st);
         cudaStreamSynchronize(st);
     };
@@ -530,19 +543,32 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
         cudaMallocAsync((void**)&vals, (size_t)n_pow2 * 4, st) != cudaSuccess)
         return fail_with(TPCF_ENOMEM, "scratch allocation failed");
     if (cudaMemsetAsync(err, 0, 16, st) != cudaSuccess) return fail_with(TPCF_ECUDA, "memset failed");
-    if (nseg > 0 && n > 0) {
-        std::vector<uint32_t> hs(n);
-        for (int s = 0; s < nseg; ++s)
+    if (nseg > 0) {
+        // segment of each input point, shift of each segment to its aligned start, and the
+        // segment of each kSegAlign-point block of the device layout (blocks past the last
+        // segment: the last segment; they hold only zero vectors)
+        std::vector<uint32_t> hs(n), hd(nseg);
+        for (int s = 0; s < nseg; ++s) {
+            hd[s] = (uint32_t)(c->seg_start[s] - offsets[s]);
             for (uint64_t i = offsets[s]; i < offsets[s + 1]; ++i) hs[i] = (uint32_t)s;
-        if (cudaMallocAsync((void**)&seg, n * 4, st) != cudaSuccess)
+        }
+        const uint32_t nblk = c->n_pad / kSegAlign;
+        std::vector<uint32_t> hb(nblk, (uint32_t)(nseg - 1));
+        for (int s = 0; s < nseg; ++s)
+            for (uint64_t b = c->seg_start[s] / kSegAlign; b < c->seg_start[s + 1] / kSegAlign; ++b) hb[b] = (uint32_t)s;
+        if (alloc((void**)&c->seg_of_block, (size_t)nblk * 4) != cudaSuccess ||
+            cudaMallocAsync((void**)&seg_delta, (size_t)nseg * 4, st) != cudaSuccess ||
+            (n > 0 && cudaMallocAsync((void**)&seg, n * 4, st) != cudaSuccess))
             return fail_with(TPCF_ENOMEM, "segment allocation failed");
-        if (cudaMemcpyAsync(seg, hs.data(), n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        if ((n > 0 && cudaMemcpyAsync(seg, hs.data(), n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+            cudaMemcpyAsync(seg_delta, hd.data(), (size_t)nseg * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(c->seg_of_block, hb.data(), (size_t)nblk * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return fail_with(TPCF_ECUDA, "segment copy failed");
     }
     uint32_t nl = 0;
-    cudaError_t e = launch_prepare(in, (uint32_t)n, seg, sort ? 1 : 0, c->d64, c->d32, c->d32x2, c->n_pad, keys,
-                                   vals, n_pow2, err, err + 1, st, &nl);
+    cudaError_t e = launch_prepare(in, (uint32_t)n, seg, seg_delta, sort ? 1 : 0, c->d64, c->d32, c->d32x2, c->n_pad,
+                                   keys, vals, n_pow2, err, err + 1, st, &nl);
     ctx->launches.fetch_add(nl);
     if (e != cudaSuccess) return fail_with(TPCF_ECUDA, cudaGetErrorString(e));
     unsigned long long hw[2] = {0, 0};
@@ -576,7 +602,7 @@ extern "C" int tpcf_catalog_create(tpcf_ctx* ctx, const double* xyz, uint64_t n,
 int tpcf::catalog_destroy_impl(tpcf_catalog* c) {
     if (!c) return TPCF_EINVAL;
     cudaSetDevice(c->ctx->cfg.device);
-    void* bufs[3] = {c->d64, c->d32, c->d32x2};
+    void* bufs[4] = {c->d64, c->d32, c->d32x2, c->seg_of_block};
     if (c->stream_ordered) {
         for (void* p : bufs)
             if (p) cudaFreeAsync(p, c->free_stream);
@@ -602,6 +628,10 @@ struct SubSpec {
     bool auto_mode;
     uint32_t na, nb;        // counts (segments: sub-ranges)
     uint32_t a_off, b_off;  // first point of the range in the catalog
+    int nhist = 1;                      // histograms filled (row attribution: one per segment of A)
+    const uint32_t* row_seg = nullptr;  // device segment table of A's kSegAlign blocks (row attribution)
+    bool no_self = false;               // A == B over the full square except i == j
+    const uint64_t* totals = nullptr;   // pair total of each histogram (nhist entries); NULL: all pairs
 };
 
 int kernel_mode(const tpcf_config& cfg) {
@@ -650,7 +680,8 @@ bool choose_shape(tpcf_ctx* ctx, int mode, int nedges, uint64_t total_pairs, uin
 }
 
 uint64_t full_pairs(const SubSpec& s) {
-    return s.auto_mode ? (uint64_t)s.na * (s.na ? s.na - 1 : 0) / 2 : (uint64_t)s.na * s.nb;
+    if (s.auto_mode) return (uint64_t)s.na * (s.na ? s.na - 1 : 0) / 2;
+    return (uint64_t)s.na * s.nb - (s.no_self ? (uint64_t)std::min(s.na, s.nb) : 0);
 }
 
 // Pairs of sub-problem `sp` inside the global item range [lo, hi).
@@ -675,6 +706,7 @@ uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bi
     const uint32_t I = (uint32_t)(sh.threads * sh.ipt), Jc = (uint32_t)sh.jchunk;
     subs.assign(nsub, SubProblem());
     uint64_t items = 0;
+    size_t hist_base = 0;
     for (int s = 0; s < nsub; ++s) {
         const SubSpec& p = specs[s];
         SubProblem& sp = subs[s];
@@ -693,8 +725,12 @@ uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bi
         sp.item_begin = items;
         sp.n_items = (p.na == 0 || p.nb == 0) ? 0 : items_of(sp.n_iblk, sp.n_jchunk, p.auto_mode, I, Jc);
         sp.walk_mult = walk_multiplier(sp.n_items);
-        sp.hist = acc + (size_t)s * acc_stride;
+        sp.hist = acc + hist_base * acc_stride;
         sp.bins = bins->dev_desc;
+        sp.row_seg = p.row_seg ? p.row_seg + p.a_off / kSegAlign : nullptr;
+        sp.row_stride = (uint32_t)acc_stride;
+        sp.no_self = p.no_self ? 1u : 0u;
+        hist_base += (size_t)p.nhist;
         items += sp.n_items;
     }
     (void)ctx;
@@ -721,11 +757,21 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     if (where == TPCF_DEVICE && stats) return ctx->fail(TPCF_EINVAL, "stats need where = TPCF_HOST");
     if (!bins || bins->ctx != ctx) return ctx->fail(TPCF_EINVAL, "bins missing or from another context");
     if (nsub < 1) return ctx->fail(TPCF_EINVAL, "no histogram to count");
+    // histograms: sub-problem s fills nhist of them, from index hist_first[s]; outs has one per histogram
+    int H = 0;
+    bool any_rows = false;
     for (int s = 0; s < nsub; ++s) {
-        if (!outs[s]) return ctx->fail(TPCF_EINVAL, "NULL histogram");
         if (!specs[s].a || !specs[s].b || specs[s].a->ctx != ctx || specs[s].b->ctx != ctx)
             return ctx->fail(TPCF_EINVAL, "catalog missing or from another context");
+        if (specs[s].nhist < 1 || (specs[s].nhist > 1 && !specs[s].row_seg))
+            return ctx->fail(TPCF_EINVAL, "bad histogram count");
+        any_rows |= specs[s].row_seg != nullptr;
+        H += specs[s].nhist;
     }
+    for (int h = 0; h < H; ++h)
+        if (!outs[h]) return ctx->fail(TPCF_EINVAL, "NULL histogram");
+    if (any_rows && ctx->cfg.shard_count > 1)
+        return ctx->fail(TPCF_EINVAL, "row-attributed counts are not split into shards");
     cudaSetDevice(ctx->cfg.device);
     const int ne = bins->nedges;
     int mode = kernel_mode(ctx->cfg);
@@ -743,11 +789,13 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     if (!fits)
         return ctx->fail(TPCF_EINVAL, "no kernel shape fits (threads=%d ipt=%d jtile=%d)",
                          ctx->cfg.threads, ctx->cfg.ipt, ctx->cfg.jtile);
+    if (any_rows && 32u * (uint32_t)sh.ipt != kSegAlign)
+        return ctx->fail(TPCF_EINVAL, "row-attributed counts need %u i-points per warp", kSegAlign);
 
     // ---- accumulators and statistics: a context slot for up to 3 histograms,
     // otherwise one stream-ordered allocation for this call (a plain allocation
     // owned by the graph when capturing)
-    const bool use_slot = nsub <= 3 && !capture;
+    const bool use_slot = H <= 3 && !capture;
     tpcf_ctx::Slot* slot = nullptr;
     std::unique_lock<std::mutex> slot_lock;
     unsigned long long* acc = nullptr;
@@ -757,6 +805,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     SubProblem* dev_subs = nullptr;
     unsigned long long* dev_totals = nullptr;
     const size_t sub_bytes = ((size_t)nsub * sizeof(SubProblem) + 255) / 256 * 256;
+    const size_t tot_bytes = ((size_t)H * 8 + 255) / 256 * 256;
     size_t acc_words = 0;
     if (use_slot) {
         slot = &ctx->slots[ctx->slot_rr.fetch_add(1) % kSlots];
@@ -768,12 +817,12 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         acc_words = kSlotWords;
     } else {
         acc_stride = (size_t)ne + 1;
-        acc_words = (size_t)nsub * acc_stride + kStatWords;
-        const size_t bytes = acc_words * 8 + sub_bytes + (size_t)nsub * 8;
+        acc_words = (size_t)H * acc_stride + kStatWords;
+        const size_t bytes = acc_words * 8 + sub_bytes + tot_bytes;
         if ((capture ? dev_malloc(&call_buf, bytes) : cudaMallocAsync(&call_buf, bytes, st)) != cudaSuccess)
             return ctx->fail(TPCF_ENOMEM, "accumulator allocation failed (%zu bytes)", bytes);
         acc = (unsigned long long*)call_buf;
-        stat_w = acc + (size_t)nsub * acc_stride;
+        stat_w = acc + (size_t)H * acc_stride;
         dev_subs = (SubProblem*)((char*)call_buf + acc_words * 8);
         dev_totals = (unsigned long long*)((char*)dev_subs + sub_bytes);
     }
@@ -885,12 +934,15 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         if (rc != TPCF_OK) return release(ctx->fail(rc, "work description failed"));
     }
     // ---- per-histogram pair totals (the finalize step derives overflow from them)
-    std::vector<unsigned long long> totals(nsub);
+    std::vector<unsigned long long> totals;
+    totals.reserve(H);
     for (int s2 = 0; s2 < nsub; ++s2)
-        totals[s2] = ctx->cfg.shard_count > 1 ? range_pairs(subs[s2], wd.item_lo, wd.item_hi, wd.I, wd.Jc, wd.J)
-                                              : full_pairs(specs[s2]);
+        for (int k = 0; k < specs[s2].nhist; ++k)
+            totals.push_back(specs[s2].totals ? specs[s2].totals[k]
+                             : ctx->cfg.shard_count > 1 ? range_pairs(subs[s2], wd.item_lo, wd.item_hi, wd.I, wd.Jc, wd.J)
+                                                        : full_pairs(specs[s2]));
     if (!use_slot &&
-        cudaMemcpyAsync(dev_totals, totals.data(), (size_t)nsub * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        cudaMemcpyAsync(dev_totals, totals.data(), (size_t)H * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return release(ctx->fail(TPCF_ECUDA, "totals upload failed"));
     if (capture) {
         if (count_set_smem_limit(mode, sh.threads, sh.ipt, sh.smem) != cudaSuccess ||
@@ -925,7 +977,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
 
     // ---- finalize: overflow of each histogram = its pair total - sum of the other entries
     if (use_slot) {
-        for (int s2 = 0; s2 < nsub; ++s2) {
+        for (int s2 = 0; s2 < H; ++s2) {
             unsigned long long* a = acc + (size_t)s2 * acc_stride;
             unsigned long long* dst = where == TPCF_DEVICE ? outs[s2] : a;
             if (launch_finalize(a, ne, dst, totals[s2], stat_w + kStatError, st) != cudaSuccess)
@@ -933,9 +985,9 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
             ++launches;
         }
     } else {
-        // device outputs must be one contiguous array (outs[s] = outs[0] + s * (ne + 1))
+        // device outputs must be one contiguous array (outs[h] = outs[0] + h * (ne + 1))
         unsigned long long* dst = where == TPCF_DEVICE ? outs[0] : acc;
-        if (launch_finalize_batch(acc, (int)acc_stride, ne, dst, ne + 1, dev_totals, nsub, stat_w + kStatError, st) !=
+        if (launch_finalize_batch(acc, (int)acc_stride, ne, dst, ne + 1, dev_totals, H, stat_w + kStatError, st) !=
             cudaSuccess)
             return abort_capture(ctx->fail(TPCF_ECUDA, "finalize launch failed"));
         ++launches;
@@ -958,7 +1010,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         if (cudaMemcpyAsync(h.data(), acc, acc_words * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return release(ctx->fail(TPCF_ECUDA, "result copy failed"));
-        for (int s2 = 0; s2 < nsub; ++s2)
+        for (int s2 = 0; s2 < H; ++s2)
             memcpy(outs[s2], h.data() + (size_t)s2 * acc_stride, (size_t)(ne + 1) * 8);
         const unsigned long long* hs = h.data() + (stat_w - acc);
         const unsigned long long errw = hs[kStatError];
@@ -1027,14 +1079,141 @@ extern "C" int tpcf_count_patches(tpcf_ctx* ctx, const tpcf_catalog* d, const tp
     std::vector<SubSpec> specs(3 * (size_t)np);
     std::vector<unsigned long long*> outs(3 * (size_t)np);
     for (int p = 0; p < np; ++p) {
-        const uint32_t d0 = (uint32_t)d->offsets[p], dn = (uint32_t)(d->offsets[p + 1] - d->offsets[p]);
-        const uint32_t r0 = (uint32_t)r->offsets[p], rn = (uint32_t)(r->offsets[p + 1] - r->offsets[p]);
+        const uint32_t d0 = (uint32_t)d->seg_start[p], dn = (uint32_t)(d->offsets[p + 1] - d->offsets[p]);
+        const uint32_t r0 = (uint32_t)r->seg_start[p], rn = (uint32_t)(r->offsets[p + 1] - r->offsets[p]);
         specs[3 * p + 0] = SubSpec{d, d, true, dn, dn, d0, d0};
         specs[3 * p + 1] = SubSpec{d, r, false, dn, rn, d0, r0};
         specs[3 * p + 2] = SubSpec{r, r, true, rn, rn, r0, r0};
         for (int k = 0; k < 3; ++k) outs[3 * p + k] = (unsigned long long*)hists + (3 * (size_t)p + k) * hs;
     }
     return run_counts(ctx, specs.data(), 3 * np, bins, (cudaStream_t)stream, outs.data(), where, st, true);
+}
+
+// ====================================================================== leave-one-out jackknife
+// One launch fills, for every segment p of the two segmented catalogs:
+//   rows_DD[p] = ordered pairs (i, j), i != j, i in D_p, j in D     (full square, rows by D segment)
+//   rows_RR[p] likewise over R;  rows_DR[p] = pairs (d in D_p, r in R);  rows_RD[p] = (r in R_p, d in D)
+//   within_DD[p], within_DR[p], within_RR[p] (the per-patch counts of tpcf_count_patches).
+// Pairs touching patch p: T_DD = rows_DD - within_DD (ordered rows count the pairs inside p twice),
+// T_RR likewise, T_DR = rows_DR + rows_RD - within_DR.  Totals: DD = sum_p rows_DD / 2, RR alike,
+// DR = sum_p rows_DR.  Leave-one-out: X_{-p} = X - T_X[p].
+extern "C" int tpcf_jackknife(tpcf_ctx* ctx, const tpcf_catalog* d, const tpcf_catalog* r, const tpcf_bins* bins,
+                              void* stream, int estimator, uint64_t* loo, double* w_loo, double* cov,
+                              tpcf_stats* st) {
+    if (!ctx) return TPCF_EINVAL;
+    if (!d || !r || !bins || !loo) return ctx->fail(TPCF_EINVAL, "jackknife: NULL argument");
+    if (d->offsets.empty() || r->offsets.empty() || d->offsets.size() != r->offsets.size())
+        return ctx->fail(TPCF_EINVAL, "jackknife: both catalogs must be segmented with the same count");
+    if (estimator != TPCF_LS_EXACT && estimator != TPCF_LS_PAPER)
+        return ctx->fail(TPCF_EINVAL, "jackknife: unknown estimator");
+    if (!(bins->host.fast_t > 0.f))
+        return ctx->fail(TPCF_EINVAL, "jackknife: the histogram range must end below 90 degrees");
+    const int P = (int)d->offsets.size() - 1;
+    if (cov && P < 2) return ctx->fail(TPCF_EINVAL, "jackknife: the covariance needs at least 2 patches");
+    const int ne = bins->nedges, hs = ne + 1, B = ne - 1;
+    const uint64_t ND = d->n, NR = r->n;
+    std::vector<uint64_t> tdd(P), trr(P), tdr(P), trd(P);
+    for (int p = 0; p < P; ++p) {
+        const uint64_t np_ = d->offsets[p + 1] - d->offsets[p], mp = r->offsets[p + 1] - r->offsets[p];
+        tdd[p] = np_ * (ND ? ND - 1 : 0);
+        trr[p] = mp * (NR ? NR - 1 : 0);
+        tdr[p] = np_ * NR;
+        trd[p] = mp * ND;
+    }
+    const uint32_t AD = (uint32_t)d->seg_start[P], AR = (uint32_t)r->seg_start[P];
+    std::vector<SubSpec> specs;
+    SubSpec s_dd{d, d, false, AD, AD, 0, 0, P, d->seg_of_block, true, tdd.data()};
+    SubSpec s_rr{r, r, false, AR, AR, 0, 0, P, r->seg_of_block, true, trr.data()};
+    SubSpec s_dr{d, r, false, AD, AR, 0, 0, P, d->seg_of_block, false, tdr.data()};
+    SubSpec s_rd{r, d, false, AR, AD, 0, 0, P, r->seg_of_block, false, trd.data()};
+    specs.push_back(s_rr);
+    specs.push_back(s_dr);
+    specs.push_back(s_rd);
+    specs.push_back(s_dd);
+    for (int p = 0; p < P; ++p) {
+        const uint32_t d0 = (uint32_t)d->seg_start[p], dn = (uint32_t)(d->offsets[p + 1] - d->offsets[p]);
+        const uint32_t r0 = (uint32_t)r->seg_start[p], rn = (uint32_t)(r->offsets[p + 1] - r->offsets[p]);
+        specs.push_back(SubSpec{d, d, true, dn, dn, d0, d0});
+        specs.push_back(SubSpec{d, r, false, dn, rn, d0, r0});
+        specs.push_back(SubSpec{r, r, true, rn, rn, r0, r0});
+    }
+    // histogram order: rows_RR, rows_DR, rows_RD, rows_DD (P each), then (DD, DR, RR) per patch
+    const int H = 7 * P;
+    std::vector<uint64_t> h((size_t)H * hs);
+    std::vector<unsigned long long*> outs(H);
+    for (int k = 0; k < H; ++k) outs[k] = (unsigned long long*)h.data() + (size_t)k * hs;
+    const int rc = run_counts(ctx, specs.data(), (int)specs.size(), bins, (cudaStream_t)stream, outs.data(), TPCF_HOST,
+                              st, true);
+    if (rc != TPCF_OK) return rc;
+    auto rows_rr = [&](int p) { return h.data() + (size_t)(0 * P + p) * hs; };
+    auto rows_dr = [&](int p) { return h.data() + (size_t)(1 * P + p) * hs; };
+    auto rows_rd = [&](int p) { return h.data() + (size_t)(2 * P + p) * hs; };
+    auto rows_dd = [&](int p) { return h.data() + (size_t)(3 * P + p) * hs; };
+    auto within = [&](int p, int k) { return h.data() + (size_t)(4 * P + 3 * p + k) * hs; };
+    std::vector<uint64_t> DD(hs, 0), DR(hs, 0), RR(hs, 0), DR2(hs, 0);
+    for (int p = 0; p < P; ++p)
+        for (int b = 0; b < hs; ++b) {
+            DD[b] += rows_dd(p)[b];
+            RR[b] += rows_rr(p)[b];
+            DR[b] += rows_dr(p)[b];
+            DR2[b] += rows_rd(p)[b];
+        }
+    for (int b = 0; b < hs; ++b) {
+        if ((DD[b] & 1) || (RR[b] & 1) || DR[b] != DR2[b])
+            return ctx->fail(TPCF_ECUDA, "jackknife: inconsistent row sums (bin %d)", b);
+        DD[b] /= 2;
+        RR[b] /= 2;
+    }
+    for (int p = 0; p < P; ++p) {
+        uint64_t* o = loo + (size_t)3 * p * hs;
+        uint64_t sdd = 0, sdr = 0, srr = 0;
+        for (int b = 0; b < hs; ++b) {
+            o[b] = DD[b] - (rows_dd(p)[b] - within(p, 0)[b]);
+            o[hs + b] = DR[b] - (rows_dr(p)[b] + rows_rd(p)[b] - within(p, 1)[b]);
+            o[2 * hs + b] = RR[b] - (rows_rr(p)[b] - within(p, 2)[b]);
+            sdd += o[b];
+            sdr += o[hs + b];
+            srr += o[2 * hs + b];
+        }
+        const uint64_t nd = ND - (d->offsets[p + 1] - d->offsets[p]), nr = NR - (r->offsets[p + 1] - r->offsets[p]);
+        if (sdd != nd * (nd ? nd - 1 : 0) / 2 || sdr != nd * nr || srr != nr * (nr ? nr - 1 : 0) / 2)
+            return ctx->fail(TPCF_ECUDA, "jackknife: leave-one-out totals do not add up (patch %d)", p);
+    }
+    if (st) {
+        uint64_t pairs = ND * (ND ? ND - 1 : 0) + NR * (NR ? NR - 1 : 0) + 2 * ND * NR;
+        for (int p = 0; p < P; ++p) {
+            const uint64_t np_ = d->offsets[p + 1] - d->offsets[p], mp = r->offsets[p + 1] - r->offsets[p];
+            pairs += np_ * (np_ ? np_ - 1 : 0) / 2 + mp * (mp ? mp - 1 : 0) / 2 + np_ * mp;
+        }
+        st->pairs = pairs;  // the real pairs (the device figure includes the alignment padding)
+    }
+    if (!w_loo && !cov) return TPCF_OK;
+    std::vector<double> w((size_t)P * (B > 0 ? B : 1), NAN);
+    for (int p = 0; p < P; ++p) {
+        const uint64_t nd = ND - (d->offsets[p + 1] - d->offsets[p]), nr = NR - (r->offsets[p + 1] - r->offsets[p]);
+        const uint64_t* o = loo + (size_t)3 * p * hs;
+        if (nd >= 2 && nr >= 2)
+            tpcf_estimate(o + 1, o + hs + 1, o + 2 * hs + 1, B, nd, nr, estimator, w.data() + (size_t)p * B);
+    }
+    if (w_loo) memcpy(w_loo, w.data(), (size_t)P * B * sizeof(double));
+    if (cov) {
+        // C_ab = (P - 1) / P * sum_p (w_pa - mean_a)(w_pb - mean_b), sums in patch order
+        std::vector<double> mean(B, 0.0);
+        for (int a = 0; a < B; ++a) {
+            double sum = 0.0;
+            for (int p = 0; p < P; ++p) sum += w[(size_t)p * B + a];
+            mean[a] = sum / (double)P;
+        }
+        const double f = (double)(P - 1) / (double)P;
+        for (int a = 0; a < B; ++a)
+            for (int b2 = 0; b2 < B; ++b2) {
+                double sum = 0.0;
+                for (int p = 0; p < P; ++p)
+                    sum += (w[(size_t)p * B + a] - mean[a]) * (w[(size_t)p * B + b2] - mean[b2]);
+                cov[(size_t)a * B + b2] = f * sum;
+            }
+    }
+    return TPCF_OK;
 }
 
 // ====================================================================== captured counting graphs
@@ -1072,8 +1251,8 @@ extern "C" int tpcf_graph_create(tpcf_ctx* ctx, int kind, const tpcf_catalog* d,
                 return ctx->fail(TPCF_EINVAL, "graph: patches need two segmented catalogs with the same count");
             const int np = (int)d->offsets.size() - 1;
             for (int p = 0; p < np; ++p) {
-                const uint32_t d0 = (uint32_t)d->offsets[p], dn = (uint32_t)(d->offsets[p + 1] - d->offsets[p]);
-                const uint32_t r0 = (uint32_t)r->offsets[p], rn = (uint32_t)(r->offsets[p + 1] - r->offsets[p]);
+                const uint32_t d0 = (uint32_t)d->seg_start[p], dn = (uint32_t)(d->offsets[p + 1] - d->offsets[p]);
+                const uint32_t r0 = (uint32_t)r->seg_start[p], rn = (uint32_t)(r->offsets[p + 1] - r->offsets[p]);
                 specs.push_back(SubSpec{d, d, true, dn, dn, d0, d0});
                 specs.push_back(SubSpec{d, r, false, dn, rn, d0, r0});
                 specs.push_back(SubSpec{r, r, true, rn, rn, r0, r0});

@@ -11,6 +11,11 @@ namespace tpcf {
 // points; points past n are zero vectors (never counted, see kernels.cu).
 constexpr uint32_t kPad = 4096;
 
+// Segments of a segmented catalog start on multiples of this many points (one
+// warp's i-points of the 512 x 8 counting shape), so that a warp's i-points
+// always belong to one segment.
+constexpr uint32_t kSegAlign = 256;
+
 // Lookup table from the FP32 screen value to the candidate histogram index
 // range: cell k = rne(sat(e * lut_scale) * 2^14), k = 0 .. 2^14.
 constexpr int kLutBits = 14;
@@ -63,6 +68,13 @@ struct SubProblem {
     uint64_t walk_mult;   // position item_begin + k visits local item (k * walk_mult) mod n_items
     unsigned long long* hist;   // B + 2 accumulators (device)
     const BinsDev* bins;        // device pointer to this sub-problem's bins
+    // Row attribution (leave-one-out jackknife): pairs go to histogram
+    // hist + row_seg[b] * row_stride, b the kSegAlign-point block of A holding
+    // the pair's i-point (A's segments are aligned, so a warp's i-points share
+    // one block).  row_seg == NULL: the one histogram `hist`.
+    const uint32_t* row_seg;
+    uint32_t row_stride;        // accumulator words between consecutive segments' histograms
+    uint32_t no_self;           // 1: A == B counted over the full square except i == j
 };
 
 constexpr int kMaxInlineSub = 3;
@@ -128,7 +140,8 @@ cudaError_t launch_finalize_batch(const unsigned long long* acc, int acc_stride,
                                   unsigned long long* out, int out_stride, const unsigned long long* totals,
                                   int count, unsigned long long* err_word, cudaStream_t stream);
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
-                           int sort, Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
+                           const uint32_t* seg_delta, int sort, Point64* out64, float4* out32, float4* out32x2,
+                           uint32_t n_pad,
                            unsigned long long* key_scratch, uint32_t* val_scratch,
                            uint32_t n_pow2, unsigned long long* err_word, unsigned long long* eps_word,
                            cudaStream_t stream, uint32_t* launches);

@@ -118,6 +118,8 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_uint32), _u64p]),
     "tpcf_debug_fail_alloc_after": (None, [ctypes.c_int]),
     "tpcf_count_auto_noalloc": (ctypes.c_int, [_vp, _u64, _dp, ctypes.c_int, _vp, _vp]),
+    "tpcf_jackknife": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _u64p, _dp, _dp,
+                                      ctypes.POINTER(tpcf_stats)]),
     "tpcf_submit": (ctypes.c_int, [_vp, ctypes.POINTER(tpcf_job), _u64p]),
     "tpcf_poll": (ctypes.c_int, [_vp, _u64, ctypes.c_int, ctypes.POINTER(tpcf_result)]),
     "tpcf_cancel": (ctypes.c_int, [_vp, _u64]),
@@ -419,6 +421,23 @@ def tpcf_count_auto_noalloc(xyz_dev, edges_rad, out_dev, stream=None) -> None:
     _check(rc, "tpcf_count_auto_noalloc")
 
 
+def tpcf_jackknife(ctx: int, d: int, r: int, bins: int, nedges: int, npatch: int, stream=None,
+                   estimator: int = TPCF_LS_EXACT, stats: bool = False):
+    """Leave-one-out histograms (npatch, 3, nedges + 1), w of each resampling
+    (npatch, nedges - 1) and their covariance (nedges - 1, nedges - 1)."""
+    nb = nedges - 1
+    loo = np.empty((npatch, 3, nedges + 1), np.uint64)
+    w = np.empty((npatch, nb), np.float64)
+    cov = np.empty((nb, nb), np.float64) if npatch >= 2 else None
+    st = tpcf_stats() if stats else None
+    rc = load().tpcf_jackknife(ctx, d, r, bins, _stream_ptr(stream), estimator, loo.ctypes.data_as(_u64p),
+                               w.ctypes.data_as(_dp), cov.ctypes.data_as(_dp) if cov is not None else None,
+                               ctypes.byref(st) if st is not None else None)
+    _check(rc, "tpcf_jackknife", ctx)
+    out = (loo, w, cov)
+    return out + (st.as_dict(),) if st is not None else out
+
+
 def tpcf_submit(ctx: int, d_xyz, r_xyz, edges_rad, estimator: int = TPCF_LS_EXACT) -> int:
     """Queue a correlation job (host arrays, copied by the call); returns its id."""
     d = np.ascontiguousarray(d_xyz, dtype=np.float64).reshape(-1, 3)
@@ -529,6 +548,10 @@ class Context:
                       stats=False):
         return tpcf_count_patches(self.handle, d.handle, r.handle, bins.handle, bins.nedges, d.npatch, stream, out,
                                   device_out, stats)
+
+    def jackknife(self, d: "Catalog", r: "Catalog", bins: "Bins", stream=None, estimator=TPCF_LS_EXACT, stats=False):
+        return tpcf_jackknife(self.handle, d.handle, r.handle, bins.handle, bins.nedges, d.npatch, stream, estimator,
+                              stats)
 
     def correlate(self, d_xyz, r_xyz, edges_rad, estimator=TPCF_LS_EXACT, stream=None, stats=False):
         return tpcf_correlate(self.handle, d_xyz, r_xyz, edges_rad, estimator, stream, stats)
