@@ -391,6 +391,14 @@ def run_jackknife(args):
             sep_ms.append(ev[0].elapsed_time(ev[1]))
         same = np.array_equal(sep_out.cpu().numpy().view(np.uint64), batched)
         assert same and st["pairs"] == pairs
+        for o in sub:
+            ctx.free(o[0])
+            ctx.free(o[1])
+        # leave-one-out jackknife of the full catalogs over the same patches
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loo, w_loo, cov, jst = ctx.jackknife(cd, cr, b, stream, stats=True)
+        loo_s = time.perf_counter() - t0
     gm, sm = statistics.median(graph_ms), statistics.median(sep_ms)
     print(json.dumps({
         "mode": "jackknife", "metric": METRIC, "value": pairs / gm * 1e3, "unit": UNIT,
@@ -405,7 +413,11 @@ def run_jackknife(args):
                   "launches_per_replay": st["launches"], "band_pairs": st["band_pairs"]},
         "separate": {"ms": sm, "pairs_per_s": pairs / sm * 1e3, "calls": 3 * int(len(nd_p)),
                      "launches": 3 * 2 * int(len(nd_p))},
-        "speedup_vs_separate": sm / gm, "histograms_identical": same}))
+        "speedup_vs_separate": sm / gm, "histograms_identical": same,
+        "leave_one_out": {"s": loo_s, "kernel_ms": jst["kernel_ms"], "pairs": jst["pairs"],
+                          "pairs_per_s": jst["pairs"] / loo_s,
+                          "what": "DD/DR/RR of the catalogs without each patch (512 resamplings), w and its "
+                                  "covariance: one launch over every pair of the full catalogs"}}))
     return 0
 
 

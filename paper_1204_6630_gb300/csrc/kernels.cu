@@ -536,6 +536,9 @@ __device__ __forceinline__ void unsettled_pair(const WorkDesc& wd, int sub, floa
     queue_pair<T>(wd, sub, ig, jg, hc);
 }
 
+// Diagonal handling of a tile (warp-uniform): none, keep j > i, keep j != i.
+enum { kDiagNone = 0, kDiagAbove = 1, kDiagOffSelf = 2 };
+
 // Element k of a register array without dynamic indexing (no local memory).
 template <int R>
 __device__ __forceinline__ float pick(const float (&v)[R], int k) {
@@ -558,22 +561,33 @@ __device__ __forceinline__ float pick(const float (&v)[R], int k) {
 template <int T, int R, int U, class JPoint>
 __device__ __forceinline__ void slow_group(const WorkDesc& wd, int sub, float (&e)[U][R], const float (&ax)[R],
                                            const float (&ay)[R], const float (&az)[R], const JPoint& j_point, int jj,
-                                           uint32_t ibase, uint32_t jbase, bool masked, const HistCol& hc) {
+                                           uint32_t ibase, uint32_t jbase, int diag, const HistCol& hc) {
     static_assert(U * R <= 32, "one bit per pair of the group");
-    if (wd.need_idx || masked) {
-        const SubProblem& sp = sub_of(wd, sub);
-        const uint32_t na = sp.na, nb = sp.nb;
-        const bool no_self = sp.no_self != 0;
+    // pairs outside the sub-problem (padding, the next segment) and, on tiles that
+    // meet the diagonal, pairs with j <= i (auto counts) or j == i (full square)
+    if (wd.need_idx) {
+        const uint32_t na = sub_of(wd, sub).na, nb = sub_of(wd, sub).nb;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t jg = jbase + (uint32_t)(jj + u);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint32_t ig = ibase + 32u * r;
-                const bool diag_ok = no_self ? jg != ig : jg > ig;
-                const bool ok = (!wd.need_idx || (jg < nb && ig < na)) && (!masked || diag_ok);
-                if (!ok) e[u][r] = -1.0f;
-            }
+            for (int r = 0; r < R; ++r)
+                if (!(jg < nb && ibase + 32u * r < na)) e[u][r] = -1.0f;
+        }
+    }
+    if (diag == kDiagAbove) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (!(jbase + (uint32_t)(jj + u) > ibase + 32u * r)) e[u][r] = -1.0f;
+        }
+    } else if (diag == kDiagOffSelf) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (jbase + (uint32_t)(jj + u) == ibase + 32u * r) e[u][r] = -1.0f;
         }
     }
     constexpr int D = kSlowPipe;  // loads run D - 1 j ahead of the reductions
@@ -768,8 +782,13 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
 
         const uint32_t jbase = cons.g.j0 + cons.t * wd.J;
         // tiles that meet the diagonal: j > i (auto counts) or j != i (full square without self pairs)
-        const bool masked = (sub_of(wd, cur_sub).auto_mode != 0 && jbase < cons.g.i0 + wd.I) ||
-                            (sub_of(wd, cur_sub).no_self != 0 && jbase < cons.g.i0 + wd.I && jbase + wd.J > cons.g.i0);
+        int diag = kDiagNone;
+        if (jbase < cons.g.i0 + wd.I) {
+            const SubProblem& dsp = sub_of(wd, cur_sub);
+            if (dsp.auto_mode) diag = kDiagAbove;
+            else if (dsp.no_self && jbase + wd.J > cons.g.i0) diag = kDiagOffSelf;
+        }
+        const bool masked = diag != kDiagNone;
         const int J = (int)wd.J;
         if constexpr (PACKED) {
             // Fast loop with packed FMA: one fma.rn.f32x2 gives the screen values of
@@ -805,7 +824,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                                         const float4 bxy = sj[2 * j], bzz = sj[2 * j + 1];
                                         return make_float4(bxy.x, bxy.z, bzz.x, 0.f);
                                     },
-                                    jj, ibase, jbase, masked, hc);
+                                    jj, ibase, jbase, diag, hc);
                 maybe_drain<T>(wd, cur_sub, hc);
             }
         } else if constexpr (MODE == kModeScreen) {
@@ -831,7 +850,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                 // AND of the group's screen values (a balanced tree, not a serial
                 // chain in front of the vote): negative when every pair is overflow
                 if (!__any_sync(0xffffffffu, and_tree<U * R>(&eu[0][0]) >= 0)) continue;
-                slow_group<T, R, U>(wd, cur_sub, eu, ax, ay, az, [&](int j) { return sj[j]; }, jj, ibase, jbase, masked,
+                slow_group<T, R, U>(wd, cur_sub, eu, ax, ay, az, [&](int j) { return sj[j]; }, jj, ibase, jbase, diag,
                                     hc);
                 maybe_drain<T>(wd, cur_sub, hc);
             }

@@ -892,7 +892,9 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         return launch_count(wd, sl, mode, ne, st);
     };
 
-    // ---- optional autotuning: time every fitting shape once, keep the fastest
+    // ---- optional autotuning: time every fitting shape on a bounded window of the
+    // work (about 8 items per SM, the same window of the walk for every shape),
+    // keep the one with the least time per pair
     if ((ctx->cfg.flags & TPCF_F_AUTOTUNE) && ctx->cfg.threads == 0 && ctx->cfg.jtile == 0) {
         const std::array<int, 5> key{mode, ne, nsub, ilog2_u64(all_pairs + 1), ilog2_u64(max_n + 1)};
         std::lock_guard<std::mutex> tl(ctx->tune_mu);
@@ -902,7 +904,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         } else {
             const int cand_t[3] = {128, 256, 512};
             const int cand_j[3] = {256, 512, 1024};
-            float best = 1e30f;
+            double best = 1e300;
             Shape best_sh = sh;
             cudaEvent_t a0, a1;
             cudaEventCreate(&a0);
@@ -912,6 +914,12 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
                     Shape c;
                     if (!shape_for(ctx, mode, ne, cand_t[ti], 8, cand_j[ji], 0, &c)) continue;
                     if (setup(c) != TPCF_OK) continue;
+                    const uint64_t window = (uint64_t)ctx->num_sms * 8;
+                    if (wd.item_hi - wd.item_lo > window) wd.item_hi = wd.item_lo + window;
+                    uint64_t wpairs = 0;
+                    for (int s2 = 0; s2 < nsub; ++s2)
+                        wpairs += range_pairs(subs[s2], wd.item_lo, wd.item_hi, wd.I, wd.Jc, wd.J);
+                    if (wpairs == 0) continue;
                     cudaMemsetAsync(acc, 0, acc_words * 8, st);
                     if (capture && count_set_smem_limit(mode, c.threads, c.ipt, c.smem) != cudaSuccess) continue;
                     cudaEventRecord(a0, st);
@@ -919,7 +927,8 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
                     cudaEventRecord(a1, st);
                     float ms = 1e30f;
                     if (cudaEventSynchronize(a1) == cudaSuccess) cudaEventElapsedTime(&ms, a0, a1);
-                    if (ms < best) { best = ms; best_sh = c; }
+                    const double per_pair = (double)ms / (double)wpairs;
+                    if (per_pair < best) { best = per_pair; best_sh = c; }
                 }
             }
             cudaEventDestroy(a0);

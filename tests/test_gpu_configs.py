@@ -135,3 +135,24 @@ def test_sphere_large_full_size(T):
         got = ctx.count_all(ctx.catalog(ds), ctx.catalog(rs), b)
     for g_, o_ in zip(got, oracle_all(ds, rs, w.edges)):
         np.testing.assert_array_equal(g_, o_)
+
+
+def test_jackknife_leave_one_out_full_size(T):
+    d, r, doff, roff = synth.jackknife_patches(seed=0)
+    edges = synth.linear_edges(0.0, 5.0, 40)
+    with T.Context() as ctx:
+        cd, cr, b = ctx.catalog(d, offsets=doff), ctx.catalog(r, offsets=roff), ctx.bins(edges)
+        loo, w, cov, st = ctx.jackknife(cd, cr, b, stats=True)
+        assert st["device_error"] == 0
+        nd, nr = len(d), len(r)
+        for p in range(len(doff) - 1):
+            a, c = nd - int(doff[p + 1] - doff[p]), nr - int(roff[p + 1] - roff[p])
+            assert int(loo[p, 0].sum()) == a * (a - 1) // 2 and int(loo[p, 1].sum()) == a * c
+            assert int(loo[p, 2].sum()) == c * (c - 1) // 2
+        for p in (0, 311):  # two resamplings recounted from scratch
+            dp = np.concatenate([d[:doff[p]], d[doff[p + 1]:]])
+            rp = np.concatenate([r[:roff[p]], r[roff[p + 1]:]])
+            got = ctx.count_all(ctx.catalog(dp), ctx.catalog(rp), b)
+            for k in range(3):
+                np.testing.assert_array_equal(loo[p, k], got[k], err_msg=f"patch {p} kind {k}")
+    assert np.all(np.isfinite(np.diag(cov)))
