@@ -51,7 +51,10 @@ def _bind(lib):
     lib.oracle_count_auto_rows.argtypes = [dp, u64, dp, ctypes.c_int, u64, u64, u64p]
     lib.oracle_count_cross_rows.argtypes = [dp, u64, dp, u64, dp, ctypes.c_int, u64, u64, u64p]
     lib.oracle_estimate.argtypes = [u64p, u64p, u64p, ctypes.c_int, u64, u64, ctypes.c_int, dp]
-    for f in (lib.oracle_count_auto_rows, lib.oracle_count_cross_rows, lib.oracle_estimate):
+    lib.oracle_count_auto3_rows.argtypes = [dp, u64, dp, ctypes.c_int, u64, u64, u64p]
+    lib.oracle_count_cross3_rows.argtypes = [dp, u64, dp, u64, dp, ctypes.c_int, u64, u64, u64p]
+    for f in (lib.oracle_count_auto_rows, lib.oracle_count_cross_rows, lib.oracle_estimate,
+              lib.oracle_count_auto3_rows, lib.oracle_count_cross3_rows):
         f.restype = ctypes.c_int
     return lib
 
@@ -78,7 +81,7 @@ def _uptr(a: np.ndarray):
 def _as_xyz(x) -> np.ndarray:
     a = np.ascontiguousarray(x, dtype=np.float64)
     if a.ndim != 2 or a.shape[1] != 3:
-        raise ValueError("catalog must be an (n, 3) array of unit vectors")
+        raise ValueError("catalog must be an (n, 3) array")
     return a
 
 
@@ -93,20 +96,23 @@ def _row_splits(n_rows: int, weights, parts: int) -> list[tuple[int, int]]:
     return [(int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
 
 
-def count_auto(xyz, edges, threads: int = 1, lib=None) -> np.ndarray:
+def count_auto(xyz, edges, threads: int = 1, lib=None, euclid: bool = False) -> np.ndarray:
     """DD or RR histogram over unordered pairs i < j (B + 2 uint64 entries).
 
     ``threads > 1`` splits the rows of the triangle across host threads (the
-    C call releases the GIL) and sums the per-range histograms.
+    C call releases the GIL) and sums the per-range histograms.  ``euclid``:
+    the 3-D variant (Euclidean distances between arbitrary points, edges in
+    the same length unit) instead of angles between unit vectors.
     """
     lib = lib or load()
     a = _as_xyz(xyz)
     e = np.ascontiguousarray(edges, dtype=np.float64)
     n = a.shape[0]
+    fn = lib.oracle_count_auto3_rows if euclid else lib.oracle_count_auto_rows
 
     def run(r):
         h = np.zeros(len(e) + 1, dtype=np.uint64)
-        rc = lib.oracle_count_auto_rows(_dptr(a), n, _dptr(e), len(e), r[0], r[1], _uptr(h))
+        rc = fn(_dptr(a), n, _dptr(e), len(e), r[0], r[1], _uptr(h))
         if rc != 0:
             raise ValueError("oracle_count_auto: invalid arguments")
         return h
@@ -118,18 +124,18 @@ def count_auto(xyz, edges, threads: int = 1, lib=None) -> np.ndarray:
         return np.sum(list(ex.map(run, ranges)), axis=0, dtype=np.uint64)
 
 
-def count_cross(xyz_d, xyz_r, edges, threads: int = 1, lib=None) -> np.ndarray:
-    """DR histogram over all ordered pairs (i in D, j in R) (B + 2 uint64 entries)."""
+def count_cross(xyz_d, xyz_r, edges, threads: int = 1, lib=None, euclid: bool = False) -> np.ndarray:
+    """DR histogram over all ordered pairs (i in D, j in R) (B + 2 uint64 entries); ``euclid`` as above."""
     lib = lib or load()
     d = _as_xyz(xyz_d)
     r_ = _as_xyz(xyz_r)
     e = np.ascontiguousarray(edges, dtype=np.float64)
     nd, nr = d.shape[0], r_.shape[0]
+    fn = lib.oracle_count_cross3_rows if euclid else lib.oracle_count_cross_rows
 
     def run(rg):
         h = np.zeros(len(e) + 1, dtype=np.uint64)
-        rc = lib.oracle_count_cross_rows(_dptr(d), nd, _dptr(r_), nr, _dptr(e), len(e),
-                                         rg[0], rg[1], _uptr(h))
+        rc = fn(_dptr(d), nd, _dptr(r_), nr, _dptr(e), len(e), rg[0], rg[1], _uptr(h))
         if rc != 0:
             raise ValueError("oracle_count_cross: invalid arguments")
         return h

@@ -40,7 +40,8 @@
 #define ORACLE_OK 0
 #define ORACLE_EINVAL 1
 
-/* Histogram index of an angle: the number of edges t_m with t_m <= theta.
+/* Histogram index of a separation (an angle, or a distance in the 3-D
+ * variant): the number of edges t_m with t_m <= theta.
  * 0 = underflow, k + 1 = bin k, nedges = overflow. */
 static int bin_of_angle(double theta, const double *edges, int nedges)
 {
@@ -119,6 +120,66 @@ int oracle_count_cross(const double *xyz_d, uint64_t nd, const double *xyz_r, ui
                        const double *edges, int nedges, uint64_t *hist)
 {
     return oracle_count_cross_rows(xyz_d, nd, xyz_r, nr, edges, nedges, 0, nd, hist);
+}
+
+/* ---------------------------------------------------------------- 3-D variant
+ * Section 1 defines the two-point function for a spatial separation r as well
+ * as for an angle, and notes that the angular results extend to the
+ * 3-dimensional case.  Points are arbitrary finite 3-D positions; the
+ * separation is the Euclidean distance
+ *     r = sqrt(((xa - xb)^2 + (ya - yb)^2) + (za - zb)^2),
+ * every operation rounded to binary64 in that order (differences, squares,
+ * left-to-right sums, no fused multiply-add), sqrt from the C library
+ * (correctly rounded).  Edges r_0 < ... < r_B are finite and >= 0; the
+ * histogram index is the number of edges r_m with r_m <= r, as for angles. */
+static double pair_distance(const double *a, const double *b)
+{
+    double dx = a[0] - b[0];
+    double dy = a[1] - b[1];
+    double dz = a[2] - b[2];
+    return sqrt((dx * dx + dy * dy) + dz * dz);
+}
+
+static int edges3_ok(const double *edges, int nedges)
+{
+    if (nedges < 2)
+        return 0;
+    for (int m = 0; m < nedges; ++m)
+        if (!(edges[m] >= 0.0 && edges[m] <= 1.7976931348623157e308))
+            return 0;
+    for (int m = 1; m < nedges; ++m)
+        if (!(edges[m] > edges[m - 1]))
+            return 0;
+    return 1;
+}
+
+/* Auto count of a 3-D catalog: unordered pairs i < j, rows [row_begin, row_end). */
+int oracle_count_auto3_rows(const double *xyz, uint64_t n, const double *edges, int nedges,
+                            uint64_t row_begin, uint64_t row_end, uint64_t *hist)
+{
+    if (!edges3_ok(edges, nedges) || row_begin > row_end || row_end > n)
+        return ORACLE_EINVAL;
+    for (int h = 0; h <= nedges; ++h)
+        hist[h] = 0;
+    for (uint64_t i = row_begin; i < row_end; ++i)
+        for (uint64_t j = i + 1; j < n; ++j)
+            hist[bin_of_angle(pair_distance(xyz + 3 * i, xyz + 3 * j), edges, nedges)] += 1;
+    return ORACLE_OK;
+}
+
+/* Cross count of two 3-D catalogs: all ordered pairs, rows of D in [row_begin, row_end). */
+int oracle_count_cross3_rows(const double *xyz_d, uint64_t nd, const double *xyz_r, uint64_t nr,
+                             const double *edges, int nedges, uint64_t row_begin,
+                             uint64_t row_end, uint64_t *hist)
+{
+    if (!edges3_ok(edges, nedges) || row_begin > row_end || row_end > nd)
+        return ORACLE_EINVAL;
+    for (int h = 0; h <= nedges; ++h)
+        hist[h] = 0;
+    for (uint64_t i = row_begin; i < row_end; ++i)
+        for (uint64_t j = 0; j < nr; ++j)
+            hist[bin_of_angle(pair_distance(xyz_d + 3 * i, xyz_r + 3 * j), edges, nedges)] += 1;
+    return ORACLE_OK;
 }
 
 /* Landy-Szalay estimator, Eq. 1, for nbins bins.

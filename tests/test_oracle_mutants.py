@@ -26,10 +26,15 @@ MUTANTS = {
                     "d = (a[0] * b[0] + a[1] * b[1]);"),
     "transposed_operand": ("a[1] * b[1]", "a[1] * b[0]"),
     "edge_exclusive": ("if (edges[m] <= theta)", "if (edges[m] < theta)"),
-    "self_pairs_included": ("for (uint64_t j = i + 1; j < n; ++j)",
-                            "for (uint64_t j = i; j < n; ++j)"),
-    "cross_skips_first": ("for (uint64_t j = 0; j < nr; ++j)",
-                          "for (uint64_t j = 1; j < nr; ++j)"),
+    "self_pairs_included": ("for (uint64_t j = i + 1; j < n; ++j)\n            hist[bin_of_angle(pair_angle(",
+                            "for (uint64_t j = i; j < n; ++j)\n            hist[bin_of_angle(pair_angle("),
+    "cross_skips_first": ("for (uint64_t j = 0; j < nr; ++j)\n            hist[bin_of_angle(pair_angle(",
+                          "for (uint64_t j = 1; j < nr; ++j)\n            hist[bin_of_angle(pair_angle("),
+    "3d_drop_z_term": ("return sqrt((dx * dx + dy * dy) + dz * dz);", "return sqrt(dx * dx + dy * dy);"),
+    "3d_sum_not_difference": ("double dy = a[1] - b[1];", "double dy = a[1] + b[1];"),
+    "3d_squared_distance": ("return sqrt((dx * dx + dy * dy) + dz * dz);", "return (dx * dx + dy * dy) + dz * dz;"),
+    "3d_self_pairs_included": ("for (uint64_t j = i + 1; j < n; ++j)\n            hist[bin_of_angle(pair_distance(",
+                               "for (uint64_t j = i; j < n; ++j)\n            hist[bin_of_angle(pair_distance("),
     "no_clamp": ("    if (d > 1.0)\n        d = 1.0;\n", ""),
     "estimator_sign": ("((ndd - 2.0 * ndr) + nrr)", "((ndd + 2.0 * ndr) + nrr)"),
     "dr_normaliser": ("double pairs_dr = (double)nd * (double)nr;",
@@ -79,6 +84,25 @@ def battery(lib) -> list[str]:
     if v is not None:
         h = oracle.count_auto(np.stack([v, v]), np.array([0.0, 1e-6, 1.0]), lib=lib)
         check("clamp", np.array_equal(h, [0, 1, 0, 0]))
+
+    # 3-D variant: exact Pythagorean distances on bin edges, totals, a translated copy
+    pts = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, 2.0], [3.0, 4.0, 0.0], [2.0, 3.0, 6.0], [1.0, 4.0, 8.0]])
+    e3 = np.array([0.5, 3.0, 5.0, 7.0, 9.0, 100.0])
+    h3 = oracle.count_auto(pts[:1], e3, lib=lib, euclid=True)
+    check("3d_single_point", int(h3.sum()) == 0)
+    h3 = oracle.count_cross(pts[:1], pts[1:], e3, lib=lib, euclid=True)
+    check("3d_pythagorean", np.array_equal(h3, [0, 0, 1, 1, 1, 1, 0]))
+    g3 = np.random.default_rng(5).uniform(-20, 20, (60, 3))
+    e3b = np.array([0.0, 4.0, 9.0, 20.0])
+    check("3d_total", int(oracle.count_auto(g3, e3b, lib=lib, euclid=True).sum()) == 60 * 59 // 2)
+    check("3d_translation", np.array_equal(oracle.count_cross(g3, g3[:10] + 64.0, e3b, lib=lib, euclid=True),
+                                           oracle.count_cross(g3 - 64.0, g3[:10], e3b, lib=lib, euclid=True)))
+    want3 = np.zeros(len(e3b) + 1, np.uint64)
+    for a in g3[:20]:
+        for b in g3[20:]:
+            x, y, z = float(a[0]) - float(b[0]), float(a[1]) - float(b[1]), float(a[2]) - float(b[2])
+            want3[sum(1 for t in e3b if t <= math.sqrt((x * x + y * y) + z * z))] += 1
+    check("3d_brute_force", np.array_equal(oracle.count_cross(g3[:20], g3[20:], e3b, lib=lib, euclid=True), want3))
 
     w = oracle.estimate([6, 3, 0], [15, 10, 5], [10, 5, 10], 4, 5, oracle.LS_EXACT, lib=lib)
     check("estimator_exact", list(w) == [0.5, 0.0, 0.5])
