@@ -192,6 +192,35 @@ int tpcf_bins_destroy(tpcf_bins *bins);
 int tpcf_bins_thresholds(const double *edges_rad, int nedges, double guard_band, double *cos_thr,
                          float *lo, float *hi, int *verified);
 
+/* ------------------------------------------------------------------ 3-D variant
+ * Section 1 defines the two-point function for a spatial separation r as well
+ * as for an angle and notes that the angular method extends to 3 dimensions.
+ * A 3-D catalog holds arbitrary finite points (|coordinate| <= 1e28); the
+ * separation of a pair is r = sqrt(((xa - xb)^2 + (ya - yb)^2) + (za - zb)^2)
+ * in binary64 in that order (no FMA) with the C library's correctly rounded
+ * sqrt, and 3-D bins hold distance edges r_0 < ... < r_B (>= 0, r_B > 0,
+ * r_B <= 1e18) with the histogram layout and index rule of the angular bins.
+ * The GPU compares d^2 with S_k = the smallest double s with sqrt(s) >= r_k
+ * (host bisection), so counts equal the definition exactly; an FP32 screen of
+ * |a' - b'|^2 decides every pair outside a proven band (whose width grows with
+ * the points' largest norm) and the rest are recomputed in binary64.
+ * tpcf_count_auto / tpcf_count_cross / tpcf_count_all / tpcf_count_patches /
+ * tpcf_jackknife / tpcf_graph_create count 3-D catalogs with 3-D bins (mixing
+ * 3-D and angular objects returns TPCF_EINVAL).
+ *
+ * tpcf_catalog_create_3d: as tpcf_catalog_create (offsets/nseg as
+ * tpcf_catalog_create_segmented, or NULL/0), points validated as finite and
+ * inside the coordinate limit; reordered along a 3-D Morton curve over the
+ * catalog's bounding box.
+ * tpcf_bins_create_3d: distance edges; TPCF_EINVAL outside the limits above.
+ * tpcf_bins_thresholds_3d: host-only S_k for the edges, verified[k] = 1 when
+ * the predicate sqrt(s) >= r_k flips exactly once on 64 doubles each side of
+ * S_k (any output may be NULL). */
+int tpcf_catalog_create_3d(tpcf_ctx *ctx, const double *xyz, uint64_t n, int where, const uint64_t *offsets,
+                           int nseg, void *stream, tpcf_catalog **out);
+int tpcf_bins_create_3d(tpcf_ctx *ctx, const double *edges, int nedges, tpcf_bins **out);
+int tpcf_bins_thresholds_3d(const double *edges, int nedges, double *sq_thr, int *verified);
+
 /* ------------------------------------------------------------------ counting
  * hist: B + 2 uint64 (layout above).  where = TPCF_HOST: the call is
  * synchronous, hist is host memory, st (optional) receives the statistics.

@@ -175,7 +175,8 @@ def correlation(data, rand, edges, estimator: int = LS_EXACT, threads: int = 1):
     return dd, dr, rr, w
 
 
-def jackknife(data, rand, data_offsets, rand_offsets, edges, estimator: int = LS_EXACT, threads: int = 1):
+def jackknife(data, rand, data_offsets, rand_offsets, edges, estimator: int = LS_EXACT, threads: int = 1,
+              euclid: bool = False):
     """Delete-one jackknife of the three histograms over the patches of a segmented catalog pair.
 
     Patch p holds ``data[data_offsets[p]:data_offsets[p+1]]`` and likewise for
@@ -184,7 +185,7 @@ def jackknife(data, rand, data_offsets, rand_offsets, edges, estimator: int = LS
     shortcut); w of each resampling follows from ``estimate`` with the remaining
     point counts (NaN when fewer than 2 points remain), and the covariance is
     C_ab = (P - 1)/P sum_p (w_pa - mean_a)(w_pb - mean_b), the sums taken in
-    patch order.
+    patch order.  ``euclid``: the 3-D variant (distances).
 
     Returns ``(loo, w, cov)``: loo (P, 3, B + 2) uint64, w (P, B), cov (B, B).
     """
@@ -198,9 +199,9 @@ def jackknife(data, rand, data_offsets, rand_offsets, edges, estimator: int = LS
     for p in range(P):
         d = np.concatenate([data[:doff[p]], data[doff[p + 1]:]])
         r = np.concatenate([rand[:roff[p]], rand[roff[p + 1]:]])
-        loo[p, 0] = count_auto(d, edges, threads)
-        loo[p, 1] = count_cross(d, r, edges, threads)
-        loo[p, 2] = count_auto(r, edges, threads)
+        loo[p, 0] = count_auto(d, edges, threads, euclid=euclid)
+        loo[p, 1] = count_cross(d, r, edges, threads, euclid=euclid)
+        loo[p, 2] = count_auto(r, edges, threads, euclid=euclid)
         if len(d) >= 2 and len(r) >= 2:
             w[p] = estimate(loo[p, 0, 1:-1], loo[p, 1, 1:-1], loo[p, 2, 1:-1], len(d), len(r), estimator)
     cov = None

@@ -73,7 +73,9 @@ struct tpcf_catalog {
     std::vector<uint64_t> seg_start;  // device position of each segment's first point (multiples of
                                       // kSegAlign; zero vectors fill the gaps), size nseg + 1
     uint32_t* seg_of_block = nullptr;  // device: segment of each kSegAlign-point block (segmented only)
-    double eps_max = 0.0;           // bound on | |v|^2 - 1 | over the points
+    double eps_max = 0.0;           // bound on | |v|^2 - 1 | over the points (unit-vector catalogs)
+    bool euclid = false;            // 3-D catalog: arbitrary finite points (distances, not angles)
+    double norm_max = 0.0;          // bound on |v| over the points (3-D catalogs)
     cudaStream_t free_stream = nullptr;  // stream-ordered buffers: freed in this stream's order
     bool stream_ordered = false;
 };
@@ -93,6 +95,16 @@ struct tpcf_bins {
     tpcf::BinsDev* dev_desc = nullptr;   // device copy of `host`
     cudaStream_t free_stream = nullptr;
     bool stream_ordered = false;
+    // 3-D variant: edges are distances; the device arrays depend on a bound M of
+    // the points' norms and are built per power of two 2^k >= M (key k)
+    bool euclid = false;
+    struct Set {
+        void* dev_buf = nullptr;
+        tpcf::BinsDev host;
+        tpcf::BinsDev* dev_desc = nullptr;
+    };
+    std::mutex set_mu;
+    std::map<int, Set> sets;
 };
 
 #define CUDA_TRY(ctx, call)                                                                    \
@@ -109,7 +121,7 @@ namespace tpcf {
 // (stream_ordered = true: no device-wide synchronisation; used by the job
 // server) or with cudaMalloc/cudaFree (the public entry points).
 int catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where, const uint64_t* offsets,
-                        int nseg, cudaStream_t st, bool stream_ordered, tpcf_catalog** out);
+                        int nseg, cudaStream_t st, bool stream_ordered, tpcf_catalog** out, bool euclid = false);
 int catalog_destroy_impl(tpcf_catalog* c);
 int bins_create_impl(tpcf_ctx* ctx, const double* edges, int nedges, cudaStream_t st, bool stream_ordered,
                      tpcf_bins** out);

@@ -212,7 +212,7 @@ __device__ void cursor_next(const WorkDesc& wd, Cursor& c) {
 // ============================================================== shared-memory layout
 // Kernel variants: FP32 screen with scalar FMA, all-binary64 comparator, FP32
 // screen with packed FP32x2 FMA (j-points staged as (x,x,y,y),(z,z,0,0)).
-enum KernelMode { kModeScreen = 0, kModePlain = 1, kModeScreen2 = 2 };
+enum KernelMode { kModeScreen = 0, kModePlain = 1, kModeScreen2 = 2, kModeEuclid = 3 };
 
 // Block-wide control words (all int32 in shared memory).
 enum Ctl { kCtlAbort = 0, kCtlWarpsDone = 1, kCtlIssued = 2, kCtlRelease = 8, kCtlQueue = 24,
@@ -240,7 +240,7 @@ __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x
 __host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S, int nedges) {
     SmemLayout L;
     const bool plain = mode == kModePlain;
-    const uint32_t pt = mode == kModeScreen ? 16u : 32u;
+    const uint32_t pt = (mode == kModeScreen || mode == kModeEuclid) ? 16u : 32u;
     uint32_t off = 0;
     L.bars = off; off += kMaxStages * 8;
     L.ctl = off; off += kCtlWords * 4;
@@ -437,9 +437,85 @@ __device__ __forceinline__ uint32_t lut_entry(const WorkDesc& wd, float e) {
 // Histogram index of an unsettled pair: the FP32 comparison with the edges
 // its LUT entry leaves open, else (inside a guard band) the binary64
 // recomputation.  Band statistics are added to *band, *mism.
+// ---- 3-D variant (Euclidean separations)
+// z = fl32(|a' - b'|^2): differences, then a fused sum of squares.
+__device__ __forceinline__ float euclid_z(float ax, float ay, float az, const float4& b) {
+    const float dx = ax - b.x, dy = ay - b.y, dz = az - b.z;
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+// LUT cell of z: constant-ratio cells, clamp((bits(z) - zbits0) >> zshift) (z >= 0).
+__device__ __forceinline__ uint32_t euclid_cell_addr(const WorkDesc& wd, float z, uint32_t lut_base) {
+    int k = ((int)__float_as_uint(z) - wd.zbits0) >> wd.zshift;
+    k = min(max(k, 0), kLutCells - 1);
+    return lut_base + (uint32_t)k * 4u;
+}
+
+// binary64 d^2 in the definition's order: differences, squares, left-to-right sum.
+__device__ __forceinline__ double dist2_64(const Point64& a, const Point64& b) {
+    const double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y), dz = __dsub_rn(a.z, b.z);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// A 3-D pair whose LUT entry left edges [P, Q) open: z against the z-space
+// bounds (increasing with the edge index; z >= zhi_m proves d^2 >= S_m, z <
+// zlo_m proves d^2 < S_m).  Returns h >= 0 when z settles it; otherwise -1 and
+// the edges still open, [*lo, *hi).
+__device__ __forceinline__ int euclid_resolve(const WorkDesc& wd, float z, uint32_t ent, int* lo_out, int* hi_out) {
+    const float* zlo = sptr<const float>(wd.off_zlo);
+    const float* zhi = sptr<const float>(wd.off_zhi);
+    const int Q = (int)((ent >> 12) & 0xfffu);
+    int lo = (int)(ent & 0xfffu), hi = Q;
+    while (lo < hi) {  // first m in [P, Q) with z < zhi[m]: the edges below are crossed
+        const int mid = (lo + hi) >> 1;
+        if (z >= zhi[mid]) lo = mid + 1; else hi = mid;
+    }
+    if (lo == Q || z < zlo[lo]) return lo;
+    int a = lo + 1, c = Q;  // first m > lo with z < zlo[m]: the edges from there on are not crossed
+    while (a < c) {
+        const int mid = (a + c) >> 1;
+        if (z >= zlo[mid]) a = mid + 1; else c = mid;
+    }
+    *lo_out = lo;
+    *hi_out = a;
+    return -1;
+}
+
+// Index of a 3-D pair decided in binary64 over the open edges [lo, hi)
+// (S increasing: count the edges with d^2 >= S_m); h32 from the FP32 value
+// against RN(S_m) for the statistics.
+__device__ __forceinline__ int euclid_band_index(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg, float z, int lo,
+                                                 int hi, uint32_t* mismatch) {
+    const SubProblem& sp = sub_of(wd, sub);
+    const double* sthr = sptr<const double>(wd.off_cthr);
+    const float* s32 = sptr<const float>(wd.off_c32);
+    const double d2 = dist2_64(ldg_point(sp.a64 + ig), ldg_point(sp.b64 + jg));
+    int h = lo, h32 = lo;
+    for (int m = lo; m < hi; ++m) {
+        h += (d2 >= sthr[m]);
+        h32 += (z >= s32[m]);
+    }
+    *mismatch = (h != h32) ? 1u : 0u;
+    return h;
+}
+
 __device__ __forceinline__ int classify_unsettled(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg,
                                                   uint32_t* band, uint32_t* mism) {
     const SubProblem& sp = sub_of(wd, sub);
+    if (wd.euclid) {
+        const float4 a = __ldg(sp.a32 + ig), b = __ldg(sp.b32 + jg);
+        const float z = euclid_z(a.x, a.y, a.z, b);
+        const uint32_t ent = ld_shared_u32(euclid_cell_addr(wd, z, smem_addr(dyn_smem) + wd.off_lut));
+        if ((int)ent >= 0) return (int)(ent / (uint32_t)(4 * (blockDim.x / 2)));  // settled (not expected)
+        int lo = 0, hi = 0;
+        const int h0 = euclid_resolve(wd, z, ent, &lo, &hi);
+        if (h0 >= 0) return h0;
+        uint32_t mm;
+        const int h = euclid_band_index(wd, sub, ig, jg, z, lo, hi, &mm);
+        *band += 1;
+        *mism += mm;
+        return h;
+    }
     const float e = screen_value(wd, sp, ig, jg);
     const uint32_t ent = lut_entry(wd, e);
     if ((int)ent >= 0) return (int)(ent / (uint32_t)(4 * (blockDim.x / 2)));  // settled (not expected)
@@ -624,6 +700,77 @@ __device__ __forceinline__ void slow_group(const WorkDesc& wd, int sub, float (&
     }
 }
 
+// Slow path of the 3-D variant for a group of U j: z = fl32(|a' - b'|^2) is
+// recomputed for all R pairs of every lane (pairs that must not be counted get
+// z = +inf, the overflow cell), its constant-ratio LUT cell gives a settled
+// row (one shared load, one reduction) or the edges left open, which the
+// z-space bounds decide inline or the binary64 recheck (queue) settles.  Same
+// load-before-reduction pipelining as the angular slow path.
+template <int T, int R, int U, class JPoint>
+__device__ __forceinline__ void slow_group_euclid(const WorkDesc& wd, int sub, const float (&ax)[R],
+                                                  const float (&ay)[R], const float (&az)[R], const JPoint& j_point,
+                                                  int jj, uint32_t ibase, uint32_t jbase, int diag,
+                                                  const HistCol& hc) {
+    static_assert(U * R <= 32, "one bit per pair of the group");
+    constexpr int D = kSlowPipe;
+    const uint32_t lut_base = smem_addr(dyn_smem) + wd.off_lut;
+    uint32_t na = 0xffffffffu, nb = 0xffffffffu;
+    if (wd.need_idx) {
+        na = sub_of(wd, sub).na;
+        nb = sub_of(wd, sub).nb;
+    }
+    uint32_t ent[D][R];
+    uint32_t um = 0;  // unsettled pairs of this lane: pair k = u * R + r at bit U * R - 1 - k
+#pragma unroll
+    for (int u = 0; u < U + D - 1; ++u) {
+        if (u < U) {
+            const float4 b = j_point(jj + u);
+            const uint32_t jg = jbase + (uint32_t)(jj + u);
+            float z[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) z[r] = euclid_z(ax[r], ay[r], az[r], b);
+            if (wd.need_idx) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (!(jg < nb && ibase + 32u * r < na)) z[r] = INFINITY;
+            }
+            if (diag == kDiagAbove) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (!(jg > ibase + 32u * r)) z[r] = INFINITY;
+            } else if (diag == kDiagOffSelf) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (jg == ibase + 32u * r) z[r] = INFINITY;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(ent[u % D][r]) : "r"(euclid_cell_addr(wd, z[r], lut_base)));
+        }
+        if (u >= D - 1) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t x = ent[(u - (D - 1)) % D][r];
+                if ((int)x >= 0) red_add_shared(hc.addr + x, hc.inc);
+                um = __funnelshift_l(x, um, 1);  // (um << 1) | (x >> 31)
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, um != 0u)) {
+        while (um) {  // one iteration per unsettled pair of the lane
+            const int k = U * R - 1 - (31 - __clz(um));
+            um &= ~(1u << (U * R - 1 - k));
+            const int u = k / R, r = k % R;
+            const float z = euclid_z(pick(ax, r), pick(ay, r), pick(az, r), j_point(jj + u));
+            const uint32_t x = ld_shared_u32(euclid_cell_addr(wd, z, lut_base));
+            int lo = 0, hi = 0;
+            const int h = euclid_resolve(wd, z, x, &lo, &hi);
+            if (h >= 0) hist_inc<T>(hc, h);
+            else queue_pair<T>(wd, sub, ibase + 32u * (uint32_t)r, jbase + (uint32_t)(jj + u), hc);
+        }
+    }
+}
+
 // After a group of slow j: drain the warp's queue once it is half full.
 template <int T>
 __device__ __forceinline__ void maybe_drain(const WorkDesc& wd, int sub, const HistCol& hc) {
@@ -647,6 +794,7 @@ template <int T, int R, int MODE>
 __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ WorkDesc wd) {
     constexpr bool PLAIN = MODE == kModePlain;
     constexpr bool PACKED = MODE == kModeScreen2;
+    constexpr bool SCALAR = MODE == kModeScreen || MODE == kModeEuclid;  // FP32 i-points as scalars
     constexpr int W = T / 32;
     const uint32_t S = wd.stages;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -679,6 +827,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         mbar_expect_tx(&bars[seq % S], wd.stage_bytes);
         const void* src = PLAIN ? (const void*)(sp.b64 + jbase)
                                 : PACKED ? (const void*)(sp.b32x2 + 2ull * jbase) : (const void*)(sp.b32 + jbase);
+        // (the screen and the 3-D variant both stage FP32 points as float4)
         bulk_copy_g2s(dst, src, wd.stage_bytes, &bars[seq % S]);
     };
 
@@ -701,7 +850,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     int cur_sub = -1;
     unsigned long long* cur_hist = nullptr;  // the histogram this warp's counters belong to
     uint32_t j_since_flush = 0;
-    float ax[MODE == kModeScreen ? R : 1], ay[MODE == kModeScreen ? R : 1], az[MODE == kModeScreen ? R : 1];
+    float ax[SCALAR ? R : 1], ay[SCALAR ? R : 1], az[SCALAR ? R : 1];
     unsigned long long px[PACKED ? R / 2 : 1], py[PACKED ? R / 2 : 1], pz[PACKED ? R / 2 : 1];
     double dx[PLAIN ? R : 1], dy[PLAIN ? R : 1], dz[PLAIN ? R : 1];
     uint32_t ibase = 0;
@@ -827,6 +976,28 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                                     jj, ibase, jbase, diag, hc);
                 maybe_drain<T>(wd, cur_sub, hc);
             }
+        } else if constexpr (MODE == kModeEuclid) {
+            // 3-D fast loop: e = H - |a' - b'|^2 as three differences and a negated
+            // fused sum of squares; e < 0 proves d^2 > S_B (every pair overflow)
+            const float4* sj = sptr<const float4>(wd.off_stage + stage * wd.stage_bytes);
+            constexpr int U = R >= 16 ? 2 : 4;
+#pragma unroll 2
+            for (int jj = 0; jj < J; jj += U) {
+                float eu[U][R];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float4 b = sj[jj + u];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float dx = ax[r] - b.x, dy = ay[r] - b.y, dz = az[r] - b.z;
+                        eu[u][r] = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, wd.neg_fast_t)));
+                    }
+                }
+                if (!__any_sync(0xffffffffu, and_tree<U * R>(&eu[0][0]) >= 0)) continue;
+                slow_group_euclid<T, R, U>(wd, cur_sub, ax, ay, az, [&](int j) { return sj[j]; }, jj, ibase, jbase,
+                                           diag, hc);
+                maybe_drain<T>(wd, cur_sub, hc);
+            }
         } else if constexpr (MODE == kModeScreen) {
             const float4* sj = sptr<const float4>(wd.off_stage + stage * wd.stage_bytes);
             // Fast loop: e = FP32 dot minus the range offset T for R i-points; the AND
@@ -865,6 +1036,21 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                 const uint32_t jg = jbase + (uint32_t)jj;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
+                    if (wd.euclid) {
+                        // 3-D: h = number of edges m with d^2 >= S_m (S increasing); d^2 >= S_B is overflow
+                        const double ex = __dsub_rn(dx[r], b.x), ey = __dsub_rn(dy[r], b.y), ez = __dsub_rn(dz[r], b.z);
+                        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+                        const uint32_t ig = ibase + 32u * r;
+                        if (d2 < wd.cos_last && ig < na && jg < nb && (!masked || (no_self ? jg != ig : jg > ig))) {
+                            int lo = 0, hi = ne;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (d2 >= cthr[mid]) lo = mid + 1; else hi = mid;
+                            }
+                            hist_inc<T>(hc, lo);
+                        }
+                        continue;
+                    }
                     const double d = __dadd_rn(__dadd_rn(__dmul_rn(dx[r], b.x), __dmul_rn(dy[r], b.y)),
                                                __dmul_rn(dz[r], b.z));
                     if (d > wd.cos_last) {
@@ -1019,10 +1205,68 @@ __device__ __forceinline__ uint32_t cell_key(double x, double y, double z) {
     return (face << 28) | (spread14((uint32_t)qu) << 1) | spread14((uint32_t)qv);
 }
 
-// Sort keys and validation; eps_word receives the largest | |v|^2 - 1 | (as
-// the bits of a non-negative double, whose order is that of the integers).
+// Order-preserving map of a double to an unsigned 64-bit key (and back).
+__device__ __forceinline__ unsigned long long dkey_of(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dval_of(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+// Bounding box of a 3-D catalog: bbox[0..2] = min keys, bbox[3..5] = max keys
+// (initialised to ~0 and 0 by the caller).
+__global__ void prep_bbox_kernel(const double* __restrict__ xyz, uint32_t n, unsigned long long* bbox) {
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double v = xyz[3ull * i + c];
+            if (!isfinite(v)) continue;
+            const unsigned long long k = dkey_of(v);
+            lo[c] = k < lo[c] ? k : lo[c];
+            hi[c] = k > hi[c] ? k : hi[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        atomicMin(bbox + c, lo[c]);
+        atomicMax(bbox + 3 + c, hi[c]);
+    }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {  // 10 bits -> every third bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// 3-D Morton key (10 bits per axis) of a point inside the bounding box.
+__device__ __forceinline__ uint32_t box_key(double x, double y, double z, const unsigned long long* bbox) {
+    const double p[3] = {x, y, z};
+    uint32_t q[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double lo = dval_of(bbox[c]), hi = dval_of(bbox[3 + c]);
+        const double t = hi > lo ? (p[c] - lo) / (hi - lo) * 1024.0 : 0.0;
+        int v = (int)t;
+        q[c] = (uint32_t)(v < 0 ? 0 : (v > 1023 ? 1023 : v));
+    }
+    return (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+}
+
+// Sort keys and validation.  Unit-vector catalogs: every point finite with
+// | |v| - 1 | <= 1e-6, eps_word receives the largest | |v|^2 - 1 |; 3-D
+// catalogs (euclid): every point finite, eps_word receives the largest
+// |v|^2 (both as the bits of a non-negative double, whose order is that of
+// the integers).  Keys: cube-face curve of the direction (unit vectors) or a
+// 3-D Morton curve over the bounding box (3-D).
 __global__ void prep_keys_kernel(const double* __restrict__ xyz, uint32_t n,
-                                 const uint32_t* __restrict__ seg_of_point, int sort,
+                                 const uint32_t* __restrict__ seg_of_point, int sort, int euclid,
+                                 const unsigned long long* __restrict__ bbox,
                                  unsigned long long* keys, uint32_t* vals, uint32_t n_pow2,
                                  unsigned long long* err_word, unsigned long long* eps_word) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1034,15 +1278,20 @@ __global__ void prep_keys_kernel(const double* __restrict__ xyz, uint32_t n,
     } else {
         const double x = xyz[3ull * i], y = xyz[3ull * i + 1], z = xyz[3ull * i + 2];
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
-        const bool finite = isfinite(x) && isfinite(y) && isfinite(z);
-        // | |v| - 1 | <= 1e-6  <=>  r2 in [(1 - 1e-6)^2, (1 + 1e-6)^2]
-        if (!finite || !(r2 >= 0.999998000001 && r2 <= 1.000002000001)) {
+        const bool finite = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(r2);
+        if (euclid) {
+            // |coordinates| <= 1e28 keeps FP32 copies and differences finite
+            if (!finite || !(fabs(x) <= 1e28 && fabs(y) <= 1e28 && fabs(z) <= 1e28))
+                atomicOr(err_word, (unsigned long long)kErrBadPoint);
+            else eps = r2;
+        } else if (!finite || !(r2 >= 0.999998000001 && r2 <= 1.000002000001)) {
+            // | |v| - 1 | <= 1e-6  <=>  r2 in [(1 - 1e-6)^2, (1 + 1e-6)^2]
             atomicOr(err_word, (unsigned long long)kErrBadPoint);
         } else {
             eps = fabs(r2 - 1.0);
         }
         const unsigned long long seg = seg_of_point ? seg_of_point[i] : 0u;
-        const uint32_t ck = (sort && finite) ? cell_key(x, y, z) : 0u;
+        const uint32_t ck = (sort && finite) ? (euclid ? box_key(x, y, z, bbox) : cell_key(x, y, z)) : 0u;
         keys[i] = (seg << 32) | ck;
         vals[i] = i;
     }
@@ -1131,6 +1380,21 @@ __global__ void prep_gather_kernel(const double* __restrict__ xyz, uint32_t n,
     out32x2[2ull * q + 1] = make_float4(fz, fz, 0.f, 0.f);
 }
 
+// Padding of 3-D catalogs: (+inf, +inf, +inf).  A pair with a real point has
+// screen value -inf (fails the fast test) and z = +inf; two padding points
+// give NaN: both land in the overflow cell of the LUT (and fail the binary64
+// comparisons), so padding is never counted (unit-vector catalogs are padded
+// with zero vectors instead).
+__global__ void prep_fill_kernel(Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad, double v) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pad) return;
+    const float f = (float)v;
+    out64[p] = Point64{v, v, v, 0.0};
+    out32[p] = make_float4(f, f, f, 0.f);
+    out32x2[2ull * p] = make_float4(f, f, f, f);
+    out32x2[2ull * p + 1] = make_float4(f, f, 0.f, 0.f);
+}
+
 // ============================================================== launchers
 // Fills the block constants of the work description (shared-memory offsets of
 // the shape, merge interval) and launches.
@@ -1151,7 +1415,7 @@ static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t
     wd.off_lut = L.lut;
     wd.off_queue = L.queue;
     wd.off_prod = L.prod;
-    wd.stage_bytes = wd.J * (MODE == kModeScreen ? 16u : 32u);
+    wd.stage_bytes = wd.J * ((MODE == kModeScreen || MODE == kModeEuclid) ? 16u : 32u);
     // 16-bit counters: a lane adds at most R per j to one row plus at most 2 per
     // queue drain (at most one drain per slow j), so merging every
     // 65535 / (R + 2) - J j-points keeps every counter below 2^16
@@ -1183,6 +1447,7 @@ cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int mode, int nedg
     if (sh.threads == T_ && sh.ipt == R_) {                                      \
         if (mode == kModePlain) return launch_t<T_, R_, kModePlain>(wd, sh, stream);   \
         if (mode == kModeScreen2) return launch_t<T_, R_, kModeScreen2>(wd, sh, stream); \
+        if (mode == kModeEuclid) return launch_t<T_, R_, kModeEuclid>(wd, sh, stream); \
         return launch_t<T_, R_, kModeScreen>(wd, sh, stream);                    \
     }
     TPCF_SHAPES(X)
@@ -1195,6 +1460,7 @@ cudaError_t count_set_smem_limit(int mode, int threads, int ipt, size_t bytes) {
     if (threads == T_ && ipt == R_) {                                            \
         if (mode == kModePlain) return set_smem_t<T_, R_, kModePlain>(bytes);    \
         if (mode == kModeScreen2) return set_smem_t<T_, R_, kModeScreen2>(bytes); \
+        if (mode == kModeEuclid) return set_smem_t<T_, R_, kModeEuclid>(bytes);  \
         return set_smem_t<T_, R_, kModeScreen>(bytes);                           \
     }
     TPCF_SHAPES(X)
@@ -1222,15 +1488,20 @@ cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long l
 }
 
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
-                           const uint32_t* seg_delta, int sort, Point64* out64, float4* out32, float4* out32x2,
-                           uint32_t n_pad,
+                           const uint32_t* seg_delta, int sort, int euclid, unsigned long long* bbox,
+                           Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
                            unsigned long long* keys, uint32_t* vals, uint32_t n_pow2,
                            unsigned long long* err_word, unsigned long long* eps_word, cudaStream_t stream,
                            uint32_t* launches) {
     cudaError_t e;
     uint32_t nl = 0;
     if (n > 0) {
-        prep_keys_kernel<<<(n_pow2 + 255) / 256, 256, 0, stream>>>(xyz_in, n, seg_of_point, sort,
+        if (euclid && sort) {
+            prep_bbox_kernel<<<152, 256, 0, stream>>>(xyz_in, n, bbox);
+            ++nl;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        prep_keys_kernel<<<(n_pow2 + 255) / 256, 256, 0, stream>>>(xyz_in, n, seg_of_point, sort, euclid, bbox,
                                                                     keys, vals, n_pow2, err_word, eps_word);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1254,7 +1525,11 @@ cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
-    if (n_pad > 0) {
+    if (n_pad > 0 && euclid) {
+        prep_fill_kernel<<<(n_pad + 255) / 256, 256, 0, stream>>>(out64, out32, out32x2, n_pad, (double)INFINITY);
+        ++nl;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else if (n_pad > 0) {
         if ((e = cudaMemsetAsync(out64, 0, (size_t)n_pad * sizeof(Point64), stream)) != cudaSuccess ||
             (e = cudaMemsetAsync(out32, 0, (size_t)n_pad * sizeof(float4), stream)) != cudaSuccess ||
             (e = cudaMemsetAsync(out32x2, 0, (size_t)n_pad * 2 * sizeof(float4), stream)) != cudaSuccess)

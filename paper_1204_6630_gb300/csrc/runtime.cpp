@@ -207,6 +207,53 @@ double derive_threshold(double t, int* verified) {
     return C;
 }
 
+// 3-D variant: S = the smallest double s >= 0 with sqrt(s) >= r (host sqrt,
+// correctly rounded, hence monotone), so that a pair's r >= r_k exactly when
+// its binary64 d^2 >= S_k.  Found by bisection over the ordered doubles, then
+// the predicate is checked to flip once in a window of 64 doubles each side.
+double derive_sq_threshold(double r, int* verified) {
+    if (r <= 0.0) { *verified = 1; return 0.0; }
+    const double top = 1.7976931348623157e308;
+    if (!(std::sqrt(top) >= r)) { *verified = 1; return INFINITY; }  // no finite d^2 reaches r
+    int64_t lo = dkey(0.0), hi = dkey(top);  // pred(lo) false (r > 0), pred(hi) true
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (std::sqrt(dfromkey(mid)) >= r) hi = mid; else lo = mid;
+    }
+    bool ok = true;
+    for (int64_t k = std::max(dkey(0.0), hi - 64); k < hi && ok; ++k)
+        if (std::sqrt(dfromkey(k)) >= r) ok = false;
+    for (int64_t k = hi; k <= std::min(dkey(top), hi + 64) && ok; ++k)
+        if (!(std::sqrt(dfromkey(k)) >= r)) ok = false;
+    *verified = ok ? 1 : 0;
+    return dfromkey(hi);
+}
+
+// 3-D edges: finite, >= 0, strictly increasing, the last > 0 and at most 1e18
+// (a pair whose FP32 square overflows, |a - b| > 1.8e19, is then certainly
+// beyond the range).
+bool edges3_valid(const double* e, int ne) {
+    if (!e || ne < 2 || ne > TPCF_MAX_EDGES) return false;
+    for (int k = 0; k < ne; ++k)
+        if (!(e[k] >= 0.0 && e[k] <= 1e18)) return false;
+    for (int k = 1; k < ne; ++k)
+        if (!(e[k] > e[k - 1])) return false;
+    return e[ne - 1] > 0.0;
+}
+
+// Error bound of the 3-D screen value z = fl32(|a' - b'|^2) (a' = fl32(a)
+// per coordinate; dx = fl32(a'x - b'x); z = fl(fma(dz,dz, fma(dy,dy, dx*dx))))
+// against d^2 (the binary64 d^2 of the definition) for points of norm <= M,
+// at d^2 ~ Z:  |a' - a| <= u |a| moves a - b by at most 2uM, so
+// | |a'-b'|^2 - |a-b|^2 | <= 4uM|a-b| + 4u^2M^2; the subtractions and the three
+// roundings of the non-negative sum add a relative 5u; the binary64 d^2 is
+// within 9e-16 relative of |a - b|^2.
+double euclid_delta(double Z, double M) {
+    const double u = kUnit, s = std::sqrt(Z * (1.0 + 1e-15)) * (1.0 + 1e-15);
+    const double t = s + 2.01 * u * M;
+    return (4.001 * u * M * s + 4.01 * u * u * M * M + 5.01 * u * t * t + 9e-16 * Z) * (1.0 + 1e-9);
+}
+
 bool edges_valid(const double* e, int ne) {
     if (!e || ne < 2 || ne > TPCF_MAX_EDGES) return false;
     for (int k = 0; k < ne; ++k)
@@ -435,6 +482,10 @@ int tpcf::bins_create_impl(tpcf_ctx* ctx, const double* edges, int nedges, cudaS
 int tpcf::bins_destroy_impl(tpcf_bins* b) {
     if (!b) return TPCF_EINVAL;
     cudaSetDevice(b->ctx->cfg.device);
+    if (!b->sets.empty()) {
+        cudaDeviceSynchronize();
+        for (auto& kv : b->sets) cudaFree(kv.second.dev_buf);
+    }
     if (b->dev_buf) {
         if (b->stream_ordered) {
             cudaFreeAsync(b->dev_buf, b->free_stream);
@@ -445,6 +496,138 @@ int tpcf::bins_destroy_impl(tpcf_bins* b) {
         }
     }
     delete b;
+    return TPCF_OK;
+}
+
+// ---------------------------------------------------------------------- 3-D bins
+// The device arrays of a 3-D bin set for points of norm <= M = 2^key: S_k, the
+// z-space bounds zlo/zhi (z >= zhi_k proves d^2 >= S_k, z < zlo_k proves
+// d^2 < S_k, both with g_k = euclid_delta(S_k)), the fast-test limit H (every
+// pair with d^2 <= S_B has H - z' >= 0 for the fast loop's fl32 value z'),
+// and a LUT over z cells uniform in the float bits of z (constant ratio).
+static int euclid_set(tpcf_ctx* ctx, tpcf_bins* b, int key, const tpcf::BinsDev** host, tpcf::BinsDev** dev) {
+    std::lock_guard<std::mutex> g(b->set_mu);
+    auto it = b->sets.find(key);
+    if (it == b->sets.end()) {
+        const int ne = b->nedges;
+        const double M = std::ldexp(1.0, key), u = kUnit;
+        std::vector<float> zlo(ne), zhi(ne), s32(ne), zero(ne, 0.f);
+        double min_pos = INFINITY;
+        for (int k = 0; k < ne; ++k) {
+            const double S = b->cos_thr[k];
+            if (S == 0.0) {  // r_k = 0: every pair crosses it
+                zlo[k] = zhi[k] = -INFINITY;
+            } else if (std::isinf(S)) {
+                zlo[k] = zhi[k] = INFINITY;
+            } else {
+                const double gk = euclid_delta(S, M);
+                zhi[k] = round_up_f32(S + gk);
+                // z - delta(z) increases only once |a - b| is well above 2uM
+                zlo[k] = S < 1e6 * (u * M) * (u * M) ? -1.0f : round_down_f32(S - gk);
+                min_pos = std::min(min_pos, S);
+            }
+            s32[k] = (float)S;
+        }
+        const double SB = b->cos_thr[ne - 1];
+        const double zmax = std::pow(std::sqrt(SB * (1.0 + 1e-15)) + 2.001 * u * M, 2) * (1.0 + 2.01 * u);
+        const float H = round_up_f32(zmax * (1.0 + 6.1 * u) + 1e-300);
+        // LUT: cells of constant ratio from zmin = min S / 64 up past 2 H
+        const float zmin = round_down_f32(std::max(min_pos / 64.0, 1e-30));
+        int32_t b0;
+        memcpy(&b0, &zmin, 4);
+        const float ztop = round_up_f32(2.0 * (double)H + 1e-30);
+        int32_t bt;
+        memcpy(&bt, &ztop, 4);
+        int shift = 0;
+        while (((int64_t)(bt - b0) >> shift) + 1 >= kLutCells - 1) ++shift;
+        std::vector<uint32_t> lut(kLutCells);
+        for (int c = 0; c < kLutCells; ++c) {
+            const int64_t lo_bits = (int64_t)b0 + ((int64_t)c << shift);
+            const int64_t hi_bits = (int64_t)b0 + ((int64_t)(c + 1) << shift) - 1;
+            float cmin, cmax;
+            const int32_t lb = (int32_t)std::min<int64_t>(lo_bits, 0x7f7fffff);
+            const int32_t hb = (int32_t)std::min<int64_t>(hi_bits, 0x7f7fffff);
+            memcpy(&cmin, &lb, 4);
+            memcpy(&cmax, &hb, 4);
+            if (c == 0) cmin = 0.0f;                       // also every z below zmin
+            if (c == kLutCells - 1) cmax = INFINITY;        // and every z above
+            uint32_t P = 0, Q = 0;
+            for (int m = 0; m < ne; ++m) {
+                P += (cmin >= zhi[m]);
+                Q += (cmax >= zlo[m]);
+            }
+            lut[c] = P | (Q << 16);
+        }
+        // one device buffer with the angular layout (lo/hi unused), then the descriptor
+        const size_t nd = (size_t)ne * 8, nf = (size_t)ne * 4, nl = lut.size() * 4, nf16 = (nf + 15) / 16 * 16;
+        const size_t off_lo = (nd + 15) / 16 * 16, off_hi = off_lo + nf16, off_c32 = off_hi + nf16,
+                     off_zlo = off_c32 + nf16, off_zhi = off_zlo + nf16, off_lut = off_zhi + nf16,
+                     off_desc = (off_lut + nl + 255) / 256 * 256, total = off_desc + sizeof(BinsDev);
+        tpcf_bins::Set set;
+        if (dev_malloc(&set.dev_buf, total) != cudaSuccess) return ctx->fail(TPCF_ENOMEM, "bins: allocation failed");
+        unsigned char* base = (unsigned char*)set.dev_buf;
+        memset(&set.host, 0, sizeof set.host);
+        set.host.cos_thr = (const double*)base;
+        set.host.lo = (const float*)(base + off_lo);
+        set.host.hi = (const float*)(base + off_hi);
+        set.host.cos32 = (const float*)(base + off_c32);
+        set.host.zlo = (const float*)(base + off_zlo);
+        set.host.zhi = (const float*)(base + off_zhi);
+        set.host.lut = (const uint32_t*)(base + off_lut);
+        set.host.nedges = ne;
+        set.host.lut_scale = 0.f;
+        set.host.fast_t = H;
+        set.host.cos_last = SB;
+        set.host.euclid = 1;
+        set.host.zbits0 = b0;
+        set.host.zshift = shift;
+        set.dev_desc = (BinsDev*)(base + off_desc);
+        std::vector<unsigned char> hs(total, 0);
+        memcpy(hs.data(), b->cos_thr.data(), nd);
+        memcpy(hs.data() + off_lo, zero.data(), nf);
+        memcpy(hs.data() + off_hi, zero.data(), nf);
+        memcpy(hs.data() + off_c32, s32.data(), nf);
+        memcpy(hs.data() + off_zlo, zlo.data(), nf);
+        memcpy(hs.data() + off_zhi, zhi.data(), nf);
+        memcpy(hs.data() + off_lut, lut.data(), nl);
+        memcpy(hs.data() + off_desc, &set.host, sizeof(BinsDev));
+        if (cudaMemcpy(set.dev_buf, hs.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(set.dev_buf);
+            return ctx->fail(TPCF_ECUDA, "bins: upload failed");
+        }
+        it = b->sets.emplace(key, set).first;
+    }
+    *host = &it->second.host;
+    *dev = it->second.dev_desc;
+    return TPCF_OK;
+}
+
+extern "C" int tpcf_bins_create_3d(tpcf_ctx* ctx, const double* edges, int nedges, tpcf_bins** out) {
+    if (!ctx || !out) return TPCF_EINVAL;
+    *out = nullptr;
+    if (!edges3_valid(edges, nedges))
+        return ctx->fail(TPCF_EINVAL, "edges: need 2..%d strictly increasing finite distances >= 0, the last > 0",
+                         TPCF_MAX_EDGES);
+    tpcf_bins* b = new tpcf_bins();
+    b->ctx = ctx;
+    b->nedges = nedges;
+    b->euclid = true;
+    b->edges.assign(edges, edges + nedges);
+    b->cos_thr.resize(nedges);
+    b->verified.resize(nedges);
+    for (int k = 0; k < nedges; ++k) b->cos_thr[k] = derive_sq_threshold(edges[k], &b->verified[k]);
+    *out = b;
+    return TPCF_OK;
+}
+
+extern "C" int tpcf_bins_thresholds_3d(const double* edges, int nedges, double* sq_thr, int* verified) {
+    if (!edges3_valid(edges, nedges)) return TPCF_EINVAL;
+    for (int k = 0; k < nedges; ++k) {
+        int v;
+        const double S = derive_sq_threshold(edges[k], &v);
+        if (sq_thr) sq_thr[k] = S;
+        if (verified) verified[k] = v;
+    }
     return TPCF_OK;
 }
 
@@ -461,7 +644,7 @@ size_t tpcf::catalog_bytes(uint64_t n) {
 }
 
 int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where, const uint64_t* offsets,
-                              int nseg, cudaStream_t st, bool stream_ordered, tpcf_catalog** out) {
+                              int nseg, cudaStream_t st, bool stream_ordered, tpcf_catalog** out, bool euclid) {
     if (!ctx || !out) return TPCF_EINVAL;
     *out = nullptr;
     if (n > TPCF_MAX_POINTS) return ctx->fail(TPCF_EOVERFLOW, "catalog: %llu points > limit",
@@ -480,6 +663,7 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
     tpcf_catalog* c = new tpcf_catalog();
     c->ctx = ctx;
     c->n = n;
+    c->euclid = euclid;
     c->stream_ordered = stream_ordered;
     c->free_stream = st;
     uint64_t n_layout = n;  // device positions in use (segments are aligned: gaps of zero vectors)
@@ -538,11 +722,13 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
             return fail_with(TPCF_ECUDA, "host-to-device copy failed");
         in = (const double*)tmp_in;
     }
-    if (cudaMallocAsync((void**)&err, 16, st) != cudaSuccess ||
+    // err: error word, largest |v|^2 or | |v|^2 - 1 |, then the bounding box (3 min, 3 max keys)
+    if (cudaMallocAsync((void**)&err, 64, st) != cudaSuccess ||
         cudaMallocAsync((void**)&keys, (size_t)n_pow2 * 8, st) != cudaSuccess ||
         cudaMallocAsync((void**)&vals, (size_t)n_pow2 * 4, st) != cudaSuccess)
         return fail_with(TPCF_ENOMEM, "scratch allocation failed");
-    if (cudaMemsetAsync(err, 0, 16, st) != cudaSuccess) return fail_with(TPCF_ECUDA, "memset failed");
+    if (cudaMemsetAsync(err, 0, 64, st) != cudaSuccess || cudaMemsetAsync(err + 2, 0xff, 24, st) != cudaSuccess)
+        return fail_with(TPCF_ECUDA, "memset failed");
     if (nseg > 0) {
         // segment of each input point, shift of each segment to its aligned start, and the
         // segment of each kSegAlign-point block of the device layout (blocks past the last
@@ -567,8 +753,8 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
             return fail_with(TPCF_ECUDA, "segment copy failed");
     }
     uint32_t nl = 0;
-    cudaError_t e = launch_prepare(in, (uint32_t)n, seg, seg_delta, sort ? 1 : 0, c->d64, c->d32, c->d32x2, c->n_pad,
-                                   keys, vals, n_pow2, err, err + 1, st, &nl);
+    cudaError_t e = launch_prepare(in, (uint32_t)n, seg, seg_delta, sort ? 1 : 0, euclid ? 1 : 0, err + 2, c->d64,
+                                   c->d32, c->d32x2, c->n_pad, keys, vals, n_pow2, err, err + 1, st, &nl);
     ctx->launches.fetch_add(nl);
     if (e != cudaSuccess) return fail_with(TPCF_ECUDA, cudaGetErrorString(e));
     unsigned long long hw[2] = {0, 0};
@@ -576,12 +762,19 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail_with(TPCF_ECUDA, "preparation failed");
     const unsigned long long herr = hw[0];
-    double eps_dev;
-    memcpy(&eps_dev, &hw[1], 8);
-    c->eps_max = eps_dev + 4e-16;  // the device sum of squares is within 3.4e-16 of |v|^2
+    double word;
+    memcpy(&word, &hw[1], 8);
+    if (euclid) {
+        c->eps_max = INFINITY;  // not unit vectors: no chord refinement of angular counts
+        c->norm_max = std::sqrt(word * (1.0 + 1e-15)) * (1.0 + 1e-15);  // the device |v|^2 is within 3.4e-16 relative
+    } else {
+        c->eps_max = word + 4e-16;  // the device sum of squares is within 3.4e-16 of |v|^2
+        c->norm_max = 1.0 + 1e-6;
+    }
     if (herr & kErrBadPoint) {
         rc = TPCF_EINVAL;
-        return fail_with(rc, "a point is not finite or not a unit vector (| |v| - 1 | > 1e-6)");
+        return fail_with(rc, euclid ? "a point is not finite"
+                                    : "a point is not finite or not a unit vector (| |v| - 1 | > 1e-6)");
     }
     release();
     *out = c;
@@ -597,6 +790,11 @@ extern "C" int tpcf_catalog_create_segmented(tpcf_ctx* ctx, const double* xyz, u
 extern "C" int tpcf_catalog_create(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where,
                                    void* stream, tpcf_catalog** out) {
     return catalog_create_impl(ctx, xyz, n, where, nullptr, 0, (cudaStream_t)stream, false, out);
+}
+
+extern "C" int tpcf_catalog_create_3d(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where,
+                                      const uint64_t* offsets, int nseg, void* stream, tpcf_catalog** out) {
+    return catalog_create_impl(ctx, xyz, n, where, offsets, nseg, (cudaStream_t)stream, false, out, true);
 }
 
 int tpcf::catalog_destroy_impl(tpcf_catalog* c) {
@@ -634,8 +832,9 @@ struct SubSpec {
     const uint64_t* totals = nullptr;   // pair total of each histogram (nhist entries); NULL: all pairs
 };
 
-int kernel_mode(const tpcf_config& cfg) {
+int kernel_mode(const tpcf_config& cfg, bool euclid) {
     if (cfg.precision == TPCF_PLAIN_FP64) return kModePlainFP64;
+    if (euclid) return kModeEuclidScreen;
     return (cfg.flags & TPCF_F_PACKED_FMA) ? kModeScreenPacked : kModeScreenScalar;
 }
 
@@ -701,7 +900,7 @@ uint64_t range_pairs(const SubProblem& sp, uint64_t lo, uint64_t hi, uint32_t I,
 // subs_out receives the sub-problem records (placed inline or uploaded by the
 // caller); acc is the accumulator array (stride acc_stride words per
 // histogram); returns the number of items.
-uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* bins, const Shape& sh,
+uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const BinsDev* bins_dev, const Shape& sh,
                     unsigned long long* acc, size_t acc_stride, std::vector<SubProblem>& subs) {
     const uint32_t I = (uint32_t)(sh.threads * sh.ipt), Jc = (uint32_t)sh.jchunk;
     subs.assign(nsub, SubProblem());
@@ -726,7 +925,7 @@ uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bi
         sp.n_items = (p.na == 0 || p.nb == 0) ? 0 : items_of(sp.n_iblk, sp.n_jchunk, p.auto_mode, I, Jc);
         sp.walk_mult = walk_multiplier(sp.n_items);
         sp.hist = acc + hist_base * acc_stride;
-        sp.bins = bins->dev_desc;
+        sp.bins = bins_dev;
         sp.row_seg = p.row_seg ? p.row_seg + p.a_off / kSegAlign : nullptr;
         sp.row_stride = (uint32_t)acc_stride;
         sp.no_self = p.no_self ? 1u : 0u;
@@ -774,7 +973,28 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         return ctx->fail(TPCF_EINVAL, "row-attributed counts are not split into shards");
     cudaSetDevice(ctx->cfg.device);
     const int ne = bins->nedges;
-    int mode = kernel_mode(ctx->cfg);
+    // the device bin set: angular bins have one; 3-D bins one per bound 2^key on the points' norms
+    const BinsDev* bh = &bins->host;
+    const BinsDev* bdev = bins->dev_desc;
+    if (bins->euclid) {
+        double M = 0.0;
+        for (int s = 0; s < nsub; ++s) {
+            if (!specs[s].a->euclid || !specs[s].b->euclid)
+                return ctx->fail(TPCF_EINVAL, "3-D bins count 3-D catalogs (tpcf_catalog_create_3d)");
+            M = std::max(M, std::max(specs[s].a->norm_max, specs[s].b->norm_max));
+        }
+        int key = -64;
+        while (std::ldexp(1.0, key) < M) ++key;
+        BinsDev* dv = nullptr;
+        const int rc = euclid_set(ctx, const_cast<tpcf_bins*>(bins), key, &bh, &dv);
+        if (rc != TPCF_OK) return rc;
+        bdev = dv;
+    } else {
+        for (int s = 0; s < nsub; ++s)
+            if (specs[s].a->euclid || specs[s].b->euclid)
+                return ctx->fail(TPCF_EINVAL, "angular bins count unit-vector catalogs");
+    }
+    int mode = kernel_mode(ctx->cfg, bins->euclid);
     uint64_t all_pairs = 0, max_n = 0;
     for (int s = 0; s < nsub; ++s) {
         all_pairs += full_pairs(specs[s]);
@@ -841,7 +1061,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     memset(&wd, 0, sizeof wd);
     std::vector<SubProblem> subs;
     auto setup = [&](const Shape& shp) -> int {
-        const uint64_t items = build_work(ctx, specs, nsub, bins, shp, acc, acc_stride, subs);
+        const uint64_t items = build_work(ctx, specs, nsub, bdev, shp, acc, acc_stride, subs);
         if (items > 0xffff0000ull) return TPCF_EOVERFLOW;
         if (use_slot) {
             for (int s2 = 0; s2 < nsub; ++s2) wd.sub[s2] = subs[s2];
@@ -868,13 +1088,17 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         wd.force_idx = force_idx ? 1u : 0u;
         wd.nedges_max = ne;
         wd.ne = ne;
-        wd.neg_fast_t = -bins->host.fast_t;
-        wd.lut_scale = bins->host.lut_scale;
-        wd.cos_last = bins->host.cos_last;
+        wd.euclid = bh->euclid ? 1u : 0u;
+        wd.neg_fast_t = bh->euclid ? bh->fast_t : -bh->fast_t;  // 3-D: +H, angular: -T
+        wd.lut_scale = bh->lut_scale;
+        wd.cos_last = bh->cos_last;
+        wd.zbits0 = bh->zbits0;
+        wd.zshift = bh->zshift;
         // zero-vector padding has screen value e = -T: it can look in range only
-        // when T <= 0; sub-ranges of segmented catalogs are followed by real points
-        wd.need_idx = (force_idx || !(bins->host.fast_t > 0.f)) ? 1u : 0u;
-        wd.chord_ok = 1u;
+        // when T <= 0 (3-D catalogs are padded with a far point instead); sub-ranges
+        // of segmented catalogs are followed by real points
+        wd.need_idx = (force_idx || (!bh->euclid && !(bh->fast_t > 0.f))) ? 1u : 0u;
+        wd.chord_ok = bh->euclid ? 0u : 1u;
         for (int s2 = 0; s2 < nsub; ++s2)
             if (!(specs[s2].a->eps_max <= kChordEpsRef && specs[s2].b->eps_max <= kChordEpsRef)) wd.chord_ok = 0u;
         wd.wait_limit_ns = (uint64_t)ctx->cfg.wait_timeout_us * 1000ull;
@@ -1115,7 +1339,7 @@ extern "C" int tpcf_jackknife(tpcf_ctx* ctx, const tpcf_catalog* d, const tpcf_c
         return ctx->fail(TPCF_EINVAL, "jackknife: both catalogs must be segmented with the same count");
     if (estimator != TPCF_LS_EXACT && estimator != TPCF_LS_PAPER)
         return ctx->fail(TPCF_EINVAL, "jackknife: unknown estimator");
-    if (!(bins->host.fast_t > 0.f))
+    if (!bins->euclid && !(bins->host.fast_t > 0.f))
         return ctx->fail(TPCF_EINVAL, "jackknife: the histogram range must end below 90 degrees");
     const int P = (int)d->offsets.size() - 1;
     if (cov && P < 2) return ctx->fail(TPCF_EINVAL, "jackknife: the covariance needs at least 2 patches");

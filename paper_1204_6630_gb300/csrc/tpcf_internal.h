@@ -45,6 +45,13 @@ struct BinsDev {
     const float* zhi;       // [nedges]                                          z >= zhi_k => crossed
     int nedges;             // B + 1
     float lut_scale;        // 2^-q with 2^q >= every in-range e: cell width 2^(q - 14)
+    // 3-D variant (euclid = 1): cos_thr holds S_k (r >= r_k <=> d^2 >= S_k),
+    // cos32 RN(S_k), fast_t the limit H of the fast test H - |a' - b'|^2 >= 0,
+    // cos_last S_B; the LUT cell of z = fl32(|a' - b'|^2) is
+    // clamp((bits(z) - zbits0) >> zshift, 0, kLutCells - 1).
+    int euclid;
+    int32_t zbits0;
+    int zshift;
     float fast_t;           // T = RD(C_B - 10u): a screen value e < 0 is certainly overflow
     double cos_last;        // C_B (binary64 range limit, plain kernel)
 };
@@ -106,6 +113,9 @@ struct WorkDesc {
     float lut_scale;                 // 2^-q (LUT span)
     uint32_t need_idx;               // 1: check i < na, j < nb for every slow pair
     uint32_t chord_ok;               // 1: every catalog of the launch has | |v|^2 - 1 | <= kChordEpsRef
+    uint32_t euclid;                 // 1: 3-D variant (distances); neg_fast_t then holds +H
+    int32_t zbits0;                  // 3-D variant: LUT cell origin (bits of a float) and shift
+    int zshift;
     double cos_last;                 // C_B (all-binary64 kernel)
     // ... and the shared-memory layout of the shape (set by the launcher).
     uint32_t off_bars, off_ctl, off_stage, off_hist, off_cthr, off_lo, off_hi, off_c32, off_zlo, off_zhi,
@@ -127,7 +137,7 @@ struct Shape {
 
 // Kernel variants (mode argument of the launchers): FP32 screen with scalar
 // FMA, all-binary64 comparator, FP32 screen with packed FP32x2 FMA.
-enum { kModeScreenScalar = 0, kModePlainFP64 = 1, kModeScreenPacked = 2 };
+enum { kModeScreenScalar = 0, kModePlainFP64 = 1, kModeScreenPacked = 2, kModeEuclidScreen = 3 };
 
 // Launchers (kernels.cu).  All are asynchronous in `stream` and return a
 // cudaError_t from the launch.
@@ -140,8 +150,8 @@ cudaError_t launch_finalize_batch(const unsigned long long* acc, int acc_stride,
                                   unsigned long long* out, int out_stride, const unsigned long long* totals,
                                   int count, unsigned long long* err_word, cudaStream_t stream);
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
-                           const uint32_t* seg_delta, int sort, Point64* out64, float4* out32, float4* out32x2,
-                           uint32_t n_pad,
+                           const uint32_t* seg_delta, int sort, int euclid, unsigned long long* bbox,
+                           Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
                            unsigned long long* key_scratch, uint32_t* val_scratch,
                            uint32_t n_pow2, unsigned long long* err_word, unsigned long long* eps_word,
                            cudaStream_t stream, uint32_t* launches);

@@ -299,3 +299,48 @@ def materialise_job(job: dict) -> Workload:
     d = clustered(job["nd"], 128, 0.5, fp, job["seed"])
     r = randoms(job["nr"], fp, job["seed"])
     return Workload(f"job{job['id']}", d, r, linear_edges(0.0, 2.0, job["nbins"]))
+
+
+# --------------------------------------------------------------------------- 3-D variant
+def box_points(n: int, side: float, seed: int = 0) -> np.ndarray:
+    """Uniform points in the cube [0, side)^3 (3-D randoms)."""
+    return _rngs(seed)["randoms"].uniform(0.0, side, (n, 3))
+
+
+def box_clustered(n: int, n_clusters: int, sigma: float, side: float, seed: int = 0,
+                  clustered_fraction: float = 0.7) -> np.ndarray:
+    """Clustered 3-D points in the cube [0, side)^3: ``round(clustered_fraction * n)``
+    members of ``n_clusters`` centres (uniform in the cube), offset by isotropic
+    Gaussians of width ``sigma`` and redrawn when they leave the cube; the rest
+    uniform."""
+    g = _rngs(seed)
+    n_cl = int(round(clustered_fraction * n)) if n_clusters > 0 else 0
+    centres = g["centres"].uniform(0.0, side, (max(n_clusters, 1), 3))
+    member_of = g["memberships"].integers(0, max(n_clusters, 1), n_cl)
+    pts = np.empty((n_cl, 3))
+    todo = np.arange(n_cl)
+    for _ in range(1000):
+        if todo.size == 0:
+            break
+        p = centres[member_of[todo]] + g["offsets"].normal(0.0, sigma, (todo.size, 3))
+        ok = np.all((p >= 0.0) & (p < side), axis=1)
+        pts[todo[ok]] = p[ok]
+        todo = todo[~ok]
+    if todo.size:
+        raise RuntimeError("cluster members could not be placed inside the box")
+    return np.concatenate([pts, g["background"].uniform(0.0, side, (n - n_cl, 3))])
+
+
+def log_edges_r(r_min: float, r_max: float, nbins: int) -> np.ndarray:
+    """Log-spaced distance edges with the endpoints exactly r_min and r_max."""
+    t = r_min * 10.0 ** (np.arange(nbins + 1) * (math.log10(r_max / r_min) / nbins))
+    t[0], t[-1] = r_min, r_max
+    return t
+
+
+def box_precision(seed: int = 0, n: int = 1_000_000, side: float = 1000.0) -> Workload:
+    """3-D workload: n clustered points (4096 clusters of sigma 2) and n uniform
+    points in a cube of side 1000, 30 log distance bins 0.5-50."""
+    return Workload(f"box_n{n}", box_clustered(n, 4096, 2.0, side, seed), box_points(n, side, seed + 1),
+                    log_edges_r(0.5, 50.0, 30))
+

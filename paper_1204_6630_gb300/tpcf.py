@@ -99,6 +99,10 @@ _SIGS = {
     "tpcf_catalog_destroy": (ctypes.c_int, [_vp]),
     "tpcf_catalog_size": (_u64, [_vp]),
     "tpcf_bins_create": (ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "tpcf_catalog_create_3d": (ctypes.c_int, [_vp, _vp, _u64, ctypes.c_int, _u64p, ctypes.c_int, _vp,
+                                              ctypes.POINTER(_vp)]),
+    "tpcf_bins_create_3d": (ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "tpcf_bins_thresholds_3d": (ctypes.c_int, [_dp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)]),
     "tpcf_bins_destroy": (ctypes.c_int, [_vp]),
     "tpcf_bins_thresholds": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_double, _dp,
                                             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
@@ -248,6 +252,21 @@ def tpcf_catalog_create_segmented(ctx: int, xyz, offsets, stream=None) -> int:
     return tpcf_catalog_create(ctx, xyz, stream, offsets)
 
 
+def tpcf_catalog_create_3d(ctx: int, xyz, stream=None, offsets=None) -> int:
+    """3-D catalog from an (n, 3) float64 array of points (numpy or torch)."""
+    where, ptr, keep = _where_ptr(xyz, np.float64)
+    shape = tuple(keep.shape)
+    if len(shape) != 2 or (shape[0] and shape[1] != 3):
+        raise ValueError("xyz must be an (n, 3) array")
+    h = _vp()
+    off = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.uint64)
+    rc = load().tpcf_catalog_create_3d(ctx, ptr, shape[0], where,
+                                       off.ctypes.data_as(_u64p) if off is not None else None,
+                                       len(off) - 1 if off is not None else 0, _stream_ptr(stream), ctypes.byref(h))
+    _check(rc, "tpcf_catalog_create_3d", ctx)
+    return h.value
+
+
 def tpcf_catalog_destroy(cat: int) -> None:
     _check(load().tpcf_catalog_destroy(cat), "tpcf_catalog_destroy")
 
@@ -262,6 +281,24 @@ def tpcf_bins_create(ctx: int, edges_rad) -> int:
     rc = load().tpcf_bins_create(ctx, e.ctypes.data_as(_dp), len(e), ctypes.byref(h))
     _check(rc, "tpcf_bins_create", ctx)
     return h.value
+
+
+def tpcf_bins_create_3d(ctx: int, edges) -> int:
+    """3-D bins from distance edges."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    h = _vp()
+    _check(load().tpcf_bins_create_3d(ctx, e.ctypes.data_as(_dp), len(e), ctypes.byref(h)), "tpcf_bins_create_3d", ctx)
+    return h.value
+
+
+def tpcf_bins_thresholds_3d(edges):
+    """(S, verified) for 3-D distance edges; host-only, no GPU needed."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    sq = np.empty(len(e), np.float64)
+    ver = np.empty(len(e), np.int32)
+    _check(load().tpcf_bins_thresholds_3d(e.ctypes.data_as(_dp), len(e), sq.ctypes.data_as(_dp),
+                                          ver.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), "tpcf_bins_thresholds_3d")
+    return sq, ver
 
 
 def tpcf_bins_destroy(bins: int) -> None:
@@ -525,6 +562,17 @@ class Context:
         c = Catalog(self, h, tpcf_catalog_size(h), 0 if offsets is None else len(offsets) - 1)
         self._owned.append(("cat", h))
         return c
+
+    def catalog3d(self, xyz, stream=None, offsets=None) -> "Catalog":
+        h = tpcf_catalog_create_3d(self.handle, xyz, stream, offsets)
+        c = Catalog(self, h, tpcf_catalog_size(h), 0 if offsets is None else len(offsets) - 1)
+        self._owned.append(("cat", h))
+        return c
+
+    def bins3d(self, edges) -> "Bins":
+        h = tpcf_bins_create_3d(self.handle, edges)
+        self._owned.append(("bins", h))
+        return Bins(self, h, len(edges))
 
     def bins(self, edges_rad) -> "Bins":
         h = tpcf_bins_create(self.handle, edges_rad)

@@ -175,3 +175,19 @@ def test_graph_entry_points_reject_null():
     assert lib.tpcf_graph_launch(None, None) == tpcf.TPCF_EINVAL
     assert lib.tpcf_graph_stats(None, None) == tpcf.TPCF_EINVAL
     assert lib.tpcf_graph_destroy(None) == tpcf.TPCF_EINVAL
+
+
+def test_3d_thresholds_are_the_smallest_squares_reaching_each_edge():
+    from paper_1204_6630_gb300 import tpcf
+    rng = np.random.default_rng(9)
+    edges = np.concatenate([[0.0], np.sort(rng.uniform(1e-3, 1e3, 60)), [5.0, 1e18]])
+    edges = np.unique(edges)
+    S, ver = tpcf.tpcf_bins_thresholds_3d(edges)
+    assert S[0] == 0.0 and ver.all()
+    for r, s in zip(edges[1:], S[1:]):
+        assert math.sqrt(s) >= r
+        assert math.sqrt(np.nextafter(s, 0.0)) < r
+    s5 = S[list(edges).index(5.0)]
+    assert s5 <= 25.0 and math.sqrt(s5) == 5.0  # doubles just below 25 already round up to 5
+    with pytest.raises(tpcf.TpcfError):
+        tpcf.tpcf_bins_thresholds_3d(np.array([1.0, 0.5]))
