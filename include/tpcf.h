@@ -114,7 +114,8 @@ typedef struct tpcf_config {
     uint32_t flags;            /* TPCF_F_* */
     int threads;               /* kernel shape override: threads per block (0 = tuned default) */
     int ipt;                   /* kernel shape override: i-points per thread (0 = default) */
-    int jtile;                 /* kernel shape override: j-points per shared-memory tile (0 = default) */
+    int jtile;                 /* kernel shape override: j-points per shared-memory tile, a multiple
+                                  of 128 dividing 4096 (0 = default) */
     int stages;                /* kernel shape override: shared-memory pipeline stages 2..16 (0 = default) */
     uint32_t shard_index;      /* multi-process split of the pair tiles: this process's index */
     uint32_t shard_count;      /* number of shards (0 or 1 = no split); histograms of all

@@ -220,6 +220,7 @@ enum Ctl { kCtlAbort = 0, kCtlWarpsDone = 1, kCtlIssued = 2, kCtlRelease = 8, kC
 constexpr int kMaxStages = 16;   // release counters live at kCtlRelease + stage
 constexpr int kQueuePerWarp = 64;   // band pairs per warp awaiting the binary64 recheck
 constexpr int kSlowPipe = 2;        // slow path: j-points whose LUT loads are in flight
+constexpr int kMaskGroups = 32;     // fast loop: groups per warp reduction of the slow-group mask
 constexpr uint32_t kCursorBytes = 32;  // one producer cursor slot
 
 struct SmemLayout {
@@ -229,7 +230,7 @@ struct SmemLayout {
     uint32_t hist;      // (nedges + 1) * T / 2 uint32: row h, column c at word h * T/2 + c (see HistCol)
     uint32_t cos_thr;   // nedges doubles
     uint32_t lo, hi, cos32, zlo, zhi;  // nedges floats each
-    uint32_t lut;       // kLutCells uint32 (screen only)
+    uint32_t lut;       // kLutCells 16-bit entries (screen only)
     uint32_t queue;     // W * kQueuePerWarp unsettled pairs (i, j) (uint2, screen only)
     uint32_t prod;      // W producer cursors (one per warp, used by its lane 0)
     uint32_t total;
@@ -255,13 +256,51 @@ __host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S,
     L.zlo = off; off += (uint32_t)nedges * 4;
     L.zhi = off; off += (uint32_t)nedges * 4;
     off = align_up(off, 16);
-    L.lut = off; off += plain ? 0u : (uint32_t)kLutCells * 4;
+    L.lut = off; off += plain ? 0u : (uint32_t)kLutCells * 2;
     off = align_up(off, 16);
     L.queue = off; off += plain ? 0u : (uint32_t)(T / 32) * kQueuePerWarp * 8;
     off = align_up(off, 16);
     L.prod = off; off += (uint32_t)(T / 32) * kCursorBytes;
     L.total = off;
     return L;
+}
+
+// ============================================================== LUT entries
+// A cell of the shared LUT is a 16-bit code, read sign-extended:
+//   - settled in row P < ne (P == Q): P (0 <= code < kLutRowLimit);
+//   - settled in the overflow row (P == Q == ne): kLutSkip, a non-negative
+//     code >= kLutRowLimit, so the pair adds nothing (the overflow row is
+//     never merged: the finalize derives it from the pair total);
+//   - unsettled (edges [P, Q) open): bit 15 set (negative), P in bits 0..8,
+//     min(Q - P, 63) in bits 9..14; the span 63 stands for Q = ne, a wider
+//     range that every resolver handles with the same result (the edges
+//     past the true Q are decided "not crossed" by their bounds).
+// Rows fit 9 bits: ne <= TPCF_MAX_EDGES = 321.
+constexpr uint32_t kLutRowLimit = 512;
+constexpr uint32_t kLutSkip = 0x4000;
+constexpr uint32_t kLutSpanCap = 63;
+
+__device__ __forceinline__ unsigned short lut_code(uint32_t P, uint32_t Q, uint32_t ne) {
+    if (P == Q) return (unsigned short)(P == ne ? kLutSkip : P);
+    return (unsigned short)(0x8000u | P | (min(Q - P, kLutSpanCap) << 9));
+}
+__device__ __forceinline__ int lut_P(int x) { return x & 0x1ff; }
+__device__ __forceinline__ int lut_Q(int x, int ne) {
+    const int span = (x >> 9) & 0x3f;
+    return span == (int)kLutSpanCap ? ne : (x & 0x1ff) + span;
+}
+
+// Byte offset of histogram row h from a thread's column: h * (T/2) * 4 = h << log2(2T).
+template <int T>
+__host__ __device__ constexpr int row_shift() {
+    static_assert(T == 128 || T == 256 || T == 512 || T == 1024, "power-of-two block");
+    return T == 128 ? 8 : T == 256 ? 9 : T == 512 ? 10 : 11;
+}
+
+__device__ __forceinline__ int ld_shared_s16(uint32_t addr) {
+    int v;
+    asm volatile("ld.shared.s16 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
 }
 
 // ============================================================== block helpers
@@ -286,15 +325,12 @@ __device__ void load_bins(const BinsDev* bd, const WorkDesc& wd, bool plain) {
         zhi[k] = bd->zhi[k];
     }
     if (!plain) {
-        // Shared copy of the LUT re-encoded for this block shape: a settled entry
-        // (P == Q) holds the byte offset P * (T/2) * 4 of row P from a thread's
-        // column (non-negative); an unsettled entry has bit 31 set and P, Q in
-        // bits 0..11, 12..23.
-        uint32_t* lut = sptr<uint32_t>(wd.off_lut);
+        // Shared copy of the LUT as 16-bit entries (see lut_code): two cells per
+        // word, so lanes whose pairs fall in neighbouring cells share a bank word.
+        unsigned short* lut = sptr<unsigned short>(wd.off_lut);
         for (int k = threadIdx.x; k < kLutCells; k += T) {
             const uint32_t e = bd->lut[k];
-            const uint32_t P = e & 0xffffu, Q = e >> 16;
-            lut[k] = (P == Q) ? P * (uint32_t)(T / 2) * 4u : 0x80000000u | P | (Q << 12);
+            lut[k] = lut_code(e & 0xffffu, e >> 16, (uint32_t)ne);
         }
     }
 }
@@ -428,10 +464,10 @@ __device__ __forceinline__ float screen_value(const WorkDesc& wd, const SubProbl
 }
 
 // LUT entry of screen value e (see slow_group).
-__device__ __forceinline__ uint32_t lut_entry(const WorkDesc& wd, float e) {
+__device__ __forceinline__ int lut_entry(const WorkDesc& wd, float e) {
     const float v = __saturatef(e * wd.lut_scale);
     const float f = fmaf(v, 16384.0f, 8388608.0f);
-    return ld_shared_u32(smem_addr(dyn_smem) + wd.off_lut + (__float_as_uint(f) - 0x4B000000u) * 4u);
+    return ld_shared_s16(smem_addr(dyn_smem) + wd.off_lut + (__float_as_uint(f) - 0x4B000000u) * 2u);
 }
 
 // Histogram index of an unsettled pair: the FP32 comparison with the edges
@@ -448,7 +484,7 @@ __device__ __forceinline__ float euclid_z(float ax, float ay, float az, const fl
 __device__ __forceinline__ uint32_t euclid_cell_addr(const WorkDesc& wd, float z, uint32_t lut_base) {
     int k = ((int)__float_as_uint(z) - wd.zbits0) >> wd.zshift;
     k = min(max(k, 0), kLutCells - 1);
-    return lut_base + (uint32_t)k * 4u;
+    return lut_base + (uint32_t)k * 2u;
 }
 
 // binary64 d^2 in the definition's order: differences, squares, left-to-right sum.
@@ -461,11 +497,11 @@ __device__ __forceinline__ double dist2_64(const Point64& a, const Point64& b) {
 // bounds (increasing with the edge index; z >= zhi_m proves d^2 >= S_m, z <
 // zlo_m proves d^2 < S_m).  Returns h >= 0 when z settles it; otherwise -1 and
 // the edges still open, [*lo, *hi).
-__device__ __forceinline__ int euclid_resolve(const WorkDesc& wd, float z, uint32_t ent, int* lo_out, int* hi_out) {
+__device__ __forceinline__ int euclid_resolve(const WorkDesc& wd, float z, int ent, int* lo_out, int* hi_out) {
     const float* zlo = sptr<const float>(wd.off_zlo);
     const float* zhi = sptr<const float>(wd.off_zhi);
-    const int Q = (int)((ent >> 12) & 0xfffu);
-    int lo = (int)(ent & 0xfffu), hi = Q;
+    const int Q = lut_Q(ent, wd.ne);
+    int lo = lut_P(ent), hi = Q;
     while (lo < hi) {  // first m in [P, Q) with z < zhi[m]: the edges below are crossed
         const int mid = (lo + hi) >> 1;
         if (z >= zhi[mid]) lo = mid + 1; else hi = mid;
@@ -505,8 +541,8 @@ __device__ __forceinline__ int classify_unsettled(const WorkDesc& wd, int sub, u
     if (wd.euclid) {
         const float4 a = __ldg(sp.a32 + ig), b = __ldg(sp.b32 + jg);
         const float z = euclid_z(a.x, a.y, a.z, b);
-        const uint32_t ent = ld_shared_u32(euclid_cell_addr(wd, z, smem_addr(dyn_smem) + wd.off_lut));
-        if ((int)ent >= 0) return (int)(ent / (uint32_t)(4 * (blockDim.x / 2)));  // settled (not expected)
+        const int ent = ld_shared_s16(euclid_cell_addr(wd, z, smem_addr(dyn_smem) + wd.off_lut));
+        if (ent >= 0) return ent == (int)kLutSkip ? wd.ne : ent;  // settled (not expected)
         int lo = 0, hi = 0;
         const int h0 = euclid_resolve(wd, z, ent, &lo, &hi);
         if (h0 >= 0) return h0;
@@ -517,9 +553,9 @@ __device__ __forceinline__ int classify_unsettled(const WorkDesc& wd, int sub, u
         return h;
     }
     const float e = screen_value(wd, sp, ig, jg);
-    const uint32_t ent = lut_entry(wd, e);
-    if ((int)ent >= 0) return (int)(ent / (uint32_t)(4 * (blockDim.x / 2)));  // settled (not expected)
-    const Resolved rs = resolve_f32(wd, e, (int)(ent & 0xfffu), (int)((ent >> 12) & 0xfffu));
+    const int ent = lut_entry(wd, e);
+    if (ent >= 0) return ent == (int)kLutSkip ? wd.ne : ent;  // settled (not expected)
+    const Resolved rs = resolve_f32(wd, e, lut_P(ent), lut_Q(ent, wd.ne));
     if (rs.h >= 0) return rs.h;
     uint32_t mm;
     const int h = band_index(wd, sub, ig, jg, rs.nbv, rs.nav, rs.h32, &mm);
@@ -593,12 +629,12 @@ __device__ __forceinline__ void unsettled_pair(const WorkDesc& wd, int sub, floa
                                                const float4& b, uint32_t ig, uint32_t jg, const HistCol& hc) {
     if (wd.chord_ok) {
         const float e = fmaf(az, b.z, fmaf(ay, b.y, fmaf(ax, b.x, wd.neg_fast_t)));
-        const uint32_t ent = lut_entry(wd, e);
+        const int ent = lut_entry(wd, e);
         const float dx = ax - b.x, dy = ay - b.y, dz = az - b.z;
         const float z = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float* zlo = sptr<const float>(wd.off_zlo);
         const float* zhi = sptr<const float>(wd.off_zhi);
-        int lo = (int)(ent & 0xfffu), hi = (int)((ent >> 12) & 0xfffu);
+        int lo = lut_P(ent), hi = lut_Q(ent, wd.ne);
         const int Q = hi;
         while (lo < hi) {  // first m in [P, Q) with z < zhi[m]
             const int mid = (lo + hi) >> 1;
@@ -622,6 +658,19 @@ __device__ __forceinline__ float pick(const float (&v)[R], int k) {
 #pragma unroll
     for (int r = 1; r < R; ++r) x = (k == r) ? v[r] : x;
     return x;
+}
+
+// Screen values of a group: e[u][r] = fma(az, bz, fma(ay, by, fma(ax, bx, -T)))
+// for the U j-points at b (one broadcast shared load each) and the R i-points.
+template <int R, int U>
+__device__ __forceinline__ void screen_group(float (&e)[U][R], const float (&ax)[R], const float (&ay)[R],
+                                             const float (&az)[R], const float4* b, float neg_t) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const float4 q = b[u];
+#pragma unroll
+        for (int r = 0; r < R; ++r) e[u][r] = fmaf(az[r], q.z, fmaf(ay[r], q.y, fmaf(ax[r], q.x, neg_t)));
+    }
 }
 
 // Slow path for a group of U j (warp-uniform), all R pairs of every lane,
@@ -667,7 +716,7 @@ __device__ __forceinline__ void slow_group(const WorkDesc& wd, int sub, float (&
         }
     }
     constexpr int D = kSlowPipe;  // loads run D - 1 j ahead of the reductions
-    const uint32_t lut_adj = smem_addr(dyn_smem) + wd.off_lut - 0x4B000000u * 4u;  // + 4 bits(f): entry
+    const uint32_t lut_adj = smem_addr(dyn_smem) + wd.off_lut - 0x4B000000u * 2u;  // + 2 bits(f): entry
     uint32_t ent[D][R];
     uint32_t um = 0;  // unsettled pairs of this lane: pair k = u * R + r at bit U * R - 1 - k
 #pragma unroll
@@ -677,14 +726,15 @@ __device__ __forceinline__ void slow_group(const WorkDesc& wd, int sub, float (&
             for (int r = 0; r < R; ++r) {
                 const float v = __saturatef(e[u][r] * wd.lut_scale);
                 const float f = fmaf(v, 16384.0f, 8388608.0f);
-                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(ent[u % D][r]) : "r"(__float_as_uint(f) * 4u + lut_adj));
+                asm volatile("ld.shared.s16 %0, [%1];" : "=r"(ent[u % D][r]) : "r"(__float_as_uint(f) * 2u + lut_adj));
             }
         }
         if (u >= D - 1) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
+                // settled rows add one; overflow (skip) and unsettled codes add nothing here
                 const uint32_t x = ent[(u - (D - 1)) % D][r];
-                if ((int)x >= 0) red_add_shared(hc.addr + x, hc.inc);
+                if (x < kLutRowLimit) red_add_shared(hc.addr + (x << row_shift<T>()), hc.inc);
                 um = __funnelshift_l(x, um, 1);  // (um << 1) | (x >> 31)
             }
         }
@@ -745,13 +795,13 @@ __device__ __forceinline__ void slow_group_euclid(const WorkDesc& wd, int sub, c
             }
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(ent[u % D][r]) : "r"(euclid_cell_addr(wd, z[r], lut_base)));
+                asm volatile("ld.shared.s16 %0, [%1];" : "=r"(ent[u % D][r]) : "r"(euclid_cell_addr(wd, z[r], lut_base)));
         }
         if (u >= D - 1) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const uint32_t x = ent[(u - (D - 1)) % D][r];
-                if ((int)x >= 0) red_add_shared(hc.addr + x, hc.inc);
+                if (x < kLutRowLimit) red_add_shared(hc.addr + (x << row_shift<T>()), hc.inc);
                 um = __funnelshift_l(x, um, 1);  // (um << 1) | (x >> 31)
             }
         }
@@ -762,7 +812,7 @@ __device__ __forceinline__ void slow_group_euclid(const WorkDesc& wd, int sub, c
             um &= ~(1u << (U * R - 1 - k));
             const int u = k / R, r = k % R;
             const float z = euclid_z(pick(ax, r), pick(ay, r), pick(az, r), j_point(jj + u));
-            const uint32_t x = ld_shared_u32(euclid_cell_addr(wd, z, lut_base));
+            const int x = ld_shared_s16(euclid_cell_addr(wd, z, lut_base));
             int lo = 0, hi = 0;
             const int h = euclid_resolve(wd, z, x, &lo, &hi);
             if (h >= 0) hist_inc<T>(hc, h);
@@ -1001,29 +1051,35 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         } else if constexpr (MODE == kModeScreen) {
             const float4* sj = sptr<const float4>(wd.off_stage + stage * wd.stage_bytes);
             // Fast loop: e = FP32 dot minus the range offset T for R i-points; the AND
-            // of the group's sign bits is negative when every pair is certainly
-            // overflow.  A group with some e >= 0 in the warp takes the slow path.
-            // j-points per group: the group's screen values stay in registers until
-            // the slow path has used them (2 x R at 512 threads, 4 x R below)
+            // of a group's sign bits is negative when every pair of the group is
+            // certainly overflow.  The loop does not branch per group: each group
+            // shifts one bit (some e >= 0 in this lane) into a mask, and after
+            // kMaskGroups groups one warp reduction names the groups that take the
+            // slow path, which recomputes their screen values (bit-identical).
             constexpr int U = R >= 16 ? 2 : 4;
-            // two groups per iteration: the loop's own compare and branch once per
-            // 2U j (measured: more unrolling copies the slow path and loses)
-#pragma unroll 2
-            for (int jj = 0; jj < J; jj += U) {
-                float eu[U][R];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const float4 b = sj[jj + u];
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        eu[u][r] = fmaf(az[r], b.z, fmaf(ay[r], b.y, fmaf(ax[r], b.x, wd.neg_fast_t)));
+            static_assert(kMaskGroups <= 32, "one mask bit per group");
+#pragma unroll 1
+            for (int jc = 0; jc < J; jc += kMaskGroups * U) {
+                uint32_t lane_mask = 0;
+#pragma unroll 8
+                for (int g = 0; g < kMaskGroups; ++g) {
+                    float eu[U][R];
+                    screen_group<R, U>(eu, ax, ay, az, sj + jc + g * U, wd.neg_fast_t);
+                    // (~AND) >> 31: 1 when some screen value of the group is >= 0
+                    lane_mask = __funnelshift_l(~(uint32_t)and_tree<U * R>(&eu[0][0]), lane_mask, 1);
                 }
-                // AND of the group's screen values (a balanced tree, not a serial
-                // chain in front of the vote): negative when every pair is overflow
-                if (!__any_sync(0xffffffffu, and_tree<U * R>(&eu[0][0]) >= 0)) continue;
-                slow_group<T, R, U>(wd, cur_sub, eu, ax, ay, az, [&](int j) { return sj[j]; }, jj, ibase, jbase, diag,
-                                    hc);
-                maybe_drain<T>(wd, cur_sub, hc);
+                uint32_t m = __reduce_or_sync(0xffffffffu, lane_mask);  // bit kMaskGroups - 1 - g: group g
+#pragma unroll 1
+                while (m) {
+                    const int g = kMaskGroups - __ffs(m);  // lowest set bit first
+                    m &= m - 1u;
+                    const int jj = jc + g * U;
+                    float eu[U][R];
+                    screen_group<R, U>(eu, ax, ay, az, sj + jj, wd.neg_fast_t);
+                    slow_group<T, R, U>(wd, cur_sub, eu, ax, ay, az, [&](int j) { return sj[j]; }, jj, ibase, jbase,
+                                        diag, hc);
+                    maybe_drain<T>(wd, cur_sub, hc);
+                }
             }
         } else {
             const Point64* sj = sptr<const Point64>(wd.off_stage + stage * wd.stage_bytes);

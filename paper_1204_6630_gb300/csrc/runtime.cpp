@@ -845,7 +845,8 @@ bool shape_for(tpcf_ctx* ctx, int mode, int nedges, int T, int R, int Jreq, int 
     const int I = T * R;
     int J = Jreq ? Jreq : 1024;
     if (J > I) J = I;
-    if ((int)kPad % J != 0 || (int)kPad % I != 0 || J % 32 != 0 || I % J != 0) return false;
+    // (a tile is a whole number of the fast loop's 32-group mask chunks: 128 j)
+    if ((int)kPad % J != 0 || (int)kPad % I != 0 || J % 128 != 0 || I % J != 0) return false;
     int S = Sreq ? Sreq : 4;
     if (S < 2 || S > 16) return false;
     size_t smem = count_smem_bytes(mode, T, R, J, S, nedges);
