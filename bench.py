@@ -265,6 +265,21 @@ def run_gpu(args):
                 "histograms_identical": same}
         assert same, "FP32 screen + recheck and all-binary64 kernels disagree"
 
+    # ---- spatial pruning (opt-in flag, not the brute-force headline): one launch
+    # on the same resident catalogs, histograms compared with the brute force
+    prune = None
+    if world == 1 and not args.no_prune:
+        with tpcf.Context(device=local, flags=tpcf.TPCF_F_PRUNE) as cp:
+            cd, cr, b = cp.catalog(dev_d, stream), cp.catalog(dev_r, stream), cp.bins(w.edges)
+            cp.count_all(cd, cr, b, stream)  # warm-up
+            (qdd, qdr, qrr), stp = cp.count_all(cd, cr, b, stream, stats=True)
+        prune = {"flag": "TPCF_F_PRUNE", "kernel_ms": stp["kernel_ms"],
+                 "pairs_covered_per_s": stp["pairs"] / stp["kernel_ms"] * 1e3,
+                 "pair_slots_skipped": stp["pruned_pairs"],
+                 "skipped_fraction": stp["pruned_pairs"] / stp["pairs"],
+                 "histograms_identical": all(np.array_equal(a, c) for a, c in zip((qdd, qdr, qrr), (dd, dr, rr)))}
+        assert prune["histograms_identical"], "pruned and brute-force histograms disagree"
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
@@ -305,6 +320,7 @@ def run_gpu(args):
         "band": {"pairs": st["band_pairs"], "fraction": st["band_pairs"] / max(1, st["pairs"]),
                  "fp32_mismatch": st["band_mismatch"]},
         "fp64_plain": fp64,
+        "pruning": prune,
         "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
@@ -402,6 +418,17 @@ def run_jackknife(args):
         t0 = time.perf_counter()
         loo, w_loo, cov, jst = ctx.jackknife(cd, cr, b, stream, stats=True)
         loo_s = time.perf_counter() - t0
+    # the same leave-one-out jackknife with spatial pruning (opt-in): most block
+    # pairs of the full catalogs are farther apart than the 5 deg range
+    with tpcf.Context(flags=tpcf.TPCF_F_PRUNE) as cq:
+        qd, qr, qb = cq.catalog(d, offsets=doff), cq.catalog(r, offsets=roff), cq.bins(edges)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qloo, qw, qcov, qst = cq.jackknife(qd, qr, qb, stream, stats=True)
+        qloo_s = time.perf_counter() - t0
+    loo_same = (np.array_equal(qloo, loo) and np.array_equal(qw, w_loo, equal_nan=True)
+                and np.array_equal(qcov, cov, equal_nan=True))
+    assert loo_same, "pruned and brute-force leave-one-out results disagree"
     gm, sm = statistics.median(graph_ms), statistics.median(sep_ms)
     print(json.dumps({
         "mode": "jackknife", "metric": METRIC, "value": pairs / gm * 1e3, "unit": UNIT,
@@ -420,7 +447,11 @@ def run_jackknife(args):
         "leave_one_out": {"s": loo_s, "kernel_ms": jst["kernel_ms"], "pairs": jst["pairs"],
                           "pairs_per_s": jst["pairs"] / loo_s,
                           "what": "DD/DR/RR of the catalogs without each patch (512 resamplings), w and its "
-                                  "covariance: one launch over every pair of the full catalogs"}}))
+                                  "covariance: one launch over every pair of the full catalogs"},
+        "leave_one_out_pruned": {"flag": "TPCF_F_PRUNE", "s": qloo_s, "kernel_ms": qst["kernel_ms"],
+                                 "pairs_covered_per_s": qst["pairs"] / qloo_s,
+                                 "skipped_fraction": qst["pruned_pairs"] / max(1, qst["pairs"]),
+                                 "identical_to_brute_force": loo_same}}))
     return 0
 
 
@@ -527,6 +558,18 @@ def run_large(args):
         ds = w.data[np.sort(g.choice(nd, args.sub, replace=False))]
         rs = w.rand[np.sort(g.choice(nr, args.sub, replace=False))]
         sdd, sdr, srr = ctx.count_all(ctx.catalog(ds), ctx.catalog(rs), b)
+    # the same counts with spatial pruning (opt-in; not the brute-force headline)
+    with tpcf.Context(flags=tpcf.TPCF_F_PRUNE) as cq:
+        qd = cq.catalog(torch.from_numpy(w.data).cuda(), stream)
+        qr = cq.catalog(torch.from_numpy(w.rand).cuda(), stream)
+        qb = cq.bins(w.edges)
+        cq.count_all(qd, qr, qb, stream)
+        (qdd, qdr, qrr), qst = cq.count_all(qd, qr, qb, stream, stats=True)
+    prune = {"flag": "TPCF_F_PRUNE", "kernel_ms": qst["kernel_ms"],
+             "pairs_covered_per_s": qst["pairs"] / qst["kernel_ms"] * 1e3,
+             "skipped_fraction": qst["pruned_pairs"] / qst["pairs"],
+             "histograms_identical": all(np.array_equal(x, y) for x, y in zip((qdd, qdr, qrr), (dd, dr, rr)))}
+    assert prune["histograms_identical"], "pruned and brute-force histograms disagree"
     t0 = time.perf_counter()
     cores = os.cpu_count() or 1
     odd = oracle.count_auto(ds, w.edges, cores)
@@ -548,6 +591,7 @@ def run_large(args):
                  "fp32_mismatch": st["band_mismatch"]},
         "subsample_parity": {"points_per_catalog": args.sub, "identical_to_oracle": same,
                              "oracle_s": oracle_s, "oracle_threads": cores},
+        "pruning": prune,
         "clocks": clocks.summary()}))
     assert same, "subsample histograms differ from the oracle"
     return 0
@@ -612,6 +656,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=16_000, help="points per catalog per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-binary64 kernel comparison")
+    ap.add_argument("--no-prune", action="store_true", help="skip the spatial-pruning launch of the default line")
     ap.add_argument("--workload", default="octant_precision",
                     choices=["octant_precision", "jackknife", "serving", "large", "box3d"])
     ap.add_argument("--jobs", type=int, default=2000, help="serving: number of jobs")

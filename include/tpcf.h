@@ -89,6 +89,14 @@ extern "C" {
 #define TPCF_F_PACKED_FMA 0x4u       /* FP32 screen with packed FP32x2 FMA (fma.rn.f32x2) instead of scalar FMA */
 #define TPCF_F_AUTOTUNE 0x8u         /* the first counting call of a workload class times every kernel
                                         shape that fits and the context keeps the fastest */
+#define TPCF_F_PRUNE 0x10u           /* spatial pruning: each counting launch skips the blocks of
+                                        (one warp's i-points x 128 j-points) whose bounding spheres
+                                        are provably farther apart than the last edge (every pair
+                                        in them is overflow); counts are unchanged, the skipped pair
+                                        slots are reported in tpcf_stats.pruned_pairs.  Screen
+                                        kernels only (ignored with TPCF_PLAIN_FP64 and
+                                        TPCF_F_PACKED_FMA).  Not in the paper (its brute force
+                                        evaluates every pair). */
 #define TPCF_F_TEST_WAIT_TIMEOUT 0x100u /* test hook: the first j-tile copy of each counting
                                            launch is never issued, so its bounded wait expires
                                            and the call returns TPCF_ETIMEOUT */
@@ -132,6 +140,8 @@ typedef struct tpcf_stats {
     uint32_t device_error;  /* device error word of the call (0 = none) */
     uint32_t launches;      /* kernels launched by the call */
     double kernel_ms;       /* device time of the counting launch (CUDA events) */
+    uint64_t pruned_pairs;  /* pair slots skipped by TPCF_F_PRUNE (blocks of 32 * ipt i-points x
+                               128 j-points, padding and masked slots included; 0 without it) */
 } tpcf_stats;
 
 /* ------------------------------------------------------------------ misc */

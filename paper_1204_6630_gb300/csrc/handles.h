@@ -69,6 +69,7 @@ struct tpcf_catalog {
     tpcf::Point64* d64 = nullptr;
     float4* d32 = nullptr;
     float4* d32x2 = nullptr;        // (x,x,y,y),(z,z,0,0) per point for the packed screen
+    float4* caps = nullptr;         // bounding sphere of each kCapPoints-point group (spatial pruning)
     std::vector<uint64_t> offsets;  // segments (empty = one segment), input order
     std::vector<uint64_t> seg_start;  // device position of each segment's first point (multiples of
                                       // kSegAlign; zero vectors fill the gaps), size nseg + 1

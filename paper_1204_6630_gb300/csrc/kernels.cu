@@ -222,6 +222,7 @@ constexpr int kQueuePerWarp = 64;   // band pairs per warp awaiting the binary64
 constexpr int kSlowPipe = 2;        // slow path: j-points whose LUT loads are in flight
 constexpr int kMaskGroups = 32;     // fast loop: groups per warp reduction of the slow-group mask
 constexpr uint32_t kCursorBytes = 32;  // one producer cursor slot
+constexpr uint32_t kPruneSlotBytes = 32;  // float4 i-sphere, B's sphere pointer, pruned pair slots (u64)
 
 struct SmemLayout {
     uint32_t bars;      // S full mbarriers
@@ -233,6 +234,7 @@ struct SmemLayout {
     uint32_t lut;       // kLutCells 16-bit entries (screen only)
     uint32_t queue;     // W * kQueuePerWarp unsettled pairs (i, j) (uint2, screen only)
     uint32_t prod;      // W producer cursors (one per warp, used by its lane 0)
+    uint32_t icap;      // W pruning slots: the warp's i-sphere, B's sphere array, pruned pair slots
     uint32_t total;
 };
 
@@ -261,6 +263,8 @@ __host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S,
     L.queue = off; off += plain ? 0u : (uint32_t)(T / 32) * kQueuePerWarp * 8;
     off = align_up(off, 16);
     L.prod = off; off += (uint32_t)(T / 32) * kCursorBytes;
+    off = align_up(off, 16);
+    L.icap = off; off += (uint32_t)(T / 32) * kPruneSlotBytes;
     L.total = off;
     return L;
 }
@@ -526,6 +530,12 @@ __device__ __forceinline__ int euclid_band_index(const WorkDesc& wd, int sub, ui
     const double* sthr = sptr<const double>(wd.off_cthr);
     const float* s32 = sptr<const float>(wd.off_c32);
     const double d2 = dist2_64(ldg_point(sp.a64 + ig), ldg_point(sp.b64 + jg));
+    // two padding points (+inf) are NaN apart: not a pair (overflow, never merged);
+    // real points are finite, |x| <= 1e28, so their binary64 d^2 is finite
+    if (d2 != d2) {
+        *mismatch = 0u;
+        return wd.ne;
+    }
     int h = lo, h32 = lo;
     for (int m = lo; m < hi; ++m) {
         h += (d2 >= sthr[m]);
@@ -811,12 +821,19 @@ __device__ __forceinline__ void slow_group_euclid(const WorkDesc& wd, int sub, c
             const int k = U * R - 1 - (31 - __clz(um));
             um &= ~(1u << (U * R - 1 - k));
             const int u = k / R, r = k % R;
+            // a pair given z = +inf above (padding, the diagonal) reads the last
+            // cell, which is unsettled only when the FP32 bounds overflow (huge
+            // coordinates): such pairs are not counted
+            const uint32_t ig = ibase + 32u * (uint32_t)r, jg = jbase + (uint32_t)(jj + u);
+            if ((wd.need_idx && !(jg < nb && ig < na)) || (diag == kDiagAbove && !(jg > ig)) ||
+                (diag == kDiagOffSelf && jg == ig))
+                continue;
             const float z = euclid_z(pick(ax, r), pick(ay, r), pick(az, r), j_point(jj + u));
             const int x = ld_shared_s16(euclid_cell_addr(wd, z, lut_base));
             int lo = 0, hi = 0;
             const int h = euclid_resolve(wd, z, x, &lo, &hi);
             if (h >= 0) hist_inc<T>(hc, h);
-            else queue_pair<T>(wd, sub, ibase + 32u * (uint32_t)r, jbase + (uint32_t)(jj + u), hc);
+            else queue_pair<T>(wd, sub, ig, jg, hc);
         }
     }
 }
@@ -827,6 +844,76 @@ __device__ __forceinline__ void maybe_drain(const WorkDesc& wd, int sub, const H
     __syncwarp();
     if (*sptr<volatile int>(queue_count_off(wd, (int)(threadIdx.x >> 5))) >= kQueuePerWarp / 2)
         warp_drain_queue<T>(wd, sub, hc);
+}
+
+// ============================================================== spatial pruning
+// Every point p of a group lies within radius r of the group's centre c
+// (bounding spheres from prep_caps_kernel, in the catalog's scaled space).  By
+// the triangle inequality, any pair (a, b) of two groups is at least
+// |cA - cB| - rA - rB apart; when that gap exceeds prune_thr (the host's
+// bound: every pair that far apart is overflow), the block is skipped.  The
+// FP32 evaluation here under-estimates the gap (relative margin 2^-20 on the
+// centre distance and on the radii, far above the few-ulp rounding of these
+// FP32 operations).
+constexpr float kPruneMargin = 9.5367431640625e-07f;  // 2^-20
+
+__device__ __forceinline__ bool prune_block(const WorkDesc& wd, const float4& ic, const float4& jc) {
+    const float dx = ic.x - jc.x, dy = ic.y - jc.y, dz = ic.z - jc.z;
+    const float D = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+    const float L = D * (1.0f - kPruneMargin) - (ic.w + jc.w) * (1.0f + kPruneMargin);
+    return L > wd.prune_thr;
+}
+
+// The sphere of a warp's 32 R i-points (R / 4 consecutive groups): centre the
+// FP32 mean of the groups' centres, radius max_k |c - c_k| + r_k (enlarged by
+// 2^-20 relative); empty groups (radius -1e30) are left out.
+template <int R>
+__device__ __forceinline__ float4 warp_sphere(const float4* caps) {
+    static_assert((32 * R) % kCapPoints == 0, "whole groups per warp");
+    constexpr int K = 32 * R / kCapPoints;
+    float4 g[K];
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        g[k] = __ldg(caps + k);
+        if (g[k].w > -1e29f) {
+            sx += g[k].x;
+            sy += g[k].y;
+            sz += g[k].z;
+            ++cnt;
+        }
+    }
+    if (cnt == 0) return make_float4(0.f, 0.f, 0.f, -1e30f);
+    const float inv = 1.0f / (float)cnt;
+    const float cx = sx * inv, cy = sy * inv, cz = sz * inv;
+    float r = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (g[k].w > -1e29f) {
+            const float dx = cx - g[k].x, dy = cy - g[k].y, dz = cz - g[k].z;
+            r = fmaxf(r, sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) + g[k].w);
+        }
+    }
+    return make_float4(cx, cy, cz, r * (1.0f + kPruneMargin));
+}
+
+struct PruneSlot {
+    float4 sphere;          // the warp's i-points
+    const float4* b_caps;   // spheres of the current sub-problem's B
+    unsigned long long pruned;  // pair slots skipped by this warp
+};
+static_assert(sizeof(PruneSlot) == kPruneSlotBytes, "prune slot layout");
+
+// One pruning test for the warp's i-points against the kCapPoints-point group
+// holding j-point jg0 of B (warp-uniform); lane 0 counts the skipped slots.
+__device__ __forceinline__ bool prune_chunk(const WorkDesc& wd, uint32_t jg0, uint32_t slots) {
+    PruneSlot* ps = sptr<PruneSlot>(wd.off_icap + (threadIdx.x >> 5) * kPruneSlotBytes);
+    const float4 ic = ps->sphere;
+    const float4 jc = __ldg(ps->b_caps + jg0 / kCapPoints);
+    if (!prune_block(wd, ic, jc)) return false;
+    if ((threadIdx.x & 31) == 0) ps->pruned += slots;
+    return true;
 }
 
 // ============================================================== the counting kernel
@@ -861,6 +948,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         fence_mbar_init();
     }
     for (int k = tid; k < kCtlWords; k += T) ctl[k] = 0;
+    if (tid < W) sptr<PruneSlot>(wd.off_icap + (uint32_t)tid * kPruneSlotBytes)->pruned = 0ull;
     {
         uint32_t* hist = sptr<uint32_t>(wd.off_hist);
         for (int k = tid; k < (wd.nedges_max + 1) * (T / 2); k += T) hist[k] = 0;
@@ -937,6 +1025,15 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                 atomicAdd(wd.stats + kStatPairs,
                           (unsigned long long)item_pairs(cons.g, sp.na, sp.nb, sp.auto_mode != 0, wd.I, wd.Jc));
             ibase = cons.g.i0 + (uint32_t)warp * (32u * R) + (uint32_t)lane;
+            if (wd.prune) {
+                const float4 sph = warp_sphere<R>(sp.a_caps + (ibase - (uint32_t)lane) / kCapPoints);
+                if (lane == 0) {
+                    PruneSlot* ps = sptr<PruneSlot>(wd.off_icap + (uint32_t)warp * kPruneSlotBytes);
+                    ps->sphere = sph;
+                    ps->b_caps = sp.b_caps;
+                }
+                __syncwarp();
+            }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const uint32_t i = ibase + 32u * r;
@@ -1031,22 +1128,25 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             // fused sum of squares; e < 0 proves d^2 > S_B (every pair overflow)
             const float4* sj = sptr<const float4>(wd.off_stage + stage * wd.stage_bytes);
             constexpr int U = R >= 16 ? 2 : 4;
+            for (int jc = 0; jc < J; jc += (int)kCapPoints) {
+                if (wd.prune && prune_chunk(wd, jbase + (uint32_t)jc, 32u * R * kCapPoints)) continue;
 #pragma unroll 2
-            for (int jj = 0; jj < J; jj += U) {
-                float eu[U][R];
+                for (int jj = jc; jj < jc + (int)kCapPoints; jj += U) {
+                    float eu[U][R];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const float4 b = sj[jj + u];
+                    for (int u = 0; u < U; ++u) {
+                        const float4 b = sj[jj + u];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float dx = ax[r] - b.x, dy = ay[r] - b.y, dz = az[r] - b.z;
-                        eu[u][r] = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, wd.neg_fast_t)));
+                        for (int r = 0; r < R; ++r) {
+                            const float dx = ax[r] - b.x, dy = ay[r] - b.y, dz = az[r] - b.z;
+                            eu[u][r] = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, wd.neg_fast_t)));
+                        }
                     }
+                    if (!__any_sync(0xffffffffu, and_tree<U * R>(&eu[0][0]) >= 0)) continue;
+                    slow_group_euclid<T, R, U>(wd, cur_sub, ax, ay, az, [&](int j) { return sj[j]; }, jj, ibase,
+                                               jbase, diag, hc);
+                    maybe_drain<T>(wd, cur_sub, hc);
                 }
-                if (!__any_sync(0xffffffffu, and_tree<U * R>(&eu[0][0]) >= 0)) continue;
-                slow_group_euclid<T, R, U>(wd, cur_sub, ax, ay, az, [&](int j) { return sj[j]; }, jj, ibase, jbase,
-                                           diag, hc);
-                maybe_drain<T>(wd, cur_sub, hc);
             }
         } else if constexpr (MODE == kModeScreen) {
             const float4* sj = sptr<const float4>(wd.off_stage + stage * wd.stage_bytes);
@@ -1060,6 +1160,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             static_assert(kMaskGroups <= 32, "one mask bit per group");
 #pragma unroll 1
             for (int jc = 0; jc < J; jc += kMaskGroups * U) {
+                if (wd.prune && prune_chunk(wd, jbase + (uint32_t)jc, 32u * R * kMaskGroups * U)) continue;
                 uint32_t lane_mask = 0;
 #pragma unroll 8
                 for (int g = 0; g < kMaskGroups; ++g) {
@@ -1150,6 +1251,10 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     if (!aborted && cur_sub >= 0) {
         if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
         warp_flush_hist<T>(hc, wd.ne, cur_hist);
+    }
+    if (wd.prune && lane == 0) {
+        const unsigned long long np = sptr<PruneSlot>(wd.off_icap + (uint32_t)warp * kPruneSlotBytes)->pruned;
+        if (np) atomicAdd(wd.stats + kStatPruned, np);
     }
     __syncwarp();
     if (lane == 0) {
@@ -1438,9 +1543,10 @@ __global__ void prep_gather_kernel(const double* __restrict__ xyz, uint32_t n,
 
 // Padding of 3-D catalogs: (+inf, +inf, +inf).  A pair with a real point has
 // screen value -inf (fails the fast test) and z = +inf; two padding points
-// give NaN: both land in the overflow cell of the LUT (and fail the binary64
-// comparisons), so padding is never counted (unit-vector catalogs are padded
-// with zero vectors instead).
+// give NaN: both land in the overflow cell of the LUT, and where the screen
+// cannot settle them (coordinates so large that the FP32 bounds overflow) the
+// binary64 recheck maps the NaN distance to overflow, so padding is never
+// counted (unit-vector catalogs are padded with zero vectors instead).
 __global__ void prep_fill_kernel(Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad, double v) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pad) return;
@@ -1449,6 +1555,62 @@ __global__ void prep_fill_kernel(Point64* out64, float4* out32, float4* out32x2,
     out32[p] = make_float4(f, f, f, 0.f);
     out32x2[2ull * p] = make_float4(f, f, f, f);
     out32x2[2ull * p + 1] = make_float4(f, f, 0.f, 0.f);
+}
+
+// Bounding sphere of each kCapPoints-point group of a prepared catalog (one
+// warp per group), for spatial pruning: centre c = the FP32-rounded mean of
+// the group's real points (padding left out: zero vectors of unit-vector
+// catalogs, non-finite points of 3-D catalogs), radius = max |p - c| over
+// them in binary64 from the binary64 points, enlarged by 2^-20 relative and
+// rounded up to FP32; all multiplied by the exact power of two `scale`.  A
+// group without real points gets radius -1e30: every block with it prunes
+// (it holds nothing to count).
+__global__ void prep_caps_kernel(const Point64* __restrict__ p64, uint32_t n_groups, int euclid, double scale,
+                                 float4* caps) {
+    const uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (grp >= n_groups) return;  // warp-uniform
+    constexpr int K = (int)kCapPoints / 32;
+    Point64 q[K];
+    bool real[K];
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        q[k] = p64[(size_t)grp * kCapPoints + (uint32_t)k * 32u + lane];
+        real[k] = euclid ? (isfinite(q[k].x) && isfinite(q[k].y) && isfinite(q[k].z))
+                         : (q[k].x != 0.0 || q[k].y != 0.0 || q[k].z != 0.0);
+        if (real[k]) {
+            sx += q[k].x * scale;
+            sy += q[k].y * scale;
+            sz += q[k].z * scale;
+            ++cnt;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (cnt == 0) {
+        if (lane == 0) caps[grp] = make_float4(0.f, 0.f, 0.f, -1e30f);
+        return;
+    }
+    const float cx = __double2float_rn(sx / cnt), cy = __double2float_rn(sy / cnt), cz = __double2float_rn(sz / cnt);
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (real[k]) {
+            const double dx = q[k].x * scale - (double)cx, dy = q[k].y * scale - (double)cy,
+                         dz = q[k].z * scale - (double)cz;
+            r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) caps[grp] = make_float4(cx, cy, cz, __double2float_ru(r * (1.0 + 0x1p-20)));
 }
 
 // ============================================================== launchers
@@ -1471,6 +1633,7 @@ static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t
     wd.off_lut = L.lut;
     wd.off_queue = L.queue;
     wd.off_prod = L.prod;
+    wd.off_icap = L.icap;
     wd.stage_bytes = wd.J * ((MODE == kModeScreen || MODE == kModeEuclid) ? 16u : 32u);
     // 16-bit counters: a lane adds at most R per j to one row plus at most 2 per
     // queue drain (at most one drain per slow j), so merging every
@@ -1545,7 +1708,7 @@ cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long l
 
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
                            const uint32_t* seg_delta, int sort, int euclid, unsigned long long* bbox,
-                           Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
+                           Point64* out64, float4* out32, float4* out32x2, float4* caps, uint32_t n_pad,
                            unsigned long long* keys, uint32_t* vals, uint32_t n_pow2,
                            unsigned long long* err_word, unsigned long long* eps_word, cudaStream_t stream,
                            uint32_t* launches) {
@@ -1594,6 +1757,13 @@ cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg
     if (n > 0) {
         prep_gather_kernel<<<(n + 255) / 256, 256, 0, stream>>>(xyz_in, n, do_sort ? vals : nullptr, seg_of_point,
                                                                seg_delta, out64, out32, out32x2);
+        ++nl;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (n_pad > 0 && caps) {
+        const uint32_t groups = n_pad / kCapPoints;  // n_pad is a multiple of kPad
+        prep_caps_kernel<<<(groups + 7) / 8, 256, 0, stream>>>(out64, groups, euclid,
+                                                               euclid ? kCapScale3d : 1.0, caps);
         ++nl;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

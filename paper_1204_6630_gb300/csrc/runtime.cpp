@@ -315,6 +315,45 @@ void derive_e_space(const std::vector<double>& C, float T, double g, std::vector
 // z >= zhi_k = RU(Z_k + g_k) proves Z >= Z_k (else z <= Z + delta(Z) <
 // Z_k + g_k), and z < zlo_k = RD(Z_k - g_k) proves Z < Z_k (Z - delta(Z) is
 // increasing for Z >= 1e-12; smaller Z_k get no lower bound).
+// LUT over a squared separation z >= 0 with cells of constant ratio: the cell
+// of z is clamp((bits(z) - b0) >> shift, 0, kLutCells - 1), b0 = bits of
+// RD(zmin), shift the smallest with every z up to ztop inside the cells.  Cell
+// c covers [cmin, cmax] (cell 0 also every smaller z, the last every larger)
+// and stores P = #{m : cmin >= zhi_m} (edges every z of the cell crosses) and
+// Q = #{m : cmax >= zlo_m} (edges some z may cross); P == Q settles the cell.
+void build_zlut(const std::vector<float>& zlo, const std::vector<float>& zhi, double zmin_d, double ztop_d,
+                int32_t* b0_out, int* shift_out, std::vector<uint32_t>& lut) {
+    const int ne = (int)zlo.size();
+    const float zmin = round_down_f32(zmin_d);
+    int32_t b0;
+    memcpy(&b0, &zmin, 4);
+    const float ztop = round_up_f32(ztop_d);
+    int32_t bt;
+    memcpy(&bt, &ztop, 4);
+    int shift = 0;
+    while (((int64_t)(bt - b0) >> shift) + 1 >= kLutCells - 1) ++shift;
+    lut.assign(kLutCells, 0);
+    for (int c = 0; c < kLutCells; ++c) {
+        const int64_t lo_bits = (int64_t)b0 + ((int64_t)c << shift);
+        const int64_t hi_bits = (int64_t)b0 + ((int64_t)(c + 1) << shift) - 1;
+        float cmin, cmax;
+        const int32_t lb = (int32_t)std::min<int64_t>(lo_bits, 0x7f7fffff);
+        const int32_t hb = (int32_t)std::min<int64_t>(hi_bits, 0x7f7fffff);
+        memcpy(&cmin, &lb, 4);
+        memcpy(&cmax, &hb, 4);
+        if (c == 0) cmin = 0.0f;                   // also every z below zmin
+        if (c == kLutCells - 1) cmax = INFINITY;   // and every z above
+        uint32_t P = 0, Q = 0;
+        for (int m = 0; m < ne; ++m) {
+            P += (cmin >= zhi[m]);
+            Q += (cmax >= zlo[m]);
+        }
+        lut[c] = P | (Q << 16);
+    }
+    *b0_out = b0;
+    *shift_out = shift;
+}
+
 void derive_chord_space(const std::vector<double>& C, std::vector<float>& zlo, std::vector<float>& zhi) {
     const int ne = (int)C.size();
     const double u = kUnit, eps = kChordEpsRef;
@@ -521,7 +560,10 @@ static int euclid_set(tpcf_ctx* ctx, tpcf_bins* b, int key, const tpcf::BinsDev*
                 zlo[k] = zhi[k] = INFINITY;
             } else {
                 const double gk = euclid_delta(S, M);
-                zhi[k] = round_up_f32(S + gk);
+                // past the FP32 range there is no upper bound: NaN makes z >= zhi
+                // false for every z (an overflowed z = +inf proves nothing; the
+                // pair goes to binary64)
+                zhi[k] = S + gk <= 3.4028234663852886e38 ? round_up_f32(S + gk) : NAN;
                 // z - delta(z) increases only once |a - b| is well above 2uM
                 zlo[k] = S < 1e6 * (u * M) * (u * M) ? -1.0f : round_down_f32(S - gk);
                 min_pos = std::min(min_pos, S);
@@ -532,32 +574,10 @@ static int euclid_set(tpcf_ctx* ctx, tpcf_bins* b, int key, const tpcf::BinsDev*
         const double zmax = std::pow(std::sqrt(SB * (1.0 + 1e-15)) + 2.001 * u * M, 2) * (1.0 + 2.01 * u);
         const float H = round_up_f32(zmax * (1.0 + 6.1 * u) + 1e-300);
         // LUT: cells of constant ratio from zmin = min S / 64 up past 2 H
-        const float zmin = round_down_f32(std::max(min_pos / 64.0, 1e-30));
         int32_t b0;
-        memcpy(&b0, &zmin, 4);
-        const float ztop = round_up_f32(2.0 * (double)H + 1e-30);
-        int32_t bt;
-        memcpy(&bt, &ztop, 4);
-        int shift = 0;
-        while (((int64_t)(bt - b0) >> shift) + 1 >= kLutCells - 1) ++shift;
-        std::vector<uint32_t> lut(kLutCells);
-        for (int c = 0; c < kLutCells; ++c) {
-            const int64_t lo_bits = (int64_t)b0 + ((int64_t)c << shift);
-            const int64_t hi_bits = (int64_t)b0 + ((int64_t)(c + 1) << shift) - 1;
-            float cmin, cmax;
-            const int32_t lb = (int32_t)std::min<int64_t>(lo_bits, 0x7f7fffff);
-            const int32_t hb = (int32_t)std::min<int64_t>(hi_bits, 0x7f7fffff);
-            memcpy(&cmin, &lb, 4);
-            memcpy(&cmax, &hb, 4);
-            if (c == 0) cmin = 0.0f;                       // also every z below zmin
-            if (c == kLutCells - 1) cmax = INFINITY;        // and every z above
-            uint32_t P = 0, Q = 0;
-            for (int m = 0; m < ne; ++m) {
-                P += (cmin >= zhi[m]);
-                Q += (cmax >= zlo[m]);
-            }
-            lut[c] = P | (Q << 16);
-        }
+        int shift;
+        std::vector<uint32_t> lut;
+        build_zlut(zlo, zhi, std::max(min_pos / 64.0, 1e-30), 2.0 * (double)H + 1e-30, &b0, &shift, lut);
         // one device buffer with the angular layout (lo/hi unused), then the descriptor
         const size_t nd = (size_t)ne * 8, nf = (size_t)ne * 4, nl = lut.size() * 4, nf16 = (nf + 15) / 16 * 16;
         const size_t off_lo = (nd + 15) / 16 * 16, off_hi = off_lo + nf16, off_c32 = off_hi + nf16,
@@ -712,7 +732,8 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
     };
     if (alloc((void**)&c->d64, (size_t)c->n_pad * sizeof(Point64)) != cudaSuccess ||
         alloc((void**)&c->d32, (size_t)c->n_pad * sizeof(float4)) != cudaSuccess ||
-        alloc((void**)&c->d32x2, (size_t)c->n_pad * 2 * sizeof(float4)) != cudaSuccess)
+        alloc((void**)&c->d32x2, (size_t)c->n_pad * 2 * sizeof(float4)) != cudaSuccess ||
+        alloc((void**)&c->caps, (size_t)(c->n_pad / kCapPoints) * sizeof(float4)) != cudaSuccess)
         return fail_with(TPCF_ENOMEM, "device allocation failed");
     const double* in = xyz;
     if (n > 0 && where == TPCF_HOST) {
@@ -754,7 +775,7 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
     }
     uint32_t nl = 0;
     cudaError_t e = launch_prepare(in, (uint32_t)n, seg, seg_delta, sort ? 1 : 0, euclid ? 1 : 0, err + 2, c->d64,
-                                   c->d32, c->d32x2, c->n_pad, keys, vals, n_pow2, err, err + 1, st, &nl);
+                                   c->d32, c->d32x2, c->caps, c->n_pad, keys, vals, n_pow2, err, err + 1, st, &nl);
     ctx->launches.fetch_add(nl);
     if (e != cudaSuccess) return fail_with(TPCF_ECUDA, cudaGetErrorString(e));
     unsigned long long hw[2] = {0, 0};
@@ -800,7 +821,7 @@ extern "C" int tpcf_catalog_create_3d(tpcf_ctx* ctx, const double* xyz, uint64_t
 int tpcf::catalog_destroy_impl(tpcf_catalog* c) {
     if (!c) return TPCF_EINVAL;
     cudaSetDevice(c->ctx->cfg.device);
-    void* bufs[4] = {c->d64, c->d32, c->d32x2, c->seg_of_block};
+    void* bufs[5] = {c->d64, c->d32, c->d32x2, c->seg_of_block, c->caps};
     if (c->stream_ordered) {
         for (void* p : bufs)
             if (p) cudaFreeAsync(p, c->free_stream);
@@ -916,6 +937,8 @@ uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const BinsDev
         sp.b32x2 = p.b->d32x2 + 2ull * p.b_off;
         sp.a64 = p.a->d64 + p.a_off;
         sp.b64 = p.b->d64 + p.b_off;
+        sp.a_caps = p.a->caps + p.a_off / kCapPoints;  // sub-ranges start on kSegAlign boundaries
+        sp.b_caps = p.b->caps + p.b_off / kCapPoints;
         sp.na = p.na;
         sp.nb = p.nb;
         sp.n_iblk = (p.na + I - 1) / I;
@@ -1103,6 +1126,28 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         for (int s2 = 0; s2 < nsub; ++s2)
             if (!(specs[s2].a->eps_max <= kChordEpsRef && specs[s2].b->eps_max <= kChordEpsRef)) wd.chord_ok = 0u;
         wd.wait_limit_ns = (uint64_t)ctx->cfg.wait_timeout_us * 1000ull;
+        // Spatial pruning (screen kernels): a block whose spheres are at least
+        // prune_thr apart (scaled space) holds only overflow pairs.  Angular: a
+        // pair of points with | |v|^2 - 1 | <= eps at distance delta has exact
+        // dot <= 1 + eps - delta^2 / 2, at most C_B - 1e-15 (so the binary64
+        // dot, within 3.4e-16 of it, is <= C_B: overflow) once delta >=
+        // sqrt(2 (1 + eps) - 2 (C_B - 1e-15)).  3-D: delta >= sqrt(S_B) (1 +
+        // 1e-12) makes the binary64 d^2 (relative error < 1e-15) >= S_B.
+        wd.prune = 0u;
+        wd.prune_thr = INFINITY;
+        if ((ctx->cfg.flags & TPCF_F_PRUNE) && (mode == kModeScreenScalar || mode == kModeEuclidScreen)) {
+            double thr;
+            if (bh->euclid) {
+                thr = std::sqrt(bh->cos_last) * (1.0 + 1e-12) * kCapScale3d;
+            } else {
+                double eps = 0.0;
+                for (int s2 = 0; s2 < nsub; ++s2) eps = std::max(eps, std::max(specs[s2].a->eps_max, specs[s2].b->eps_max));
+                thr = std::sqrt(std::max(0.0, 2.0 * (1.0 + eps) - 2.0 * (bh->cos_last - 1e-15)));
+            }
+            const float t32 = (float)thr;
+            wd.prune_thr = (double)t32 >= thr ? t32 : std::nextafter(t32, INFINITY);
+            wd.prune = std::isfinite(wd.prune_thr) ? 1u : 0u;
+        }
         return TPCF_OK;
     };
     auto launch = [&](const Shape& shp) -> cudaError_t {
@@ -1258,6 +1303,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
             float ms = 0.f;
             cudaEventElapsedTime(&ms, t0, t1);
             stats->kernel_ms = ms;
+            stats->pruned_pairs = hs[kStatPruned];
         }
         if (errw & kErrWaitTimeout) rc = ctx->fail(TPCF_ETIMEOUT, "a bounded device wait timed out");
         else if (errw) rc = ctx->fail(TPCF_ECUDA, "device error word 0x%llx", errw);
@@ -1551,6 +1597,7 @@ extern "C" int tpcf_graph_stats(tpcf_graph* g, tpcf_stats* st) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, g->t0, g->t1);
         st->kernel_ms = ms;
+        st->pruned_pairs = h[kStatPruned];
     }
     if (h[kStatError] & kErrWaitTimeout) return ctx->fail(TPCF_ETIMEOUT, "a bounded device wait timed out");
     if (h[kStatError]) return ctx->fail(TPCF_ECUDA, "device error word 0x%llx", h[kStatError]);

@@ -15,6 +15,12 @@ constexpr uint32_t kPad = 4096;
 // warp's i-points of the 512 x 8 counting shape), so that a warp's i-points
 // always belong to one segment.
 constexpr uint32_t kSegAlign = 256;
+// Bounding spheres for spatial pruning: one per kCapPoints consecutive
+// points of a catalog's device layout.
+constexpr uint32_t kCapPoints = 128;
+// 3-D catalogs store their spheres scaled by 2^-64 (exact), so that FP32
+// squares of separations up to 2e28 stay finite.
+constexpr double kCapScale3d = 5.421010862427522e-20;
 
 // Lookup table from the FP32 screen value to the candidate histogram index
 // range: cell k = rne(sat(e * lut_scale) * 2^14), k = 0 .. 2^14.
@@ -82,12 +88,16 @@ struct SubProblem {
     const uint32_t* row_seg;
     uint32_t row_stride;        // accumulator words between consecutive segments' histograms
     uint32_t no_self;           // 1: A == B counted over the full square except i == j
+    // Bounding spheres (x, y, z, radius) of A's and B's kCapPoints-point groups,
+    // starting at the sub-range's first point (spatial pruning).
+    const float4* a_caps;
+    const float4* b_caps;
 };
 
 constexpr int kMaxInlineSub = 3;
 
 // Device statistics words (per call, in the scratch slot after the histograms).
-enum StatWord { kStatPairs = 0, kStatBand = 1, kStatMismatch = 2, kStatError = 3,
+enum StatWord { kStatPairs = 0, kStatBand = 1, kStatMismatch = 2, kStatError = 3, kStatPruned = 4,
                 kStatWords = 8 };
 
 // Device error word bits.
@@ -117,9 +127,11 @@ struct WorkDesc {
     int32_t zbits0;                  // 3-D variant: LUT cell origin (bits of a float) and shift
     int zshift;
     double cos_last;                 // C_B (all-binary64 kernel)
+    uint32_t prune;                  // 1: skip (warp, 128-j chunk) blocks proven beyond the range
+    float prune_thr;                 // sphere-gap threshold of the pruning test (see prune_block)
     // ... and the shared-memory layout of the shape (set by the launcher).
     uint32_t off_bars, off_ctl, off_stage, off_hist, off_cthr, off_lo, off_hi, off_c32, off_zlo, off_zhi,
-        off_lut, off_queue, off_prod;
+        off_lut, off_queue, off_prod, off_icap;
     uint32_t stage_bytes;            // J * bytes per staged point
     uint32_t flush_limit;            // j-points between merges of the 16-bit counters
 };
@@ -151,7 +163,7 @@ cudaError_t launch_finalize_batch(const unsigned long long* acc, int acc_stride,
                                   int count, unsigned long long* err_word, cudaStream_t stream);
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
                            const uint32_t* seg_delta, int sort, int euclid, unsigned long long* bbox,
-                           Point64* out64, float4* out32, float4* out32x2, uint32_t n_pad,
+                           Point64* out64, float4* out32, float4* out32x2, float4* caps, uint32_t n_pad,
                            unsigned long long* key_scratch, uint32_t* val_scratch,
                            uint32_t n_pow2, unsigned long long* err_word, unsigned long long* eps_word,
                            cudaStream_t stream, uint32_t* launches);

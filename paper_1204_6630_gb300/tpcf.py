@@ -32,6 +32,7 @@ TPCF_LS_EXACT, TPCF_LS_PAPER = 0, 1
 TPCF_F_NO_SORT = 0x1
 TPCF_F_PACKED_FMA = 0x4
 TPCF_F_AUTOTUNE = 0x8
+TPCF_F_PRUNE = 0x10
 TPCF_F_TEST_WAIT_TIMEOUT = 0x100
 TPCF_MAX_EDGES = 321
 TPCF_GRAPH_AUTO, TPCF_GRAPH_CROSS, TPCF_GRAPH_ALL, TPCF_GRAPH_PATCHES = 0, 1, 2, 3
@@ -57,7 +58,8 @@ class tpcf_config(ctypes.Structure):
 class tpcf_stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_uint64), ("band_pairs", ctypes.c_uint64),
                 ("band_mismatch", ctypes.c_uint64), ("device_error", ctypes.c_uint32),
-                ("launches", ctypes.c_uint32), ("kernel_ms", ctypes.c_double)]
+                ("launches", ctypes.c_uint32), ("kernel_ms", ctypes.c_double),
+                ("pruned_pairs", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

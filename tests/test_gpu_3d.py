@@ -129,3 +129,18 @@ def test_mixing_angular_and_3d_is_refused(T):
             ctx.catalog3d(np.array([[1e29, 0.0, 0.0]]))
         with pytest.raises(T.TpcfError):
             ctx.bins3d(np.array([0.0, 1e19]))
+
+
+@pytest.mark.parametrize("precision", [SCREEN, PLAIN])
+def test_coordinates_near_the_limit(T, precision):
+    # coordinates near 1e27: the FP32 screen bounds overflow, so every pair takes
+    # the binary64 recheck, padding pairs (NaN apart) included
+    rng = np.random.default_rng(12)
+    d = rng.uniform(-1e27, 1e27, (1500, 3))
+    r = np.concatenate([d[:300] + rng.normal(0, 3e17, (300, 3)), rng.uniform(-1e27, 1e27, (900, 3))])
+    edges = np.array([0.0, 1e16, 1e17, 3e17, 1e18])
+    with T.Context(precision=precision) as ctx:
+        got, st = ctx.count_all(ctx.catalog3d(d), ctx.catalog3d(r), ctx.bins3d(edges), stats=True)
+    assert st["device_error"] == 0
+    for a, b in zip(got, o3(d, r, edges)):
+        np.testing.assert_array_equal(a, b)
