@@ -191,3 +191,30 @@ def test_3d_thresholds_are_the_smallest_squares_reaching_each_edge():
     assert s5 <= 25.0 and math.sqrt(s5) == 5.0  # doubles just below 25 already round up to 5
     with pytest.raises(tpcf.TpcfError):
         tpcf.tpcf_bins_thresholds_3d(np.array([1.0, 0.5]))
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets
+    (a C program compiled against include/tpcf.h prints them)."""
+    import subprocess
+    from paper_1204_6630_gb300 import tpcf as T
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = [T.tpcf_config, T.tpcf_stats, T.tpcf_job, T.tpcf_result]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tpcf.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(got[n]) == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(got[f"{n}.{f}"]) == getattr(st, f).offset, f"{n}.{f}"
