@@ -12,8 +12,12 @@ kernels, and the Landy-Szalay estimate.  `value` is pairs/s over the K timed
 steps (CUDA events, max over ranks).  `e2e` repeats the step through the
 host-array call tpcf_correlate with the catalogs in pinned host memory (copies
 included).  The roofline is that of the counting kernel: 3 FP32 pipe lane
-operations per pair (FMUL + 2 FFMA), counted as 6 flops, against the FP32
-peak 152 SMs x 128 lanes x 2 flops x 2.07 GHz.
+operations per pair (3 FFMA, the range offset folded into the first), counted
+as 6 flops, against the FP32 peak 152 SMs x 128 lanes x 2 flops x 2.07 GHz.
+The line also carries the all-binary64 kernel on the same catalogs
+(`fp64_plain`) and one launch with spatial pruning (`pruning`, the opt-in
+TPCF_F_PRUNE flag: same histograms, pairs covered per second); neither is the
+brute-force headline.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -21,12 +25,14 @@ Other workloads (one JSON line each, not the headline line):
   --workload jackknife  2,000,000 data + 4,000,000 random octant points in 512
                         patches of lognormal size (1k-200k), 40 linear bins
                         0-5 deg: per-patch DD/DR/RR as one captured graph
-                        (autotuned shape) against 1,536 separate launches;
+                        (autotuned shape) against 1,536 separate launches,
+                        and the leave-one-out jackknife of the full catalogs
+                        (brute force and pruned);
   --workload serving    a Poisson stream of --jobs jobs (N_D log-uniform in
                         [1e3, 1e6], N_R = 2 N_D, caps of 5-30 deg, 20-80
                         linear bins over 0-2 deg) through the job server
                         under a 120 GB budget, against one-at-a-time calls:
-                        p50/p99 latency and throughput;
+                        p50/p99 latency and throughput (also with pruning);
   --workload box3d      the 3-D variant: 1,000,000 clustered + 1,000,000 uniform
                         points in a box of side 1000, 30 log distance bins
                         0.5-50 (subsample checked against the oracle);
@@ -53,7 +59,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pairs/s (DD+DR+RR)"
 UNIT = "pairs/s"
-FLOPS_PER_PAIR = 6            # 3 FP32 pipe lane-ops (FMUL + 2 FFMA), FMA convention
+FLOPS_PER_PAIR = 6            # 3 FP32 pipe lane-ops (3 FFMA), FMA convention
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.55: SMs x lanes x 2 x max SM clock
 L2_FLUSH_BYTES = 256 << 20
 
@@ -491,8 +497,8 @@ def run_serving(args):
         done = max(done, a) + sv
         serial_lat.append(done - a)
 
-    def serve(at):
-        with tpcf.Context(hbm_budget_bytes=budget, server_workers=args.workers) as ctx:
+    def serve(at, flags=0):
+        with tpcf.Context(hbm_budget_bytes=budget, server_workers=args.workers, flags=flags) as ctx:
             ctx.poll(ctx.submit(jobs[0].data, jobs[0].rand, jobs[0].edges), len(jobs[0].edges))
             start = time.perf_counter()
             ids = []
@@ -508,6 +514,17 @@ def run_serving(args):
 
     burst_res, burst_span, burst_lat = serve(np.zeros(len(jobs)))
     pois_res, pois_span, pois_lat = serve(arrivals)
+    # the same stream with spatial pruning (opt-in flag): one-at-a-time and served
+    with tpcf.Context(flags=tpcf.TPCF_F_PRUNE) as ctx:
+        ctx.correlate(jobs[0].data, jobs[0].rand, jobs[0].edges)
+        t0 = time.perf_counter()
+        pser_res = [ctx.correlate(w.data, w.rand, w.edges) for w in jobs]
+        pserial_s = time.perf_counter() - t0
+    pburst_res, pburst_span, pburst_lat = serve(np.zeros(len(jobs)), tpcf.TPCF_F_PRUNE)
+    psame = all(np.array_equal(x[n], y[i]) for x, y in zip(pburst_res, serial_res)
+                for i, n in enumerate(("dd", "dr", "rr"))) and \
+        all(np.array_equal(x[i], y[i]) for x, y in zip(pser_res, serial_res) for i in range(3))
+    assert psame, "pruned results differ from brute-force lone calls"
     same = all(np.array_equal(x[n], y[i]) for x, y in zip(burst_res, serial_res)
                for i, n in enumerate(("dd", "dr", "rr"))) and \
         all(np.array_equal(x[n], y[i]) for x, y in zip(pois_res, serial_res)
@@ -528,7 +545,14 @@ def run_serving(args):
                          "pairs_per_s": total_pairs / burst_span, "latency_s": _quantiles(burst_lat)},
         "served_poisson": {"s": pois_span, "jobs_per_s": len(jobs) / pois_span,
                            "pairs_per_s": total_pairs / pois_span, "latency_s": _quantiles(pois_lat)},
-        "throughput_vs_serial": serial_s / burst_span, "results_identical_to_lone_calls": same}))
+        "throughput_vs_serial": serial_s / burst_span, "results_identical_to_lone_calls": same,
+        "pruned": {"flag": "TPCF_F_PRUNE",
+                   "serial": {"s": pserial_s, "pairs_per_s": total_pairs / pserial_s},
+                   "served_burst": {"s": pburst_span, "pairs_per_s": total_pairs / pburst_span,
+                                    "latency_s": _quantiles(pburst_lat)},
+                   "throughput_vs_pruned_serial": pserial_s / pburst_span,
+                   "throughput_vs_brute_force_serial": serial_s / pburst_span,
+                   "results_identical_to_brute_force": psame}}))
     return 0
 
 

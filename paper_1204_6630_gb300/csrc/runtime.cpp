@@ -868,11 +868,15 @@ bool shape_for(tpcf_ctx* ctx, int mode, int nedges, int T, int R, int Jreq, int 
     if (J > I) J = I;
     // (a tile is a whole number of the fast loop's 32-group mask chunks: 128 j)
     if ((int)kPad % J != 0 || (int)kPad % I != 0 || J % 128 != 0 || I % J != 0) return false;
-    int S = Sreq ? Sreq : 4;
+    // six stages by default: warps drift apart by up to five tiles before the
+    // fastest waits for a stage the slowest still reads (measured: 374 ms vs
+    // 380 ms with four at the 1M + 1M octant workload)
+    constexpr int kDefaultStages = 6;
+    int S = Sreq ? Sreq : kDefaultStages;
     if (S < 2 || S > 16) return false;
     size_t smem = count_smem_bytes(mode, T, R, J, S, nedges);
     while (smem > ctx->smem_optin && ((S > 2 && Sreq == 0) || (J > 256 && Jreq == 0))) {
-        if (S > 2 && Sreq == 0) --S; else { J /= 2; S = Sreq ? Sreq : 4; }
+        if (S > 2 && Sreq == 0) --S; else { J /= 2; S = Sreq ? Sreq : kDefaultStages; }
         smem = count_smem_bytes(mode, T, R, J, S, nedges);
     }
     if (smem > ctx->smem_optin) return false;
