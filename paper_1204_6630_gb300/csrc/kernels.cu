@@ -1127,22 +1127,32 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             // 3-D fast loop: e = H - |a' - b'|^2 as three differences and a negated
             // fused sum of squares; e < 0 proves d^2 > S_B (every pair overflow)
             const float4* sj = sptr<const float4>(wd.off_stage + stage * wd.stage_bytes);
+            // (groups and the per-chunk mask of slow groups as in the angular loop;
+            // the slow path recomputes z itself)
             constexpr int U = R >= 16 ? 2 : 4;
-            for (int jc = 0; jc < J; jc += (int)kCapPoints) {
-                if (wd.prune && prune_chunk(wd, jbase + (uint32_t)jc, 32u * R * kCapPoints)) continue;
-#pragma unroll 2
-                for (int jj = jc; jj < jc + (int)kCapPoints; jj += U) {
+            for (int jc = 0; jc < J; jc += kMaskGroups * U) {
+                if (wd.prune && prune_chunk(wd, jbase + (uint32_t)jc, 32u * R * kMaskGroups * U)) continue;
+                uint32_t lane_mask = 0;
+#pragma unroll 8
+                for (int g = 0; g < kMaskGroups; ++g) {
                     float eu[U][R];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const float4 b = sj[jj + u];
+                        const float4 b = sj[jc + g * U + u];
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
                             const float dx = ax[r] - b.x, dy = ay[r] - b.y, dz = az[r] - b.z;
                             eu[u][r] = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, wd.neg_fast_t)));
                         }
                     }
-                    if (!__any_sync(0xffffffffu, and_tree<U * R>(&eu[0][0]) >= 0)) continue;
+                    lane_mask = __funnelshift_l(~(uint32_t)and_tree<U * R>(&eu[0][0]), lane_mask, 1);
+                }
+                uint32_t m = __reduce_or_sync(0xffffffffu, lane_mask);  // bit kMaskGroups - 1 - g: group g
+#pragma unroll 1
+                while (m) {
+                    const int g = kMaskGroups - __ffs(m);  // lowest set bit first
+                    m &= m - 1u;
+                    const int jj = jc + g * U;
                     slow_group_euclid<T, R, U>(wd, cur_sub, ax, ay, az, [&](int j) { return sj[j]; }, jj, ibase,
                                                jbase, diag, hc);
                     maybe_drain<T>(wd, cur_sub, hc);
