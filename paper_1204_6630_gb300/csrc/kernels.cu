@@ -104,13 +104,6 @@ __device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, u
     }
 }
 
-// Ordered integer key of an FP32 value: key(a) < key(b) iff a < b (for
-// non-NaN a, b; -0 and +0 share key 0).
-__device__ __forceinline__ int32_t f32_key(float v) {
-    int32_t b = __float_as_int(v);
-    return b >= 0 ? b : -(b & 0x7fffffff);
-}
-
 // Packed FP32x2 helpers (sm_100+): two lanes of FP32 in one 64-bit register pair.
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
     unsigned long long r;
