@@ -183,3 +183,17 @@ def test_3d_huge_coordinates(T):
     got, _ = run(T, d, r, edges, True, euclid=True)
     for g, o in zip(got, oracle_all(d, r, edges, euclid=True)):
         np.testing.assert_array_equal(g, o)
+
+
+def test_server_jobs_with_pruning(T):
+    # jobs served by a pruning context == the oracle
+    specs = sorted(synth.serving_jobs(60, seed=3), key=lambda s: s["nd"])[:6]
+    jobs = [synth.materialise_job(s) for s in specs]
+    with T.Context(flags=T.TPCF_F_PRUNE, server_workers=3) as ctx:
+        ids = [ctx.submit(w.data, w.rand, w.edges) for w in jobs]
+        for jid, w in zip(ids, jobs):
+            res = ctx.poll(jid, len(w.edges))
+            dd, dr, rr = oracle_all(w.data, w.rand, w.edges)
+            np.testing.assert_array_equal(res["dd"], dd)
+            np.testing.assert_array_equal(res["dr"], dr)
+            np.testing.assert_array_equal(res["rr"], rr)
