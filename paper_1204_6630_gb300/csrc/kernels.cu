@@ -151,7 +151,7 @@ __device__ __forceinline__ int and_tree(const float* v) {
 // consumer (all threads) and the producer (thread 0, S tiles ahead) each
 // keep one.
 struct Cursor {
-    uint32_t q;       // walk position
+    uint32_t k;       // the block's item sequence number
     int sub;
     ItemGeom g;
     uint32_t t;       // current tile within the item
@@ -171,35 +171,88 @@ __device__ int find_sub(const WorkDesc& wd, uint64_t q) {
     return lo;
 }
 
-// Load the item at walk position c.q (and skip items without countable
-// tiles).  Within a sub-problem, position item_begin + k visits local item
-// (k * walk_mult) mod n_items (see walk_item).  Positions fit 32 bits (the
-// host checks the item count).
-__device__ void cursor_load(const WorkDesc& wd, Cursor& c) {
+// Items are handed out dynamically: block b starts with walk position
+// item_lo + b, and every later item of any block is the next position of a
+// per-launch counter (a statistics word, zeroed before each launch), so blocks
+// that draw cheap items simply take more of them.  Within a sub-problem,
+// position item_begin + k visits local item (k * walk_mult) mod n_items (see
+// walk_item).  Positions fit 32 bits (the host checks the item count).
+//
+// One producer cursor per block (shared memory) runs S tiles ahead: thread 0
+// advances it in the prologue, then the warp that releases a stage last (the
+// releases of successive stages are ordered, since every warp finishes tile
+// seq before tile seq + 1).  When it moves to a new item it draws a position,
+// skips items without countable tiles, and publishes the block's k-th item in
+// a ring before issuing any of its tiles; each warp's consumer cursor reads
+// the ring when it reaches the item.  The producer is at most S tiles (so S
+// items) ahead of the slowest consumer, so kItemRing > S + 1 slots suffice.
+constexpr int kItemRing = 32;
+constexpr uint32_t kItemEnd = 0xffffffffu;  // published position: no further item
+struct ItemSlot {
+    uint32_t q;    // walk position (kItemEnd: the block has no further item)
+    uint32_t seq;  // k + 1 once the block's k-th item is published
+};
+
+__device__ __forceinline__ uint32_t draw_item(const WorkDesc& wd) {
+    return (uint32_t)wd.item_lo + gridDim.x + (uint32_t)atomicAdd(wd.stats + kStatNextItem, 1ull);
+}
+
+__device__ bool load_item(const WorkDesc& wd, uint32_t q, Cursor& c) {
+    c.sub = find_sub(wd, q);
+    const SubProblem& sp = sub_of(wd, c.sub);
+    const uint64_t local = walk_item(q - sp.item_begin, sp.n_items, sp.walk_mult);
+    c.g = item_geom(local, sp.na, sp.nb, sp.n_iblk, sp.n_jchunk, sp.auto_mode != 0, wd.I, wd.Jc, wd.J);
+    c.t = c.g.t_first;
+    return c.t < c.g.t_end;
+}
+
+// Producer: from candidate position q, the first item with countable tiles
+// (drawing again past empty ones), published as the block's item c.k.
+__device__ void producer_load(const WorkDesc& wd, Cursor& c, uint32_t q) {
     const uint32_t q_end = (uint32_t)wd.item_hi;
-    while (c.q < q_end) {
-        c.sub = find_sub(wd, c.q);
-        const SubProblem& sp = sub_of(wd, c.sub);
-        const uint64_t local = walk_item(c.q - sp.item_begin, sp.n_items, sp.walk_mult);
-        c.g = item_geom(local, sp.na, sp.nb, sp.n_iblk, sp.n_jchunk, sp.auto_mode != 0, wd.I, wd.Jc,
-                        wd.J);
-        c.t = c.g.t_first;
-        if (c.t < c.g.t_end) { c.valid = true; return; }
-        c.q += gridDim.x;
-    }
-    c.valid = false;
+    while (q < q_end && !load_item(wd, q, c)) q = draw_item(wd);
+    c.valid = q < q_end;
+    volatile ItemSlot* slot = sptr<ItemSlot>(wd.off_items) + (c.k % kItemRing);
+    slot->q = c.valid ? q : kItemEnd;
+    __threadfence_block();
+    slot->seq = c.k + 1u;
 }
 
-__device__ void cursor_begin(const WorkDesc& wd, Cursor& c) {
-    c.q = (uint32_t)wd.item_lo + blockIdx.x;
-    cursor_load(wd, c);
+__device__ void producer_begin(const WorkDesc& wd, Cursor& c) {
+    c.k = 0;
+    producer_load(wd, c, (uint32_t)wd.item_lo + blockIdx.x);
 }
 
-__device__ void cursor_next(const WorkDesc& wd, Cursor& c) {
+__device__ void producer_next(const WorkDesc& wd, Cursor& c) {
     if (!c.valid) return;
     if (++c.t < c.g.t_end) return;
-    c.q += gridDim.x;
-    cursor_load(wd, c);
+    ++c.k;
+    producer_load(wd, c, draw_item(wd));
+}
+
+// Consumer: the block's item c.k from the ring (bounded wait for the producer
+// to publish it); false when the wait timed out.
+__device__ bool consumer_load(const WorkDesc& wd, Cursor& c) {
+    volatile ItemSlot* slot = sptr<ItemSlot>(wd.off_items) + (c.k % kItemRing);
+    if (slot->seq != c.k + 1u) {
+        const uint64_t t0 = global_ns();
+        while (slot->seq != c.k + 1u) {
+            if (global_ns() - t0 > wd.wait_limit_ns) return false;
+            __nanosleep(64);
+        }
+    }
+    __threadfence_block();
+    const uint32_t q = slot->q;
+    c.valid = q != kItemEnd;
+    if (c.valid) load_item(wd, q, c);
+    return true;
+}
+
+__device__ __forceinline__ bool consumer_next(const WorkDesc& wd, Cursor& c) {
+    if (!c.valid) return true;
+    if (++c.t < c.g.t_end) return true;
+    ++c.k;
+    return consumer_load(wd, c);
 }
 
 // ============================================================== shared-memory layout
@@ -214,7 +267,7 @@ constexpr int kMaxStages = 16;   // release counters live at kCtlRelease + stage
 constexpr int kQueuePerWarp = 64;   // band pairs per warp awaiting the binary64 recheck
 constexpr int kSlowPipe = 2;        // slow path: j-points whose LUT loads are in flight
 constexpr int kMaskGroups = 32;     // fast loop: groups per warp reduction of the slow-group mask
-constexpr uint32_t kCursorBytes = 32;  // one producer cursor slot
+constexpr uint32_t kCursorBytes = 32;  // the producer cursor
 constexpr uint32_t kPruneSlotBytes = 32;  // float4 i-sphere, B's sphere pointer, pruned pair slots (u64)
 
 struct SmemLayout {
@@ -226,7 +279,8 @@ struct SmemLayout {
     uint32_t lo, hi, cos32, zlo, zhi;  // nedges floats each
     uint32_t lut;       // kLutCells 16-bit entries (screen only)
     uint32_t queue;     // W * kQueuePerWarp unsettled pairs (i, j) (uint2, screen only)
-    uint32_t prod;      // W producer cursors (one per warp, used by its lane 0)
+    uint32_t prod;      // the block's producer cursor
+    uint32_t items;     // kItemRing published items (ItemSlot)
     uint32_t icap;      // W pruning slots: the warp's i-sphere, B's sphere array, pruned pair slots
     uint32_t total;
 };
@@ -255,7 +309,9 @@ __host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S,
     off = align_up(off, 16);
     L.queue = off; off += plain ? 0u : (uint32_t)(T / 32) * kQueuePerWarp * 8;
     off = align_up(off, 16);
-    L.prod = off; off += (uint32_t)(T / 32) * kCursorBytes;
+    L.prod = off; off += kCursorBytes;
+    off = align_up(off, 16);
+    L.items = off; off += (uint32_t)kItemRing * 8u;
     off = align_up(off, 16);
     L.icap = off; off += (uint32_t)(T / 32) * kPruneSlotBytes;
     L.total = off;
@@ -916,7 +972,9 @@ __device__ __forceinline__ bool prune_chunk(const WorkDesc& wd, uint32_t jg0, ui
 // seq % S == s; its full mbarrier completes when the TMA bulk copy lands.
 // Warps run independently (no block barrier in the main loop): after a warp
 // finishes a tile its lane 0 increments the stage's release counter, and the
-// warp that releases last issues the copy of tile seq + S into the stage.
+// warp that releases last issues the copy of tile seq + S into the stage
+// (advancing the block's producer cursor; items are drawn dynamically, see
+// producer_load).
 // Every wait is bounded; a timeout sets the abort word, after which no copy is
 // issued, warps leave the loop, and thread 0 waits (bounded) for the copies
 // still in flight before the block exits.
@@ -931,8 +989,15 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     uint64_t* bars = sptr<uint64_t>(wd.off_bars);
     volatile int* ctl = sptr<volatile int>(wd.off_ctl);
 
+    // ---- the block's first item (published by thread 0, read by every thread)
+    Cursor* prod = sptr<Cursor>(wd.off_prod);
+    for (int k = tid; k < kItemRing; k += T) sptr<ItemSlot>(wd.off_items)[k].seq = 0u;
+    __syncthreads();
+    if (tid == 0) producer_begin(wd, *prod);
+    __syncthreads();
     Cursor cons;
-    cursor_begin(wd, cons);
+    cons.k = 0;
+    consumer_load(wd, cons);  // published before the barrier: no wait
     if (!cons.valid) return;  // block-uniform
 
     // ---- set up: barriers, control words, histogram, bins (all sub-problems share them)
@@ -962,18 +1027,15 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         bulk_copy_g2s(dst, src, wd.stage_bytes, &bars[seq % S]);
     };
 
-    // ---- prologue: thread 0 issues the first S tiles; lane 0 of every warp
-    // keeps a producer cursor S tiles ahead (in shared memory) for its refill
-    // turns.
-    if (lane == 0) {
-        Cursor pc = cons;
+    // ---- prologue: thread 0 issues the first S tiles; the producer cursor then
+    // points at tile S (refills: the last releaser of each stage)
+    if (tid == 0) {
         uint32_t k = 0;
-        for (; k < S && pc.valid; ++k) {
-            if (tid == 0) issue(k, pc);
-            cursor_next(wd, pc);
+        for (; k < S && prod->valid; ++k) {
+            issue(k, *prod);
+            producer_next(wd, *prod);
         }
-        *sptr<Cursor>(wd.off_prod + (uint32_t)warp * kCursorBytes) = pc;
-        if (tid == 0) ctl[kCtlIssued] = (int)k;
+        ctl[kCtlIssued] = (int)k;
     }
     __syncwarp();
 
@@ -1232,7 +1294,6 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         // ---- release the stage; the last warp to release refills it with tile seq + S
         __syncwarp();
         if (lane == 0) {
-            Cursor* prod = sptr<Cursor>(wd.off_prod + (uint32_t)warp * kCursorBytes);
             __threadfence_block();
             const int old = atomicAdd((int*)&ctl[kCtlRelease + stage], 1);
             if (old == W - 1) {
@@ -1242,12 +1303,20 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                     fence_proxy_async_smem();
                     issue(seq + S, *prod);
                     atomicAdd((int*)&ctl[kCtlIssued], 1);
+                    producer_next(wd, *prod);
                 }
+                __threadfence_block();
             }
-            cursor_next(wd, *prod);
         }
         ++seq;
-        cursor_next(wd, cons);
+        if (!consumer_next(wd, cons)) {  // the producer never published the next item
+            if (lane == 0) {
+                ctl[kCtlAbort] = 1;
+                atomicOr(wd.stats + kStatError, (unsigned long long)kErrWaitTimeout);
+            }
+            aborted = true;
+            break;
+        }
     }
 
     // ---- merge this warp's columns (skipped after an abort: outputs are invalid)
@@ -1636,6 +1705,7 @@ static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t
     wd.off_lut = L.lut;
     wd.off_queue = L.queue;
     wd.off_prod = L.prod;
+    wd.off_items = L.items;
     wd.off_icap = L.icap;
     wd.stage_bytes = wd.J * ((MODE == kModeScreen || MODE == kModeEuclid) ? 16u : 32u);
     // 16-bit counters: a lane adds at most R per j to one row plus at most 2 per

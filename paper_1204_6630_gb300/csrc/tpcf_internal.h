@@ -98,6 +98,7 @@ constexpr int kMaxInlineSub = 3;
 
 // Device statistics words (per call, in the scratch slot after the histograms).
 enum StatWord { kStatPairs = 0, kStatBand = 1, kStatMismatch = 2, kStatError = 3, kStatPruned = 4,
+                kStatNextItem = 5,  // counting kernel: items drawn from the launch's dynamic pool
                 kStatWords = 8 };
 
 // Device error word bits.
@@ -131,7 +132,7 @@ struct WorkDesc {
     float prune_thr;                 // sphere-gap threshold of the pruning test (see prune_block)
     // ... and the shared-memory layout of the shape (set by the launcher).
     uint32_t off_bars, off_ctl, off_stage, off_hist, off_cthr, off_lo, off_hi, off_c32, off_zlo, off_zhi,
-        off_lut, off_queue, off_prod, off_icap;
+        off_lut, off_queue, off_prod, off_icap, off_items;
     uint32_t stage_bytes;            // J * bytes per staged point
     uint32_t flush_limit;            // j-points between merges of the 16-bit counters
 };
