@@ -147,9 +147,10 @@ __device__ __forceinline__ int and_tree(const float* v) {
 }
 
 // ============================================================== work cursor
-// Enumerates (item, tile) pairs of one block in processing order.  The
-// consumer (all threads) and the producer (thread 0, S tiles ahead) each
-// keep one.
+// Enumerates (item, tile) pairs of one block in processing order.  Every
+// thread keeps a consumer cursor (registers); the block's one producer cursor
+// (shared memory, S tiles ahead) is advanced by thread 0 in the prologue and
+// then by the last releaser of each stage.
 struct Cursor {
     uint32_t k;       // the block's item sequence number
     int sub;
