@@ -560,59 +560,73 @@ class Context:
         self._owned: list[tuple[str, int]] = []
 
     def catalog(self, xyz, stream=None, offsets=None) -> "Catalog":
+        """tpcf_catalog_create[_segmented]: (n, 3) float64 unit vectors, host array or CUDA tensor;
+        offsets (P + 1 ascending, from 0 to n) make a segmented catalog for patches and the jackknife."""
         h = tpcf_catalog_create(self.handle, xyz, stream, offsets)
         c = Catalog(self, h, tpcf_catalog_size(h), 0 if offsets is None else len(offsets) - 1)
         self._owned.append(("cat", h))
         return c
 
     def catalog3d(self, xyz, stream=None, offsets=None) -> "Catalog":
+        """tpcf_catalog_create_3d: (n, 3) float64 points of the 3-D variant (finite, |x| <= 1e28)."""
         h = tpcf_catalog_create_3d(self.handle, xyz, stream, offsets)
         c = Catalog(self, h, tpcf_catalog_size(h), 0 if offsets is None else len(offsets) - 1)
         self._owned.append(("cat", h))
         return c
 
     def bins3d(self, edges) -> "Bins":
+        """tpcf_bins_create_3d: distance edges (B + 1 increasing, finite, the last in (0, 1e18])."""
         h = tpcf_bins_create_3d(self.handle, edges)
         self._owned.append(("bins", h))
         return Bins(self, h, len(edges))
 
     def bins(self, edges_rad) -> "Bins":
+        """tpcf_bins_create: angular edges in radians (B + 1 strictly increasing, in [0, pi])."""
         h = tpcf_bins_create(self.handle, edges_rad)
         self._owned.append(("bins", h))
         return Bins(self, h, len(edges_rad))
 
     def count_auto(self, cat: "Catalog", bins: "Bins", stream=None, out=None, device_out=False, stats=False):
+        """tpcf_count_auto: DD or RR over pairs i < j; B + 2 uint64 [underflow, bins, overflow]."""
         return tpcf_count_auto(self.handle, cat.handle, bins.handle, bins.nedges, stream, out, device_out, stats)
 
     def count_cross(self, d: "Catalog", r: "Catalog", bins: "Bins", stream=None, out=None, device_out=False,
                     stats=False):
+        """tpcf_count_cross: DR over all ordered pairs (i in d, j in r)."""
         return tpcf_count_cross(self.handle, d.handle, r.handle, bins.handle, bins.nedges, stream, out,
                                 device_out, stats)
 
     def count_all(self, d: "Catalog", r: "Catalog", bins: "Bins", stream=None, outs=None, device_out=False,
                   stats=False):
+        """tpcf_count_all: (DD, DR, RR) in one fused launch."""
         return tpcf_count_all(self.handle, d.handle, r.handle, bins.handle, bins.nedges, stream, outs,
                               device_out, stats)
 
     def count_patches(self, d: "Catalog", r: "Catalog", bins: "Bins", stream=None, out=None, device_out=False,
                       stats=False):
+        """tpcf_count_patches: (P, 3, B + 2) per-patch DD, DR, RR of two segmented catalogs, one launch."""
         return tpcf_count_patches(self.handle, d.handle, r.handle, bins.handle, bins.nedges, d.npatch, stream, out,
                                   device_out, stats)
 
     def jackknife(self, d: "Catalog", r: "Catalog", bins: "Bins", stream=None, estimator=TPCF_LS_EXACT, stats=False):
+        """tpcf_jackknife: leave-one-out histograms (P, 3, B + 2), w (P, B) and its covariance (B, B)."""
         return tpcf_jackknife(self.handle, d.handle, r.handle, bins.handle, bins.nedges, d.npatch, stream, estimator,
                               stats)
 
     def correlate(self, d_xyz, r_xyz, edges_rad, estimator=TPCF_LS_EXACT, stream=None, stats=False):
+        """tpcf_correlate: host arrays in, (DD, DR, RR, w) out."""
         return tpcf_correlate(self.handle, d_xyz, r_xyz, edges_rad, estimator, stream, stats)
 
     def submit(self, d_xyz, r_xyz, edges_rad, estimator=TPCF_LS_EXACT) -> int:
+        """tpcf_submit: queue a correlation job on the context's job server; returns its id."""
         return tpcf_submit(self.handle, d_xyz, r_xyz, edges_rad, estimator)
 
     def poll(self, job_id: int, nedges: int, timeout_ms: int = -1, raise_on_error: bool = True):
+        """tpcf_poll: wait up to timeout_ms (0: do not wait, < 0: no limit) for a job; its histograms, w, timings."""
         return tpcf_poll(self.handle, job_id, nedges, timeout_ms, raise_on_error)
 
     def cancel(self, job_id: int) -> None:
+        """tpcf_cancel: cancel a queued job."""
         tpcf_cancel(self.handle, job_id)
 
     def graph(self, kind: int, d: "Catalog", r: "Catalog | None", bins: "Bins", out_dev=None) -> "Graph":
@@ -631,12 +645,14 @@ class Context:
     _DESTROY = {"cat": "tpcf_catalog_destroy", "bins": "tpcf_bins_destroy", "graph": "tpcf_graph_destroy"}
 
     def free(self, obj) -> None:
+        """Destroy a catalog, bins or graph made by this context before the context closes."""
         kind = "cat" if isinstance(obj, Catalog) else ("graph" if isinstance(obj, Graph) else "bins")
         if (kind, obj.handle) in self._owned:
             self._owned.remove((kind, obj.handle))
             globals()[self._DESTROY[kind]](obj.handle)
 
     def close(self) -> None:
+        """Destroy everything this context made, then the context."""
         if self.handle:
             for kind, h in reversed(self._owned):
                 globals()[self._DESTROY[kind]](h)
