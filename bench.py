@@ -130,15 +130,39 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(w, n_sample: int, threads: int):
-    """Time the oracle on the first n_sample points of D and R (DD + DR + RR)."""
+def oracle_sample(w, n_sample: int, threads: int, hists: bool = False):
+    """Time the oracle on the first n_sample points of D and R (DD + DR + RR);
+    with ``hists`` also return its (DD, DR, RR) histograms."""
     import oracle
     d, r = w.data[:n_sample], w.rand[:n_sample]
     t0 = time.perf_counter()
-    oracle.correlation(d, r, w.edges, threads=threads)
+    dd, dr, rr, _ = oracle.correlation(d, r, w.edges, threads=threads)
     dt = time.perf_counter() - t0
     pairs = n_sample * (n_sample - 1) + n_sample * n_sample
+    if hists:
+        return pairs / dt, dt, pairs, (dd, dr, rr)
     return pairs / dt, dt, pairs
+
+
+def near_edge_count(d, r, edges, threads: int, tol: float = 1e-12) -> int:
+    """Oracle pairs (DD, RR, DR of the sample) whose angle is within tol of an edge:
+    the only pairs whose bin may depend on the arc-cosine that decides it."""
+    import oracle
+    return sum(oracle.near_edge_pairs(a, b, edges, auto, tol=tol, threads=threads)[0]
+               for auto, a, b in ((True, d, None), (True, r, None), (False, d, r)))
+
+
+def roofline_peaks(local: int, clocks: dict):
+    """Derived FP32 peak (device SM count x 128 lanes x 2 flops x the maximum SM
+    clock nvidia-smi reports), the same at the median clock sampled under load,
+    and the measured FMA-chain throughput (scalar and packed)."""
+    import torch
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    med_mhz = clocks.get("sm_mhz") or max_mhz
+    derived = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    at_clock = sms * 128 * 2 * med_mhz * 1e6 / 1e12
+    return sms, max_mhz, med_mhz, derived, at_clock
 
 
 def run_reference(args):
@@ -312,12 +336,36 @@ def run_gpu(args):
                  "histograms_identical": all(np.array_equal(a, c) for a, c in zip((qdd, qdr, qrr), (dd, dr, rr)))}
         assert prune["histograms_identical"], "pruned and brute-force histograms disagree"
 
+    # measured FP32 FMA throughput (the roofline's measured denominator), GPU otherwise idle
+    peak_meas = None
+    if rank == 0:
+        pk_s = tpcf.tpcf_fp32_peak(local, packed=False)
+        pk_p = tpcf.tpcf_fp32_peak(local, packed=True)
+        peak_meas = {"value": max(pk_s, pk_p), "fma_f32": pk_s, "fma_f32x2": pk_p,
+                     "source": "tpcf_fp32_peak: 16 independent FMA chains per thread, 4 x 512 threads per SM, "
+                               "best of 5 launches (CUDA events)"}
+
     cpu = None
+    sub_parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        v, dt, sp = oracle_sample(w, args.cpu_sample, cores)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {args.cpu_sample:,} points of D and of R, DD+DR+RR = {sp:,} pairs, {dt:.1f} s"}
+        # single-threaded oracle (the baseline), then the same oracle on every host core
+        v1, dt1, sp1 = oracle_sample(w, args.cpu_sample_1t, 1)
+        v, dt, sp, ohist = oracle_sample(w, args.cpu_sample, cores, hists=True)
+        cpu = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {args.cpu_sample_1t:,} points of D and of R, DD+DR+RR = {sp1:,} pairs, "
+                         f"{dt1:.1f} s on one host thread",
+               "multi_thread": {"value": v, "unit": UNIT, "threads": cores,
+                                "sample": f"first {args.cpu_sample:,} points of D and of R, DD+DR+RR = "
+                                          f"{sp:,} pairs, {dt:.1f} s"}}
+        # the GPU path on the same sample, compared with the oracle's histograms
+        cs_d, cs_r = ctx.catalog(w.data[:args.cpu_sample]), ctx.catalog(w.rand[:args.cpu_sample])
+        gs = ctx.count_all(cs_d, cs_r, ctx.bins(w.edges))
+        sub_parity = {"points_per_catalog": args.cpu_sample,
+                      "identical_to_oracle": all(np.array_equal(a, b) for a, b in zip(gs, ohist)),
+                      "near_edge_pairs": near_edge_count(w.data[:args.cpu_sample], w.rand[:args.cpu_sample],
+                                                         w.edges, cores),
+                      "near_edge_tol_rad": 1e-12}
 
     kern_s = statistics.mean(kernel_ms) / 1e3
     achieved = st["pairs"] * FLOPS_PER_PAIR / kern_s / 1e12   # this rank's launch
@@ -337,24 +385,32 @@ def run_gpu(args):
     cfg = workload_config(args.n, nbins)
     cfg["pairs_per_step"] = pairs
     cfg["parallelism"] = f"shards{world}" if world > 1 else "single"
+    csum = clocks.summary()
+    sms, max_mhz, med_mhz, peak_derived, peak_clock = roofline_peaks(local, csum)
+    if peak_meas:
+        peak_meas["frac"] = achieved / peak_meas["value"]
     line = {
         "metric": METRIC, "value": pairs * args.steps / (elapsed_ms / 1e3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f32", "precision": "FP32 screen + binary64 guard-band recheck, uint64 counts",
         "data": "synthetic", "config": cfg,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "count_kernel<512,8,screen> (fused DD/DR/RR)",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_derived, "unit": "TFLOP/s",
+                     "frac": achieved / peak_derived, "traffic": traffic,
+                     "kernel": "count_kernel (screen, fused DD/DR/RR)",
                      "kernel_ms": statistics.mean(kernel_ms),
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no FP32 entry in "
-                                    "MEASURED_PEAKS.json)"},
+                     "peak_source": f"derived: {sms} SMs (device) x 128 FP32 lanes x 2 flops x {max_mhz:.0f} MHz "
+                                    "(maximum SM clock, nvidia-smi); MEASURED_PEAKS.json has no FP32 entry",
+                     "peak_at_sampled_clock": {"value": peak_clock, "sm_mhz": med_mhz,
+                                               "frac": achieved / peak_clock},
+                     "peak_measured": peak_meas},
         "band": {"pairs": st["band_pairs"], "fraction": st["band_pairs"] / max(1, st["pairs"]),
                  "fp32_mismatch": st["band_mismatch"]},
         "fp64_plain": fp64,
         "pruning": prune,
+        "subsample_parity": sub_parity,
         "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches,
-        "clocks": clocks.summary(),
+        "clocks": csum,
     }
     ctx.close()
     if rank == 0:
@@ -702,7 +758,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000, help="points per catalog")
-    ap.add_argument("--cpu-sample", type=int, default=40_000, help="points per catalog for the oracle timing")
+    ap.add_argument("--cpu-sample", type=int, default=40_000,
+                    help="points per catalog for the multi-threaded oracle timing and the subsample parity check")
+    ap.add_argument("--cpu-sample-1t", type=int, default=10_000,
+                    help="points per catalog for the single-threaded oracle timing (the cpu_baseline value)")
     ap.add_argument("--ref-sample", type=int, default=16_000, help="points per catalog per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-binary64 kernel comparison")

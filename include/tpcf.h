@@ -156,6 +156,17 @@ int tpcf_version(void);
 /* Number of this library's kernels launched through ctx so far (telemetry). */
 uint64_t tpcf_kernel_launches(const tpcf_ctx *ctx);
 
+/* ------------------------------------------------------------------ measurement
+ * tpcf_fp32_peak: the measured FP32 fused multiply-add throughput of `device`
+ * in TFLOP/s (2 flops per FMA), the denominator of the counting kernel's
+ * roofline.  16 independent FMA chains per thread, 4 blocks of 512 threads per
+ * SM, best of 5 timed launches (CUDA events) after a warm-up launch; packed = 0
+ * issues fma.rn.f32, packed = 1 fma.rn.f32x2 (two FMAs per instruction).
+ * Synchronous (about 0.1 s); allocates nothing; changes no device setting.
+ * Not in the paper (it puts the pair rate in proportion to the hardware).
+ * Errors: TPCF_EINVAL (NULL tflops, packed not 0 or 1), TPCF_ECUDA. */
+int tpcf_fp32_peak(int device, int packed, double *tflops);
+
 /* ------------------------------------------------------------------ context */
 /* Creates a context on cfg->device (NULL cfg = defaults).  Allocates the
  * per-call device scratch slots.  *out is NULL on failure. */
@@ -411,7 +422,12 @@ int tpcf_cancel(tpcf_ctx *ctx, uint64_t job_id);
  *   edges_rad: host array of nedges edges (as in tpcf_bins_create);
  *   hist_dev: device array of nedges + 1 uint64, written in `stream` order.
  * Every pair is computed in binary64 (the all-FP64 kernel), one launch plus a
- * finalize launch, asynchronous in `stream`.
+ * finalize launch, asynchronous in `stream`.  Each block keeps 32-bit counters
+ * in shared memory and merges them into the 64-bit accumulators at least once
+ * per 2^30 pairs, so no count wraps at any n up to TPCF_MAX_POINTS.  The
+ * device cannot report an error through the return value without a
+ * synchronization: should the bins ever sum to more than n (n - 1) / 2, the
+ * overflow entry hist_dev[nedges] is set to UINT64_MAX instead.
  * Scratch: the uint64 accumulators live in a fixed 4 KB __device__ array of
  * the library, held by every GPU that loads the library until the process
  * exits.  Limit: nedges <= TPCF_MAX_EDGES (321); larger values return
@@ -439,11 +455,16 @@ int tpcf_count_auto_noalloc(const double *xyz_dev, uint64_t n, const double *edg
  * per-item pair counts the kernel reports.
  *
  * tpcf_debug_fail_alloc_after: the n-th following device allocation made by
- * the library fails with TPCF_ENOMEM (n = -1 switches this off). */
+ * the library fails with TPCF_ENOMEM (n = -1 switches this off).
+ *
+ * tpcf_debug_noalloc_grid: caps the number of blocks of the counting launch of
+ * tpcf_count_auto_noalloc (0 = the default, 8 per SM), so that a test can make
+ * one block count more than 2^32 pairs. */
 int64_t tpcf_plan_coverage(uint32_t na, uint32_t nb, int auto_mode, uint32_t I, uint32_t Jc,
                            uint32_t J, uint32_t shard_index, uint32_t shard_count, uint32_t *counts,
                            uint64_t *pairs);
 void tpcf_debug_fail_alloc_after(int n);
+void tpcf_debug_noalloc_grid(int blocks);
 
 #ifdef __cplusplus
 }

@@ -53,8 +53,10 @@ def _bind(lib):
     lib.oracle_estimate.argtypes = [u64p, u64p, u64p, ctypes.c_int, u64, u64, ctypes.c_int, dp]
     lib.oracle_count_auto3_rows.argtypes = [dp, u64, dp, ctypes.c_int, u64, u64, u64p]
     lib.oracle_count_cross3_rows.argtypes = [dp, u64, dp, u64, dp, ctypes.c_int, u64, u64, u64p]
+    lib.oracle_near_edge_rows.argtypes = [dp, u64, dp, u64, ctypes.c_int, dp, ctypes.c_int, ctypes.c_double,
+                                          u64, u64, u64, u64p, dp, u64p]
     for f in (lib.oracle_count_auto_rows, lib.oracle_count_cross_rows, lib.oracle_estimate,
-              lib.oracle_count_auto3_rows, lib.oracle_count_cross3_rows):
+              lib.oracle_count_auto3_rows, lib.oracle_count_cross3_rows, lib.oracle_near_edge_rows):
         f.restype = ctypes.c_int
     return lib
 
@@ -145,6 +147,42 @@ def count_cross(xyz_d, xyz_r, edges, threads: int = 1, lib=None, euclid: bool = 
         return run(ranges[0])
     with ThreadPoolExecutor(len(ranges)) as ex:
         return np.sum(list(ex.map(run, ranges)), axis=0, dtype=np.uint64)
+
+
+def near_edge_pairs(a, b, edges, auto: bool, tol: float = 1e-12, threads: int = 1, max_out: int = 1000,
+                    lib=None):
+    """Pairs whose angle lies within ``tol`` radians of a bin edge.
+
+    ``auto``: unordered pairs i < j of catalog ``a`` (``b`` ignored); else every
+    pair (i in a, j in b).  These are the pairs a different (correctly behaved)
+    arc-cosine could put in a neighbouring bin.  Returns ``(count, pairs)`` with
+    ``pairs`` a list of up to ``max_out`` ``(i, j, theta - t_m)`` tuples.
+    """
+    lib = lib or load()
+    a = _as_xyz(a)
+    b = a if auto else _as_xyz(b)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    na, nb = a.shape[0], b.shape[0]
+
+    def run(rg):
+        ij = np.zeros(2 * max(1, max_out), dtype=np.uint64)
+        gap = np.zeros(max(1, max_out), dtype=np.float64)
+        c = np.zeros(1, dtype=np.uint64)
+        rc = lib.oracle_near_edge_rows(_dptr(a), na, _dptr(b), nb, 1 if auto else 0, _dptr(e), len(e), float(tol),
+                                       rg[0], rg[1], max_out, _uptr(ij), _dptr(gap), _uptr(c))
+        if rc != 0:
+            raise ValueError("oracle_near_edge_rows: invalid arguments")
+        k = int(min(int(c[0]), max_out))
+        return int(c[0]), [(int(ij[2 * q]), int(ij[2 * q + 1]), float(gap[q])) for q in range(k)]
+
+    weights = (na - 1 - np.arange(na, dtype=np.float64)) if auto else np.ones(na)
+    ranges = _row_splits(na, weights, threads)
+    if len(ranges) == 1:
+        return run(ranges[0])
+    with ThreadPoolExecutor(len(ranges)) as ex:
+        parts = list(ex.map(run, ranges))
+    pairs = [p for _, ps in parts for p in ps][:max_out]
+    return sum(c for c, _ in parts), pairs
 
 
 def estimate(dd, dr, rr, nd: int, nr: int, estimator: int = LS_EXACT, lib=None) -> np.ndarray:

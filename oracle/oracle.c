@@ -122,6 +122,47 @@ int oracle_count_cross(const double *xyz_d, uint64_t nd, const double *xyz_r, ui
     return oracle_count_cross_rows(xyz_d, nd, xyz_r, nr, edges, nedges, 0, nd, hist);
 }
 
+/* Pairs near an edge.  The only pairs whose bin may legitimately depend on
+ * which correctly-behaved arc-cosine is used (the host's, another libm's, the
+ * exact one) are those whose angle lies within a tiny distance of an edge.
+ * This enumerates them for rows [row_begin, row_end) of A against B (auto:
+ * pairs i < j of one catalog, B = A; cross: all pairs): a pair counts when
+ * |theta - t_m| < tol for the edge just below or just above its angle
+ * (t_{h-1} <= theta < t_h with h the pair's histogram index, so no other edge
+ * is nearer).  *count receives the number of such pairs; the first max_out of
+ * them go to out_ij (i, j) and out_gap (theta - t_m). */
+int oracle_near_edge_rows(const double *xyz_a, uint64_t na, const double *xyz_b, uint64_t nb, int auto_mode,
+                          const double *edges, int nedges, double tol, uint64_t row_begin, uint64_t row_end,
+                          uint64_t max_out, uint64_t *out_ij, double *out_gap, uint64_t *count)
+{
+    if (!edges_ok(edges, nedges) || row_begin > row_end || row_end > na || !(tol >= 0.0) || !count)
+        return ORACLE_EINVAL;
+    if (auto_mode && (xyz_a != xyz_b || na != nb))
+        return ORACLE_EINVAL;
+    uint64_t c = 0;
+    for (uint64_t i = row_begin; i < row_end; ++i) {
+        for (uint64_t j = auto_mode ? i + 1 : 0; j < nb; ++j) {
+            const double theta = pair_angle(xyz_a + 3 * i, xyz_b + 3 * j);
+            const int h = bin_of_angle(theta, edges, nedges);
+            double gap = 1.0 / 0.0;
+            if (h > 0 && fabs(theta - edges[h - 1]) < tol)
+                gap = theta - edges[h - 1];
+            else if (h < nedges && fabs(theta - edges[h]) < tol)
+                gap = theta - edges[h];
+            if (gap == 1.0 / 0.0)
+                continue;
+            if (c < max_out) {
+                out_ij[2 * c] = i;
+                out_ij[2 * c + 1] = j;
+                out_gap[c] = gap;
+            }
+            ++c;
+        }
+    }
+    *count = c;
+    return ORACLE_OK;
+}
+
 /* ---------------------------------------------------------------- 3-D variant
  * Section 1 defines the two-point function for a spatial separation r as well
  * as for an angle, and notes that the angular results extend to the

@@ -1070,13 +1070,6 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                 cur_sub = cons.sub;
                 cur_hist = tgt;
             }
-            const uint32_t item_j = (cons.g.t_end - cons.g.t_first) * wd.J;
-            if (j_since_flush + item_j > wd.flush_limit) {
-                if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
-                warp_flush_hist<T>(hc, wd.ne, cur_hist);
-                j_since_flush = 0;
-            }
-            j_since_flush += item_j;
             if (tid == 0)
                 atomicAdd(wd.stats + kStatPairs,
                           (unsigned long long)item_pairs(cons.g, sp.na, sp.nb, sp.auto_mode != 0, wd.I, wd.Jc));
@@ -1118,6 +1111,15 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                 }
             }
         }
+
+        // ---- merge the 16-bit counters before any can wrap (checked per tile: one
+        // item may hold more j-points than the merge interval)
+        if (j_since_flush + wd.J > wd.flush_limit) {
+            if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
+            warp_flush_hist<T>(hc, wd.ne, cur_hist);
+            j_since_flush = 0;
+        }
+        j_since_flush += wd.J;
 
         // ---- wait for this tile
         const uint32_t stage = seq % S;
@@ -1353,7 +1355,8 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
 
 // ============================================================== finalize
 // out[h] = acc[h] for h < nedges (underflow and bins); out[nedges] = overflow
-// = total - sum.  acc and out may alias.
+// = total - sum, or UINT64_MAX (and kErrBadHist in the error word) when the
+// sum exceeds the total.  acc and out may alias.
 __global__ void finalize_kernel(unsigned long long* acc, int nedges, unsigned long long* out,
                                 unsigned long long total, unsigned long long* err_word) {
     __shared__ unsigned long long part[256];
@@ -1370,7 +1373,7 @@ __global__ void finalize_kernel(unsigned long long* acc, int nedges, unsigned lo
     if (threadIdx.x == 0) {
         if (sum > total) {
             atomicOr(err_word, (unsigned long long)kErrBadHist);
-            out[nedges] = 0;
+            out[nedges] = ~0ull;  // sentinel: the bins sum to more than the pair total
         } else {
             out[nedges] = total - sum;
         }
@@ -1399,7 +1402,7 @@ __global__ void finalize_batch_kernel(const unsigned long long* acc, int acc_str
         const unsigned long long total = totals[blockIdx.x];
         if (part[0] > total) {
             atomicOr(err_word, (unsigned long long)kErrBadHist);
-            o[nedges] = 0;
+            o[nedges] = ~0ull;
         } else {
             o[nedges] = total - part[0];
         }

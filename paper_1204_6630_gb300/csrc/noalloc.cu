@@ -9,6 +9,7 @@
 // keeps its only scratch (the uint64 accumulators) in a file-scope
 // __device__ array of fixed size.  Every GPU that loads the library holds
 // that array (4 KB) until the process exits.
+#include <atomic>
 #include <mutex>
 
 #include "plan.h"
@@ -21,6 +22,14 @@ namespace {
 constexpr int kNoAllocWords = 512;          // 4 KB of uint64 accumulators
 constexpr int kNoAllocTile = 256;           // i-block = j-chunk = j-tile
 constexpr int kNoAllocMaxDevices = 64;
+// A block's shared uint32 counters take at most kNoAllocTile^2 pairs per item
+// (all in one bin at worst); merging them into the uint64 accumulators every
+// kNoAllocFlushItems items keeps every counter below 2^30.
+constexpr uint32_t kNoAllocFlushItems = 16384;
+
+// Test hook: grid cap of the counting launch (0 = sms * 8), so that a test can
+// make one block take more than 2^32 pairs.
+std::atomic<int> g_noalloc_grid_cap{0};
 
 // The scratch.  In host code this name is a host-side stand-in, not a device
 // address: host code passes the address returned by cudaGetSymbolAddress.
@@ -32,9 +41,9 @@ struct Thresholds {
 
 // Binary64 pair counting over the upper triangle of raw row-major (n x 3)
 // coordinates: d = (xa xb + ya yb) + za zb without contraction, histogram
-// index = #{m : d <= C_m}.  Each block accumulates a shared histogram and adds
-// it to acc[0 .. nedges-1] (pairs beyond the last edge are left to the
-// finalize step as overflow).
+// index = #{m : d <= C_m}.  Each block accumulates a shared uint32 histogram,
+// adds it to acc[0 .. nedges-1] every kNoAllocFlushItems items and at the end
+// (pairs beyond the last edge are left to the finalize step as overflow).
 __global__ void __launch_bounds__(kNoAllocTile) noalloc_count_kernel(
     const double* __restrict__ xyz, uint32_t n, const __grid_constant__ Thresholds thr, int nedges,
     uint32_t n_blk, uint64_t n_items, unsigned long long* acc) {
@@ -45,7 +54,17 @@ __global__ void __launch_bounds__(kNoAllocTile) noalloc_count_kernel(
     for (int k = tid; k < nedges; k += kNoAllocTile) sc[k] = thr.c[k];
     for (int k = tid; k <= nedges; k += kNoAllocTile) sh[k] = 0u;
     const double c_last = thr.c[nedges - 1];
+    uint32_t since_flush = 0;  // items since the last merge (block-uniform)
     for (uint64_t q = blockIdx.x; q < n_items; q += gridDim.x) {
+        if (since_flush == kNoAllocFlushItems) {
+            __syncthreads();  // every add of the previous items is done
+            for (int h = tid; h < nedges; h += kNoAllocTile) {
+                if (sh[h]) atomicAdd(acc + h, (unsigned long long)sh[h]);
+                sh[h] = 0u;
+            }
+            since_flush = 0;  // (the barrier below orders the clears before new adds)
+        }
+        ++since_flush;
         const ItemGeom g = item_geom(q, n, n, n_blk, n_blk, true, kNoAllocTile, kNoAllocTile, kNoAllocTile);
         __syncthreads();  // previous tile fully read
         const uint32_t jl = g.j0 + (uint32_t)tid;
@@ -121,12 +140,17 @@ extern "C" int tpcf_count_auto_noalloc(const double* xyz_dev, uint64_t n, const 
     if (items > 0) {
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TPCF_ECUDA;
-        const uint64_t grid = items < (uint64_t)sms * 8 ? items : (uint64_t)sms * 8;
+        uint64_t cap = (uint64_t)sms * 8;
+        const int knob = g_noalloc_grid_cap.load();
+        if (knob > 0 && (uint64_t)knob < cap) cap = (uint64_t)knob;
+        const uint64_t grid = items < cap ? items : cap;
         noalloc_count_kernel<<<(unsigned)grid, kNoAllocTile, 0, st>>>(xyz_dev, nn, thr, nedges, n_blk,
                                                                       items, acc);
         if (cudaGetLastError() != cudaSuccess) return TPCF_ECUDA;
     }
-    // overflow = n(n-1)/2 - sum; the error word (acc[kNoAllocWords - 1]) is never set here
+    // overflow = n(n-1)/2 - sum; should the sum exceed that total (a fault the
+    // kernel cannot produce), the finalize writes UINT64_MAX as the overflow
+    // entry, which the caller can test without a synchronization here
     const unsigned long long total = (unsigned long long)n * (n ? n - 1 : 0) / 2;
     if (cudaMemsetAsync(acc + kNoAllocWords - 1, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return TPCF_ECUDA;
@@ -135,3 +159,5 @@ extern "C" int tpcf_count_auto_noalloc(const double* xyz_dev, uint64_t n, const 
         return TPCF_ECUDA;
     return TPCF_OK;
 }
+
+extern "C" void tpcf_debug_noalloc_grid(int blocks) { g_noalloc_grid_cap.store(blocks < 0 ? 0 : blocks); }

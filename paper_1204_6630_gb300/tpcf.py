@@ -123,6 +123,8 @@ _SIGS = {
                                             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_uint32), _u64p]),
     "tpcf_debug_fail_alloc_after": (None, [ctypes.c_int]),
+    "tpcf_debug_noalloc_grid": (None, [ctypes.c_int]),
+    "tpcf_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp]),
     "tpcf_count_auto_noalloc": (ctypes.c_int, [_vp, _u64, _dp, ctypes.c_int, _vp, _vp]),
     "tpcf_jackknife": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _u64p, _dp, _dp,
                                       ctypes.POINTER(tpcf_stats)]),
@@ -543,6 +545,17 @@ def tpcf_graph_destroy(graph: int) -> None:
 
 def tpcf_debug_fail_alloc_after(n: int) -> None:
     load().tpcf_debug_fail_alloc_after(n)
+
+
+def tpcf_debug_noalloc_grid(blocks: int) -> None:
+    load().tpcf_debug_noalloc_grid(blocks)
+
+
+def tpcf_fp32_peak(device: int = 0, packed: bool = False) -> float:
+    """Measured FP32 FMA throughput of the device in TFLOP/s (see include/tpcf.h)."""
+    v = ctypes.c_double(0.0)
+    _check(load().tpcf_fp32_peak(device, 1 if packed else 0, ctypes.byref(v)), "tpcf_fp32_peak")
+    return v.value
 
 
 # ------------------------------------------------------------------ object layer
