@@ -86,7 +86,8 @@ extern "C" {
 
 /* configuration flags */
 #define TPCF_F_NO_SORT 0x1u          /* keep catalog order (no spatial sort on the device) */
-#define TPCF_F_PACKED_FMA 0x4u       /* FP32 screen with packed FP32x2 FMA (fma.rn.f32x2) instead of scalar FMA */
+#define TPCF_F_PACKED_FMA 0x4u       /* no effect: the FP32 screen always uses packed FP32x2 FMA
+                                        (fma.rn.f32x2); the value stays reserved */
 #define TPCF_F_AUTOTUNE 0x8u         /* the first counting call of a workload class times every kernel
                                         shape that fits and the context keeps the fastest */
 #define TPCF_F_PRUNE 0x10u           /* spatial pruning: each counting launch skips the blocks of
@@ -94,9 +95,17 @@ extern "C" {
                                         are provably farther apart than the last edge (every pair
                                         in them is overflow); counts are unchanged, the skipped pair
                                         slots are reported in tpcf_stats.pruned_pairs.  Screen
-                                        kernels only (ignored with TPCF_PLAIN_FP64 and
-                                        TPCF_F_PACKED_FMA).  Not in the paper (its brute force
-                                        evaluates every pair). */
+                                        kernels only (ignored with TPCF_PLAIN_FP64 and with
+                                        TPCF_F_CHECK_OVERFLOW).  Not in the paper (its brute
+                                        force evaluates every pair). */
+#define TPCF_F_CHECK_OVERFLOW 0x20u  /* self-check: the kernels count the overflow row like every
+                                        other row (pairs the FP32 screen rejects included) instead
+                                        of deriving it as the pair total minus the other entries,
+                                        and a counting call whose histogram does not sum to its
+                                        pair total fails (TPCF_ECUDA, "histogram does not add up";
+                                        that histogram's overflow entry is UINT64_MAX), so a pair
+                                        the kernel lost cannot hide in overflow.  Slower on tiles
+                                        that meet the diagonal or padding. */
 #define TPCF_F_TEST_WAIT_TIMEOUT 0x100u /* test hook: the first j-tile copy of each counting
                                            launch is never issued, so its bounded wait expires
                                            and the call returns TPCF_ETIMEOUT */
@@ -122,9 +131,10 @@ typedef struct tpcf_config {
     uint32_t flags;            /* TPCF_F_* */
     int threads;               /* kernel shape override: threads per block (0 = tuned default) */
     int ipt;                   /* kernel shape override: i-points per thread (0 = default) */
-    int jtile;                 /* kernel shape override: j-points per shared-memory tile, a multiple
-                                  of 128 dividing 4096 (0 = default) */
-    int stages;                /* kernel shape override: shared-memory pipeline stages 2..16 (0 = default) */
+    int jtile;                 /* kernel shape override: j-points per shared-memory tile of a warp's
+                                  ring, a multiple of 128 dividing 4096 (0 = default) */
+    int stages;                /* kernel shape override: stages of each warp's shared-memory ring
+                                  2..16 (0 = default) */
     uint32_t shard_index;      /* multi-process split of the pair tiles: this process's index */
     uint32_t shard_count;      /* number of shards (0 or 1 = no split); histograms of all
                                   shards sum to the unsplit result exactly */

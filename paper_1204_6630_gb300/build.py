@@ -1,7 +1,8 @@
 """Build the CUDA library ``libtpcf.so`` in-tree with nvcc for sm_103a.
 
-The translation units (kernels, host runtime, job server, the
-no-allocation entry point, the FP32 peak measurement) are compiled in
+The translation units (the counting kernel, catalog preparation, host
+runtime, job server, the no-allocation entry point, the FP32 peak
+measurement) are compiled in
 parallel and linked into ``paper_1204_6630_gb300/_build/libtpcf.so``.  Host
 code is compiled with ``-ffp-contract=off`` so binary64 arithmetic (threshold
 derivation, the estimator) is rounded exactly as written.
@@ -19,7 +20,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libtpcf.so")
-SOURCES = ["kernels.cu", "runtime.cpp", "server.cpp", "noalloc.cu", "peak.cu"]
+SOURCES = ["count.cu", "prep.cu", "runtime.cpp", "server.cpp", "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

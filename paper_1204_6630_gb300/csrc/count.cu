@@ -1,0 +1,1430 @@
+// CUDA counting kernel (sm_103a) for brute-force angular pair counting.
+//
+// Paper: Ponce et al., "Application of GPUs for the calculation of two point
+// correlation functions in cosmology".  Section 3 lists the three features of
+// its CUDA design: points staged in shared memory for the dot product and the
+// angle, shared-memory atomic partial histograms combined into one global
+// histogram, and the three histograms DD, DR, RR computed in parallel.  This
+// file keeps those roles and re-designs them for GB300:
+//   * every warp is an independent worker: it draws its own work items (its
+//     32 R i-points x a chunk of j-points) from a per-launch counter and
+//     streams the j-tiles of its items into its own ring of shared-memory
+//     stages with TMA bulk copies (cp.async.bulk + mbarrier), so no warp ever
+//     waits for another;
+//   * j-tiles are staged as x | y | z arrays and i-points held in registers
+//     as (a, a) pairs, so one fma.rn.f32x2 gives the screen values of two
+//     pairs;
+//   * the angle is never formed: an FP32 dot product is compared with
+//     cos-space thresholds derived on the host from the host acos, and only
+//     pairs inside a proven guard band around a threshold are recomputed in
+//     binary64 (the exact definition);
+//   * every thread owns private 16-bit counters in shared memory, merged by
+//     its warp into uint64 global bins before any can wrap;
+//   * the work is a list of (i-block x j-chunk) items over the upper triangle
+//     (auto counts) or the rectangle (cross counts) of one or more histograms.
+#include <stdint.h>
+
+#include "plan.h"
+#include "tpcf.h"
+#include "tpcf_internal.h"
+
+namespace tpcf {
+
+// Dynamic shared memory of the counting kernel.  Helpers address it through
+// 32-bit byte offsets (one register each instead of a 64-bit pointer).
+extern __shared__ __align__(128) unsigned char dyn_smem[];
+
+template <class Tp>
+__device__ __forceinline__ Tp* sptr(uint32_t off) {
+    return reinterpret_cast<Tp*>(dyn_smem + off);
+}
+
+// ============================================================== PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D TMA bulk copy global -> shared, completion signalled on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// One bounded probe of the barrier phase.  The suspend-time hint lets the
+// hardware park the waiting warp until the phase completes or about
+// kSuspendNs elapse, instead of spinning on the probe.
+constexpr uint32_t kSuspendNs = 20000;
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar` to complete, giving up after limit_ns.
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// Packed FP32x2 (sm_100+): two FP32 lanes in one 64-bit register pair.
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pack2(float lo, float hi) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo_of(u64 v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi_of(u64 v) { return __uint_as_float((uint32_t)(v >> 32)); }
+// d = a * b + c on both halves, each rounded to nearest as fmaf rounds.
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// d = a - b on both halves, rounded to nearest.
+__device__ __forceinline__ u64 fsub2(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Three-input AND / OR in one logic instruction.
+__device__ __forceinline__ uint32_t and3(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0x80;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t or3(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0xfe;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// AND (OR) of the bit patterns of N words as a tree of three-input operations.
+template <int N, bool OR>
+__device__ __forceinline__ uint32_t lop_tree(const uint32_t* v) {
+    if constexpr (N == 1) {
+        return v[0];
+    } else if constexpr (N == 2) {
+        return OR ? (v[0] | v[1]) : (v[0] & v[1]);
+    } else {
+        constexpr int A = N / 3, B = (N - A) / 2;
+        const uint32_t x = lop_tree<A, OR>(v), y = lop_tree<B, OR>(v + A), z = lop_tree<N - A - B, OR>(v + A + B);
+        return OR ? or3(x, y, z) : and3(x, y, z);
+    }
+}
+
+// ============================================================== shared-memory layout
+// Kernel variants: FP32 screen (angles), all-binary64 comparator, FP32 screen
+// of distances (3-D variant).
+enum KernelMode { kModeScreen = 0, kModePlain = 1, kModeEuclid = 3 };
+
+// Block-wide control words (int32): the abort flag and each warp's queue length.
+enum Ctl { kCtlAbort = 0, kCtlQueue = 8, kCtlWords = 48 };
+constexpr int kQueuePerWarp = 64;   // band pairs per warp awaiting the binary64 recheck
+constexpr int kMaskGroups = 32;     // fast loop: groups per warp reduction of the slow-group mask
+constexpr uint32_t kPruneSlotBytes = 32;  // float4 i-sphere, B's sphere pointer, pruned pair slots (u64)
+
+// One stage of a warp's ring: which item (walk position) and tile it holds.
+struct TileMeta {
+    uint32_t q;
+    uint32_t t;
+};
+
+struct SmemLayout {
+    uint32_t ctl;       // control words
+    uint32_t bars;      // W x S full mbarriers (warp w: S consecutive)
+    uint32_t meta;      // W x S TileMeta
+    uint32_t stage;     // W x S stages of stage_bytes
+    uint32_t hist;      // (nedges + 1) * T / 2 uint32: row h, column c at word h * T/2 + c (see HistCol)
+    uint32_t cos_thr;   // nedges doubles
+    uint32_t lo, hi, cos32, zlo, zhi;  // nedges floats each
+    uint32_t lut;       // kLutCells 16-bit entries (screen kernels)
+    uint32_t queue;     // W * kQueuePerWarp unsettled pairs (i, j) (uint2, screen kernels)
+    uint32_t icap;      // W pruning slots: the warp's i-sphere, B's sphere array, pruned pair slots
+    uint32_t total;
+};
+
+__host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+// Bytes a staged j-point takes: x | y | z floats (screen kernels) or a
+// binary64 (x, y, z, 0) record (all-binary64 kernel).
+__host__ __device__ inline uint32_t staged_point_bytes(int mode) { return mode == kModePlain ? 32u : 12u; }
+
+__host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S, int nedges) {
+    SmemLayout L;
+    const bool plain = mode == kModePlain;
+    const uint32_t W = (uint32_t)T / 32;
+    uint32_t off = 0;
+    L.ctl = off; off += kCtlWords * 4;
+    off = align_up(off, 8);
+    L.bars = off; off += W * (uint32_t)S * 8;
+    L.meta = off; off += W * (uint32_t)S * 8;
+    off = align_up(off, 128);
+    L.stage = off; off += W * (uint32_t)S * (uint32_t)J * staged_point_bytes(mode);
+    L.hist = off; off += (uint32_t)(nedges + 1) * (uint32_t)(T / 2) * 4;
+    off = align_up(off, 16);
+    L.cos_thr = off; off += (uint32_t)nedges * 8;
+    L.lo = off; off += (uint32_t)nedges * 4;
+    L.hi = off; off += (uint32_t)nedges * 4;
+    L.cos32 = off; off += (uint32_t)nedges * 4;
+    L.zlo = off; off += (uint32_t)nedges * 4;
+    L.zhi = off; off += (uint32_t)nedges * 4;
+    off = align_up(off, 16);
+    L.lut = off; off += plain ? 0u : (uint32_t)kLutCells * 2;
+    off = align_up(off, 16);
+    L.queue = off; off += plain ? 0u : W * kQueuePerWarp * 8;
+    off = align_up(off, 16);
+    L.icap = off; off += W * kPruneSlotBytes;
+    L.total = off;
+    return L;
+}
+
+// ============================================================== LUT entries
+// A cell of the shared LUT is a 16-bit code, read sign-extended:
+//   - settled in row P < ne (P == Q): P (0 <= code < kLutRowLimit);
+//   - settled in the overflow row (P == Q == ne): kLutSkip, a non-negative
+//     code >= kLutRowLimit, so the pair adds nothing (without
+//     TPCF_F_CHECK_OVERFLOW the overflow row is never merged: the finalize
+//     derives it from the pair total); with TPCF_F_CHECK_OVERFLOW the code is
+//     the row ne itself, so overflow pairs are counted like the others;
+//   - unsettled (edges [P, Q) open): bit 15 set (negative), P in bits 0..8,
+//     min(Q - P, 63) in bits 9..14; the span 63 stands for Q = ne, a wider
+//     range that every resolver handles with the same result (the edges
+//     past the true Q are decided "not crossed" by their bounds).
+// Rows fit 9 bits: ne <= TPCF_MAX_EDGES = 321.
+constexpr uint32_t kLutRowLimit = 512;
+constexpr uint32_t kLutSkip = 0x4000;
+constexpr uint32_t kLutSpanCap = 63;
+
+__device__ __forceinline__ unsigned short lut_code(uint32_t P, uint32_t Q, uint32_t ne, bool count_over) {
+    if (P == Q) return (unsigned short)(P == ne && !count_over ? kLutSkip : P);
+    return (unsigned short)(0x8000u | P | (min(Q - P, kLutSpanCap) << 9));
+}
+__device__ __forceinline__ int lut_P(int x) { return x & 0x1ff; }
+__device__ __forceinline__ int lut_Q(int x, int ne) {
+    const int span = (x >> 9) & 0x3f;
+    return span == (int)kLutSpanCap ? ne : (x & 0x1ff) + span;
+}
+
+// Byte offset of histogram row h from a thread's column: h * (T/2) * 4 = h << log2(2T).
+template <int T>
+__host__ __device__ constexpr int row_shift() {
+    static_assert(T == 128 || T == 256 || T == 512 || T == 1024, "power-of-two block");
+    return T == 128 ? 8 : T == 256 ? 9 : T == 512 ? 10 : 11;
+}
+
+__device__ __forceinline__ int ld_shared_s16(uint32_t addr) {
+    int v;
+    asm volatile("ld.shared.s16 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+// ============================================================== work items
+// Items are drawn dynamically: every warp takes walk position item_lo + k for
+// the next k of a per-launch counter (a statistics word, zeroed before each
+// launch), so warps that draw cheap items take more of them.  Within a
+// sub-problem, position item_begin + k visits local item (k * walk_mult) mod
+// n_items (walk_item).  Positions fit 32 bits (the host checks the count).
+struct Cursor {
+    uint32_t q;       // walk position of the item
+    int sub;
+    ItemGeom g;
+    uint32_t t;       // current tile within the item
+    bool valid;
+};
+
+__device__ __forceinline__ const SubProblem& sub_of(const WorkDesc& wd, int s) {
+    return wd.sub_dev ? wd.sub_dev[s] : wd.sub[s];
+}
+
+__device__ int find_sub(const WorkDesc& wd, uint64_t q) {
+    int lo = 0, hi = wd.nsub;  // sub[lo].item_begin <= q < sub[hi].item_begin
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sub_of(wd, mid).item_begin <= q) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ bool load_item(const WorkDesc& wd, uint32_t q, Cursor& c) {
+    c.q = q;
+    c.sub = find_sub(wd, q);
+    const SubProblem& sp = sub_of(wd, c.sub);
+    const uint64_t local = walk_item(q - sp.item_begin, sp.n_items, sp.walk_mult);
+    c.g = item_geom(local, sp.na, sp.nb, sp.n_iblk, sp.n_jchunk, sp.auto_mode != 0, wd.I, wd.Jc, wd.J);
+    c.t = c.g.t_first;
+    return c.t < c.g.t_end;
+}
+
+// The warp's next item with countable tiles (drawing again past empty ones);
+// called by every lane of the warp (lane 0 draws, the position is broadcast).
+__device__ void draw_next(const WorkDesc& wd, Cursor& c) {
+    const uint32_t q_end = (uint32_t)wd.item_hi;
+    while (true) {
+        uint32_t q = 0;
+        if ((threadIdx.x & 31) == 0) q = (uint32_t)wd.item_lo + (uint32_t)atomicAdd(wd.stats + kStatNextItem, 1ull);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= q_end) {
+            c.valid = false;
+            return;
+        }
+        if (load_item(wd, q, c)) {
+            c.valid = true;
+            return;
+        }
+    }
+}
+
+__device__ __forceinline__ void advance(const WorkDesc& wd, Cursor& c) {
+    if (!c.valid) return;
+    if (++c.t < c.g.t_end) return;
+    draw_next(wd, c);
+}
+
+// ============================================================== block helpers
+// Block constants live in the kernel parameter (constant bank): the host fills
+// the shared-memory offsets and the bin scalars of WorkDesc, so the kernel
+// spends no registers on them.
+template <int T>
+__device__ void load_bins(const BinsDev* bd, const WorkDesc& wd, bool plain) {
+    const int ne = wd.ne;
+    double* c = sptr<double>(wd.off_cthr);
+    float* lo = sptr<float>(wd.off_lo);
+    float* hi = sptr<float>(wd.off_hi);
+    float* c32 = sptr<float>(wd.off_c32);
+    float* zlo = sptr<float>(wd.off_zlo);
+    float* zhi = sptr<float>(wd.off_zhi);
+    for (int k = threadIdx.x; k < ne; k += T) {
+        c[k] = bd->cos_thr[k];
+        lo[k] = bd->lo[k];
+        hi[k] = bd->hi[k];
+        c32[k] = bd->cos32[k];
+        zlo[k] = bd->zlo[k];
+        zhi[k] = bd->zhi[k];
+    }
+    if (!plain) {
+        // Shared copy of the LUT as 16-bit entries (see lut_code).
+        const bool count_over = (wd.flags & TPCF_F_CHECK_OVERFLOW) != 0;
+        unsigned short* lut = sptr<unsigned short>(wd.off_lut);
+        for (int k = threadIdx.x; k < kLutCells; k += T) {
+            const uint32_t e = bd->lut[k];
+            lut[k] = lut_code(e & 0xffffu, e >> 16, (uint32_t)ne, count_over);
+        }
+    }
+}
+
+// Thread-private 16-bit histogram counters, two per 32-bit shared word:
+// thread t < T/2 owns the low halves of column t, thread t + T/2 the high
+// halves of the same column, so every thread adds one fixed increment (1 or
+// 2^16) and a row is a plain byte offset.  A counter has a single writer; the
+// word's atomic add keeps the partner's half intact.  Lanes of a warp hold 32
+// consecutive columns, so a warp's adds to any mix of rows hit 32 banks.
+struct HistCol {
+    uint32_t addr;  // shared byte address of the thread's word in row 0
+    uint32_t inc;   // 1 (low half) or 65536 (high half)
+};
+
+template <int T>
+__device__ __forceinline__ HistCol hist_col(const WorkDesc& wd) {
+    const uint32_t t = threadIdx.x;
+    return HistCol{smem_addr(dyn_smem) + wd.off_hist + (t % (T / 2)) * 4u, t < T / 2 ? 1u : 65536u};
+}
+
+__device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+__device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+// Histogram row h of the thread's column, one increment.
+template <int T>
+__device__ __forceinline__ void hist_inc(const HistCol& hc, int h) {
+    red_add_shared(hc.addr + ((uint32_t)h << row_shift<T>()), hc.inc);
+}
+
+// One warp merges its 32 counters of every row into the global uint64 bins
+// and clears them.  Rows 0..nedges-1 (underflow and the B bins) are merged;
+// row nedges (pairs beyond the last edge) is merged only when overflow is
+// counted (TPCF_F_CHECK_OVERFLOW), otherwise only cleared: the finalize
+// kernel derives overflow from the pair total.  Each thread takes its own
+// half out of the shared word with an atomic subtract, since the partner warp
+// may be adding to the other half at the same time.
+template <int T>
+__device__ void warp_flush_hist(const HistCol& hc, int nedges, bool count_over, unsigned long long* out) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t sh = hc.inc == 1u ? 0u : 16u;
+    for (int h = 0; h <= nedges; ++h) {
+        const uint32_t a = hc.addr + ((uint32_t)h << row_shift<T>());
+        uint32_t mine = (ld_shared_u32(a) >> sh) & 0xffffu;
+        if (mine) red_add_shared(a, 0u - (mine << sh));
+        if (h == nedges && !count_over) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+        if (lane == 0 && mine != 0) atomicAdd(out + h, (unsigned long long)mine);
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ============================================================== per-pair classification
+__device__ __forceinline__ Point64 ldg_point(const Point64* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 u = __ldg(q), v = __ldg(q + 1);
+    Point64 r;
+    r.x = u.x; r.y = u.y; r.z = v.x; r.w = v.y;
+    return r;
+}
+
+// Binary64 dot product in the definition's order, no contraction.
+__device__ __forceinline__ double dot64(const Point64& a, const Point64& b) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)), __dmul_rn(a.z, b.z));
+}
+
+// Exact histogram index of a band pair: h = nbv + #{m in [nbv, nav) : d <= C_m}
+// with d the binary64 dot product (the edges below nbv are certainly crossed,
+// those from nav on certainly not).  h32 is the FP32-only index; *mismatch
+// is set when it differs (statistics).
+__device__ __forceinline__ int band_index(const WorkDesc& wd, const SubProblem& sp, uint32_t ig, uint32_t jg,
+                                          int nbv, int nav, int h32, uint32_t* mismatch) {
+    const double* cthr = sptr<const double>(wd.off_cthr);
+    const double d = dot64(ldg_point(sp.a64 + ig), ldg_point(sp.b64 + jg));
+    int h = nbv;
+    for (int m = nbv; m < nav; ++m) h += (d <= cthr[m]);
+    *mismatch = (h != h32) ? 1u : 0u;
+    return h;
+}
+
+// FP32 classification of a pair whose LUT entry left edges [P, Q) open:
+// nb(c) = #{m : c < lo_m} (edges certainly crossed), na(c) = #{m : c <= hi_m}
+// (edges possibly crossed); nb == na settles the index.  Otherwise h = -1
+// with the band range [nbv, nav) and the FP32-only index h32.
+struct Resolved {
+    int h, nbv, nav, h32;
+};
+
+__device__ __forceinline__ Resolved resolve_f32(const WorkDesc& wd, float c, int P, int Q) {
+    const float* lo = sptr<const float>(wd.off_lo);
+    const float* hi = sptr<const float>(wd.off_hi);
+    const float* c32 = sptr<const float>(wd.off_c32);
+    int nb_ = P, na_ = P;
+    for (int m = P; m < Q; ++m) {
+        nb_ += (c < lo[m]);
+        na_ += (c <= hi[m]);
+    }
+    if (nb_ == na_) return Resolved{nb_, 0, 0, 0};
+    int h = nb_;
+    for (int m = nb_; m < na_; ++m) h += (c <= c32[m]);
+    return Resolved{-1, nb_, na_, h};
+}
+
+__device__ __forceinline__ uint32_t queue_off(const WorkDesc& wd, int warp) {
+    return wd.off_queue + (uint32_t)warp * kQueuePerWarp * 8;
+}
+
+__device__ __forceinline__ uint32_t queue_count_off(const WorkDesc& wd, int warp) {
+    return wd.off_ctl + (uint32_t)(kCtlQueue + warp) * 4;
+}
+
+// Screen value of pair (ig, jg) recomputed from the FP32 copies, bit-identical
+// to the kernel's (fma.rn.f32x2 rounds each half as fmaf does).
+__device__ __forceinline__ float screen_value(const WorkDesc& wd, const SubProblem& sp, uint32_t ig, uint32_t jg) {
+    const float4 a = __ldg(sp.a32 + ig), b = __ldg(sp.b32 + jg);
+    return fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, wd.neg_fast_t)));
+}
+
+// LUT entry of screen value e: cell k = rne(sat(e * 2^-q) * 2^14), read as the
+// low bits of fma(v, 2^14, 2^23).
+__device__ __forceinline__ int lut_entry(const WorkDesc& wd, float e) {
+    const float v = __saturatef(e * wd.lut_scale);
+    const float f = fmaf(v, 16384.0f, 8388608.0f);
+    return ld_shared_s16(smem_addr(dyn_smem) + wd.off_lut + (__float_as_uint(f) - 0x4B000000u) * 2u);
+}
+
+// ---- 3-D variant (Euclidean separations)
+// z = fl32(|a' - b'|^2): differences, then a fused sum of squares.
+__device__ __forceinline__ float euclid_z(float ax, float ay, float az, float bx, float by, float bz) {
+    const float dx = ax - bx, dy = ay - by, dz = az - bz;
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+// LUT cell of z: constant-ratio cells, clamp((bits(z) - zbits0) >> zshift) (z >= 0).
+__device__ __forceinline__ uint32_t euclid_cell_addr(const WorkDesc& wd, float z, uint32_t lut_base) {
+    int k = ((int)__float_as_uint(z) - wd.zbits0) >> wd.zshift;
+    k = min(max(k, 0), kLutCells - 1);
+    return lut_base + (uint32_t)k * 2u;
+}
+
+// binary64 d^2 in the definition's order: differences, squares, left-to-right sum.
+__device__ __forceinline__ double dist2_64(const Point64& a, const Point64& b) {
+    const double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y), dz = __dsub_rn(a.z, b.z);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// A 3-D pair whose LUT entry left edges [P, Q) open: z against the z-space
+// bounds (increasing with the edge index; z >= zhi_m proves d^2 >= S_m, z <
+// zlo_m proves d^2 < S_m).  Returns h >= 0 when z settles it; otherwise -1 and
+// the edges still open, [*lo, *hi).
+__device__ __forceinline__ int euclid_resolve(const WorkDesc& wd, float z, int ent, int* lo_out, int* hi_out) {
+    const float* zlo = sptr<const float>(wd.off_zlo);
+    const float* zhi = sptr<const float>(wd.off_zhi);
+    const int Q = lut_Q(ent, wd.ne);
+    int lo = lut_P(ent), hi = Q;
+    while (lo < hi) {  // first m in [P, Q) with z < zhi[m]: the edges below are crossed
+        const int mid = (lo + hi) >> 1;
+        if (z >= zhi[mid]) lo = mid + 1; else hi = mid;
+    }
+    if (lo == Q || z < zlo[lo]) return lo;
+    int a = lo + 1, c = Q;  // first m > lo with z < zlo[m]: the edges from there on are not crossed
+    while (a < c) {
+        const int mid = (a + c) >> 1;
+        if (z >= zlo[mid]) a = mid + 1; else c = mid;
+    }
+    *lo_out = lo;
+    *hi_out = a;
+    return -1;
+}
+
+// Index of a 3-D pair decided in binary64 over the open edges [lo, hi)
+// (S increasing: count the edges with d^2 >= S_m); h32 from the FP32 value
+// against RN(S_m) for the statistics.
+__device__ __forceinline__ int euclid_band_index(const WorkDesc& wd, const SubProblem& sp, uint32_t ig, uint32_t jg,
+                                                 float z, int lo, int hi, uint32_t* mismatch) {
+    const double* sthr = sptr<const double>(wd.off_cthr);
+    const float* s32 = sptr<const float>(wd.off_c32);
+    const double d2 = dist2_64(ldg_point(sp.a64 + ig), ldg_point(sp.b64 + jg));
+    // two padding points (+inf) are NaN apart: not a pair (overflow, never merged);
+    // real points are finite, |x| <= 1e28, so their binary64 d^2 is finite
+    if (d2 != d2) {
+        *mismatch = 0u;
+        return wd.ne;
+    }
+    int h = lo, h32 = lo;
+    for (int m = lo; m < hi; ++m) {
+        h += (d2 >= sthr[m]);
+        h32 += (z >= s32[m]);
+    }
+    *mismatch = (h != h32) ? 1u : 0u;
+    return h;
+}
+
+// Histogram index of a queued pair (its LUT cell left edges open): the chord
+// refinement where the catalogs allow it (angles), the FP32 comparison with
+// the open edges' screen bounds, else the binary64 recomputation in the
+// definition's order.  Band statistics are added to *band, *mism.
+__device__ __forceinline__ int classify_unsettled(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg,
+                                                  uint32_t* band, uint32_t* mism) {
+    const SubProblem& sp = sub_of(wd, sub);
+    if (wd.euclid) {
+        const float4 a = __ldg(sp.a32 + ig), b = __ldg(sp.b32 + jg);
+        const float z = euclid_z(a.x, a.y, a.z, b.x, b.y, b.z);
+        const int ent = ld_shared_s16(euclid_cell_addr(wd, z, smem_addr(dyn_smem) + wd.off_lut));
+        if (ent >= 0) return ent == (int)kLutSkip ? wd.ne : ent;  // settled (not expected)
+        int lo = 0, hi = 0;
+        const int h0 = euclid_resolve(wd, z, ent, &lo, &hi);
+        if (h0 >= 0) return h0;
+        uint32_t mm;
+        const int h = euclid_band_index(wd, sp, ig, jg, z, lo, hi, &mm);
+        *band += 1;
+        *mism += mm;
+        return h;
+    }
+    const float e = screen_value(wd, sp, ig, jg);
+    const int ent = lut_entry(wd, e);
+    if (ent >= 0) return ent == (int)kLutSkip ? wd.ne : ent;  // settled (not expected)
+    const Resolved rs = resolve_f32(wd, e, lut_P(ent), lut_Q(ent, wd.ne));
+    if (rs.h >= 0) return rs.h;
+    uint32_t mm;
+    const int h = band_index(wd, sp, ig, jg, rs.nbv, rs.nav, rs.h32, &mm);
+    *band += 1;
+    *mism += mm;
+    return h;
+}
+
+// One warp classifies its queued pairs (i, j) and adds each to the lane's
+// own histogram column; the warp's band statistics go to the call's
+// statistics words; ends with the warp's queue empty.
+template <int T>
+__device__ __noinline__ void warp_drain_queue(const WorkDesc& wd, int sub, HistCol hc) {
+    const int warp = (int)(threadIdx.x >> 5);
+    const uint2* wq = sptr<const uint2>(queue_off(wd, warp));
+    volatile int* wq_count = sptr<volatile int>(queue_count_off(wd, warp));
+    uint32_t band = 0, mism = 0;
+    __syncwarp();
+    const int n = min(*wq_count, kQueuePerWarp);
+    for (int k = (int)(threadIdx.x & 31); k < n; k += 32) {
+        const uint2 q = wq[k];
+        hist_inc<T>(hc, classify_unsettled(wd, sub, q.x, q.y, &band, &mism));
+    }
+    const unsigned long long b = warp_sum(band), m = warp_sum(mism);
+    if ((threadIdx.x & 31) == 0) {
+        if (b) atomicAdd(wd.stats + kStatBand, b);
+        if (m) atomicAdd(wd.stats + kStatMismatch, m);
+        *wq_count = 0;
+    }
+    __syncwarp();
+}
+
+// A pair that the queue cannot take (full) is classified at once (rare, out of line).
+template <int T>
+__device__ __noinline__ void classify_now(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg, HistCol hc) {
+    uint32_t band = 0, mism = 0;
+    hist_inc<T>(hc, classify_unsettled(wd, sub, ig, jg, &band, &mism));
+    if (band) atomicAdd(wd.stats + kStatBand, 1ull);
+    if (mism) atomicAdd(wd.stats + kStatMismatch, 1ull);
+}
+
+// An unsettled pair (divergent: executed by the lanes holding one): queued
+// for the warp's drain, one shared atomic for all active lanes.
+template <int T>
+__device__ __forceinline__ void queue_pair(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg, const HistCol& hc) {
+    const uint32_t act = __activemask();
+    const uint32_t lane = threadIdx.x & 31u;
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(sptr<int>(queue_count_off(wd, (int)(threadIdx.x >> 5))), __popc(act));
+    base = __shfl_sync(act, base, leader);
+    const int pos = base + __popc(act & ((1u << lane) - 1u));
+    if (pos < kQueuePerWarp)
+        sptr<uint2>(queue_off(wd, (int)(threadIdx.x >> 5)))[pos] = make_uint2(ig, jg);
+    else
+        classify_now<T>(wd, sub, ig, jg, hc);
+}
+
+// An unsettled pair of the slow path (a = the i-point, b = the j-point, FP32):
+// its screen value and LUT entry are recomputed (bit-identical to the
+// slow path's), then the chord refinement decides the edges the entry leaves
+// open: z = fl32(|a' - b'|^2) is within 4u|a - b| + O(u |a-b|^2) of
+// 2 (1 - d) (bounds zlo, zhi: runtime.cpp), far tighter than the screen
+// value at the small and moderate angles of a histogram range.  Z-space
+// bounds increase with the edge index, so a binary search over [P, Q) finds
+// nb = #{crossed}; the pair is settled when z is also below zlo[nb].  Pairs
+// left in a chord band (or catalogs outside the chord bound's norm
+// tolerance) are queued for the binary64 recheck.
+template <int T>
+__device__ __forceinline__ void unsettled_pair(const WorkDesc& wd, int sub, float ax, float ay, float az, float bx,
+                                               float by, float bz, uint32_t ig, uint32_t jg, const HistCol& hc) {
+    if (wd.chord_ok) {
+        const float e = fmaf(az, bz, fmaf(ay, by, fmaf(ax, bx, wd.neg_fast_t)));
+        const int ent = lut_entry(wd, e);
+        const float z = euclid_z(ax, ay, az, bx, by, bz);
+        const float* zlo = sptr<const float>(wd.off_zlo);
+        const float* zhi = sptr<const float>(wd.off_zhi);
+        int lo = lut_P(ent), hi = lut_Q(ent, wd.ne);
+        const int Q = hi;
+        while (lo < hi) {  // first m in [P, Q) with z < zhi[m]
+            const int mid = (lo + hi) >> 1;
+            if (z >= zhi[mid]) lo = mid + 1; else hi = mid;
+        }
+        if (lo == Q || z < zlo[lo]) {
+            hist_inc<T>(hc, lo);
+            return;
+        }
+    }
+    queue_pair<T>(wd, sub, ig, jg, hc);
+}
+
+// After a slow group: drain the warp's queue once it is half full.
+template <int T>
+__device__ __forceinline__ void maybe_drain(const WorkDesc& wd, int sub, const HistCol& hc) {
+    __syncwarp();
+    if (*sptr<volatile int>(queue_count_off(wd, (int)(threadIdx.x >> 5))) >= kQueuePerWarp / 2)
+        warp_drain_queue<T>(wd, sub, hc);
+}
+
+// Diagonal handling of a tile (warp-uniform): none, keep j > i, keep j != i.
+enum { kDiagNone = 0, kDiagAbove = 1, kDiagOffSelf = 2 };
+
+// Element k of a register array without dynamic indexing (no local memory).
+template <int R>
+__device__ __forceinline__ float pick(const float (&v)[R], int k) {
+    float x = v[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) x = (k == r) ? v[r] : x;
+    return x;
+}
+
+// Which pairs of a group may be counted: bit r * U + u for i-point r and
+// j-point u (sub-problem bounds, then the diagonal rule of the tile).
+template <int R, int U>
+__device__ __forceinline__ uint32_t valid_pairs(uint32_t ibase, uint32_t jg0, uint32_t na, uint32_t nb, int diag) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t ig = ibase + 32u * (uint32_t)r, jg = jg0 + (uint32_t)u;
+            bool ok = ig < na && jg < nb;
+            if (diag == kDiagAbove) ok = ok && jg > ig;
+            else if (diag == kDiagOffSelf) ok = ok && jg != ig;
+            v |= (ok ? 1u : 0u) << (r * U + u);
+        }
+    }
+    return v;
+}
+
+// ---- packed screen values of a group of U j-points (x | y | z arrays at j)
+// for R i-points held as (a, a) pairs: e[r][u] = fma(az,bz, fma(ay,by, fma(ax,bx, -T))).
+template <int R, int U>
+__device__ __forceinline__ void screen_group2(float (&e)[R][U], const u64 (&ax)[R], const u64 (&ay)[R],
+                                              const u64 (&az)[R], const float* sx, const float* sy,
+                                              const float* sz, int j, u64 nt2) {
+    static_assert(U == 2 || U == 4, "j-points per group");
+    if constexpr (U == 4) {
+        const ulonglong2 bx = *reinterpret_cast<const ulonglong2*>(sx + j);
+        const ulonglong2 by = *reinterpret_cast<const ulonglong2*>(sy + j);
+        const ulonglong2 bz = *reinterpret_cast<const ulonglong2*>(sz + j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const u64 v0 = ffma2(az[r], bz.x, ffma2(ay[r], by.x, ffma2(ax[r], bx.x, nt2)));
+            const u64 v1 = ffma2(az[r], bz.y, ffma2(ay[r], by.y, ffma2(ax[r], bx.y, nt2)));
+            e[r][0] = lo_of(v0);
+            e[r][1] = hi_of(v0);
+            e[r][2] = lo_of(v1);
+            e[r][3] = hi_of(v1);
+        }
+    } else {
+        const u64 bx = *reinterpret_cast<const u64*>(sx + j);
+        const u64 by = *reinterpret_cast<const u64*>(sy + j);
+        const u64 bz = *reinterpret_cast<const u64*>(sz + j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const u64 v0 = ffma2(az[r], bz, ffma2(ay[r], by, ffma2(ax[r], bx, nt2)));
+            e[r][0] = lo_of(v0);
+            e[r][1] = hi_of(v0);
+        }
+    }
+}
+
+// ---- packed 3-D screen values: e'[r][u] = fma(dz,dz, fma(dy,dy, fma(dx,dx, -H)))
+// with d = a - b, the negation of the fast test H - |a' - b'|^2: a pair can be
+// in range only where e' <= 0 (sign bit set or zero).
+template <int R, int U>
+__device__ __forceinline__ void euclid_group2(float (&e)[R][U], const u64 (&ax)[R], const u64 (&ay)[R],
+                                              const u64 (&az)[R], const float* sx, const float* sy,
+                                              const float* sz, int j, u64 nh2) {
+    static_assert(U == 2 || U == 4, "j-points per group");
+    constexpr int P = U / 2;
+    u64 bx[P], by[P], bz[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        bx[p] = *reinterpret_cast<const u64*>(sx + j + 2 * p);
+        by[p] = *reinterpret_cast<const u64*>(sy + j + 2 * p);
+        bz[p] = *reinterpret_cast<const u64*>(sz + j + 2 * p);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const u64 dx = fsub2(ax[r], bx[p]), dy = fsub2(ay[r], by[p]), dz = fsub2(az[r], bz[p]);
+            const u64 v = ffma2(dz, dz, ffma2(dy, dy, ffma2(dx, dx, nh2)));
+            e[r][2 * p] = lo_of(v);
+            e[r][2 * p + 1] = hi_of(v);
+        }
+    }
+}
+
+// Slow path of the angular screen for a group of U j (warp-uniform), all R
+// pairs of every lane, branch-free: the LUT cell of e is k = rne(sat(e *
+// 2^-q) * 2^14), read as the low bits of fma(v, 2^14, 2^23); a settled entry
+// is the pair's row, so the pair costs one shared load and one shared
+// reduction.  The loads of i-point r + 1 are issued before the reductions of
+// i-point r (shared loads and reductions stay in program order).  Pairs
+// beyond the range land in the skip code or (TPCF_F_CHECK_OVERFLOW) the
+// overflow row; on masked tiles, pairs that must not be counted (padding,
+// j <= i on the diagonal) are forced to the skip code.  Unsettled entries
+// (bit 31) go through unsettled_pair, one per iteration of the lane.
+template <int T, int R, int U, bool MASKED>
+__device__ __forceinline__ void slow_group(const WorkDesc& wd, int sub, const u64 (&ax2)[R], const u64 (&ay2)[R],
+                                           const u64 (&az2)[R], const float* sx, const float* sy, const float* sz,
+                                           int jj, uint32_t ibase, uint32_t jbase, int diag, uint32_t na,
+                                           uint32_t nb, const HistCol& hc) {
+    static_assert(U * R <= 32, "one bit per pair of the group");
+    float e[R][U];
+    screen_group2<R, U>(e, ax2, ay2, az2, sx, sy, sz, jj, pack2(wd.neg_fast_t, wd.neg_fast_t));
+    uint32_t valid = ~0u;
+    if constexpr (MASKED) valid = valid_pairs<R, U>(ibase, jbase + (uint32_t)jj, na, nb, diag);
+    const uint32_t lut_adj = smem_addr(dyn_smem) + wd.off_lut - 0x4B000000u * 2u;  // + 2 bits(f): entry
+    uint32_t ent[2][U];
+    uint32_t um = 0;  // unsettled pairs of this lane: pair k = r * U + u at bit U * R - 1 - k
+#pragma unroll
+    for (int r = 0; r < R + 1; ++r) {
+        if (r < R) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float v = __saturatef(e[r][u] * wd.lut_scale);
+                const float f = fmaf(v, 16384.0f, 8388608.0f);
+                asm volatile("ld.shared.s16 %0, [%1];" : "=r"(ent[r & 1][u]) : "r"(__float_as_uint(f) * 2u + lut_adj));
+            }
+        }
+        if (r >= 1) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t x = ent[(r - 1) & 1][u];
+                if constexpr (MASKED) x = ((valid >> ((r - 1) * U + u)) & 1u) ? x : kLutSkip;
+                // settled rows add one; skip and unsettled codes add nothing here
+                if (x < kLutRowLimit) red_add_shared(hc.addr + (x << row_shift<T>()), hc.inc);
+                um = __funnelshift_l(x, um, 1);  // (um << 1) | (x >> 31)
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, um != 0u)) {
+        float fx[R], fy[R], fz[R];  // the i-points as scalars (register halves)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            fx[r] = lo_of(ax2[r]);
+            fy[r] = lo_of(ay2[r]);
+            fz[r] = lo_of(az2[r]);
+        }
+        while (um) {  // one iteration per unsettled pair of the lane
+            const int k = U * R - 1 - (31 - __clz(um));
+            um &= ~(1u << (U * R - 1 - k));
+            const int r = k / U, u = k % U;
+            const int j = jj + u;
+            unsettled_pair<T>(wd, sub, pick(fx, r), pick(fy, r), pick(fz, r), sx[j], sy[j], sz[j],
+                              ibase + 32u * (uint32_t)r, jbase + (uint32_t)j, hc);
+        }
+    }
+}
+
+// Slow path of the 3-D variant for a group of U j: z = fl32(|a' - b'|^2) is
+// recomputed for all R pairs of every lane, its constant-ratio LUT cell gives
+// a settled row (one shared load, one reduction) or the edges left open,
+// which the z-space bounds decide inline or the binary64 recheck (queue)
+// settles.  Same load-before-reduction pipelining and masking as the angular
+// slow path.
+template <int T, int R, int U, bool MASKED>
+__device__ __forceinline__ void slow_group_euclid(const WorkDesc& wd, int sub, const u64 (&ax2)[R],
+                                                  const u64 (&ay2)[R], const u64 (&az2)[R], const float* sx,
+                                                  const float* sy, const float* sz, int jj, uint32_t ibase,
+                                                  uint32_t jbase, int diag, uint32_t na, uint32_t nb,
+                                                  const HistCol& hc) {
+    static_assert(U * R <= 32, "one bit per pair of the group");
+    const uint32_t lut_base = smem_addr(dyn_smem) + wd.off_lut;
+    float fx[R], fy[R], fz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        fx[r] = lo_of(ax2[r]);
+        fy[r] = lo_of(ay2[r]);
+        fz[r] = lo_of(az2[r]);
+    }
+    float bx[U], by[U], bz[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        bx[u] = sx[jj + u];
+        by[u] = sy[jj + u];
+        bz[u] = sz[jj + u];
+    }
+    uint32_t valid = ~0u;
+    if constexpr (MASKED) valid = valid_pairs<R, U>(ibase, jbase + (uint32_t)jj, na, nb, diag);
+    uint32_t ent[2][U];
+    uint32_t um = 0;  // unsettled pairs of this lane: pair k = r * U + u at bit U * R - 1 - k
+#pragma unroll
+    for (int r = 0; r < R + 1; ++r) {
+        if (r < R) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float z = euclid_z(fx[r], fy[r], fz[r], bx[u], by[u], bz[u]);
+                asm volatile("ld.shared.s16 %0, [%1];" : "=r"(ent[r & 1][u]) : "r"(euclid_cell_addr(wd, z, lut_base)));
+            }
+        }
+        if (r >= 1) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t x = ent[(r - 1) & 1][u];
+                if constexpr (MASKED) x = ((valid >> ((r - 1) * U + u)) & 1u) ? x : kLutSkip;
+                if (x < kLutRowLimit) red_add_shared(hc.addr + (x << row_shift<T>()), hc.inc);
+                um = __funnelshift_l(x, um, 1);
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, um != 0u)) {
+        while (um) {  // one iteration per unsettled pair of the lane
+            const int k = U * R - 1 - (31 - __clz(um));
+            um &= ~(1u << (U * R - 1 - k));
+            const int r = k / U, u = k % U;
+            const uint32_t ig = ibase + 32u * (uint32_t)r, jg = jbase + (uint32_t)(jj + u);
+            const float z = euclid_z(pick(fx, r), pick(fy, r), pick(fz, r), sx[jj + u], sy[jj + u], sz[jj + u]);
+            const int x = ld_shared_s16(euclid_cell_addr(wd, z, lut_base));
+            int lo = 0, hi = 0;
+            const int h = euclid_resolve(wd, z, x, &lo, &hi);
+            if (h >= 0) hist_inc<T>(hc, h);
+            else queue_pair<T>(wd, sub, ig, jg, hc);
+        }
+    }
+}
+
+// ============================================================== spatial pruning
+// Every point p of a group lies within radius r of the group's centre c
+// (bounding spheres from prep_caps_kernel, in the catalog's scaled space).  By
+// the triangle inequality, any pair (a, b) of two groups is at least
+// |cA - cB| - rA - rB apart; when that gap exceeds prune_thr (the host's
+// bound: every pair that far apart is overflow), the block is skipped.  The
+// FP32 evaluation here under-estimates the gap (relative margin 2^-20 on the
+// centre distance and on the radii, far above the few-ulp rounding of these
+// FP32 operations).
+constexpr float kPruneMargin = 9.5367431640625e-07f;  // 2^-20
+
+__device__ __forceinline__ bool prune_block(const WorkDesc& wd, const float4& ic, const float4& jc) {
+    const float dx = ic.x - jc.x, dy = ic.y - jc.y, dz = ic.z - jc.z;
+    const float D = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+    const float L = D * (1.0f - kPruneMargin) - (ic.w + jc.w) * (1.0f + kPruneMargin);
+    return L > wd.prune_thr;
+}
+
+// The sphere of a warp's 32 R i-points (R / 4 consecutive groups): centre the
+// FP32 mean of the groups' centres, radius max_k |c - c_k| + r_k (enlarged by
+// 2^-20 relative); empty groups (radius -1e30) are left out.
+template <int R>
+__device__ __forceinline__ float4 warp_sphere(const float4* caps) {
+    static_assert((32 * R) % kCapPoints == 0, "whole groups per warp");
+    constexpr int K = 32 * R / kCapPoints;
+    float4 g[K];
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        g[k] = __ldg(caps + k);
+        if (g[k].w > -1e29f) {
+            sx += g[k].x;
+            sy += g[k].y;
+            sz += g[k].z;
+            ++cnt;
+        }
+    }
+    if (cnt == 0) return make_float4(0.f, 0.f, 0.f, -1e30f);
+    const float inv = 1.0f / (float)cnt;
+    const float cx = sx * inv, cy = sy * inv, cz = sz * inv;
+    float r = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (g[k].w > -1e29f) {
+            const float dx = cx - g[k].x, dy = cy - g[k].y, dz = cz - g[k].z;
+            r = fmaxf(r, sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) + g[k].w);
+        }
+    }
+    return make_float4(cx, cy, cz, r * (1.0f + kPruneMargin));
+}
+
+struct PruneSlot {
+    float4 sphere;          // the warp's i-points
+    const float4* b_caps;   // spheres of the current sub-problem's B
+    unsigned long long pruned;  // pair slots skipped by this warp
+};
+static_assert(sizeof(PruneSlot) == kPruneSlotBytes, "prune slot layout");
+
+// One pruning test for the warp's i-points against the kCapPoints-point group
+// holding j-point jg0 of B (warp-uniform); lane 0 counts the skipped slots.
+__device__ __forceinline__ bool prune_chunk(const WorkDesc& wd, uint32_t jg0, uint32_t slots) {
+    PruneSlot* ps = sptr<PruneSlot>(wd.off_icap + (threadIdx.x >> 5) * kPruneSlotBytes);
+    const float4 ic = ps->sphere;
+    const float4 jc = __ldg(ps->b_caps + jg0 / kCapPoints);
+    if (!prune_block(wd, ic, jc)) return false;
+    if ((threadIdx.x & 31) == 0) ps->pruned += slots;
+    return true;
+}
+
+// ============================================================== the counting kernel
+// T threads, R i-points per thread, MODE: KernelMode.
+//
+// Every warp is a worker of its own: it draws items (its 32 R i-points x a
+// j-chunk) from the launch's counter and streams their j-tiles through its
+// own ring of S shared-memory stages; tile seq of the warp lives in stage
+// seq % S, whose full mbarrier completes when the tile's TMA bulk copies land
+// (the stage record says which item and tile it holds).  Lane 0 refills a
+// stage with tile seq + S as soon as the warp has finished tile seq.  Warps
+// share only read-only block data (bins, LUT) and the words of their 16-bit
+// counters (two threads' halves each, updated atomically), so none ever
+// waits for another.  Every wait is bounded; a timeout sets the block's abort
+// word and the call's error word, after which no copy is issued, warps leave
+// their loops and each waits (bounded) for its own copies in flight.
+template <int T, int R, int MODE>
+__global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ WorkDesc wd) {
+    constexpr bool PLAIN = MODE == kModePlain;
+    constexpr bool EUCLID = MODE == kModeEuclid;
+    constexpr int W = T / 32;
+    constexpr int U = 32 / R;          // j-points per group (screen kernels)
+    constexpr uint32_t IB = 32u * R;   // i-points per warp item
+    const uint32_t S = wd.stages;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    volatile int* ctl = sptr<volatile int>(wd.off_ctl);
+    const bool check = (wd.flags & TPCF_F_CHECK_OVERFLOW) != 0;
+
+    // ---- block set-up: control words, counters, bins, barriers (all sub-problems share the bins)
+    for (int k = tid; k < kCtlWords; k += T) ctl[k] = 0;
+    if (tid < W) sptr<PruneSlot>(wd.off_icap + (uint32_t)tid * kPruneSlotBytes)->pruned = 0ull;
+    {
+        uint32_t* hist = sptr<uint32_t>(wd.off_hist);
+        for (int k = tid; k < (wd.nedges_max + 1) * (T / 2); k += T) hist[k] = 0;
+    }
+    load_bins<T>(sub_of(wd, 0).bins, wd, PLAIN);
+    uint64_t* bars = sptr<uint64_t>(wd.off_bars) + (uint32_t)warp * S;
+    TileMeta* meta = sptr<TileMeta>(wd.off_meta) + (uint32_t)warp * S;
+    const uint32_t stage_base = wd.off_stage + (uint32_t)warp * S * wd.stage_bytes;
+    if (lane == 0) {
+        for (uint32_t s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const HistCol hc = hist_col<T>(wd);
+
+    // Lane 0 copies the tile at cursor p into stage seq % S and records it there.
+    auto issue = [&](uint32_t seq, const Cursor& p) {
+        if (lane != 0) return;
+        if ((wd.flags & TPCF_F_TEST_WAIT_TIMEOUT) && seq == 0) return;  // test hook: never issued
+        const uint32_t s = seq % S;
+        const SubProblem& sp = sub_of(wd, p.sub);
+        const uint32_t jbase = p.g.j0 + p.t * wd.J;
+        meta[s] = TileMeta{p.q, p.t};
+        unsigned char* dst = sptr<unsigned char>(stage_base + s * wd.stage_bytes);
+        fence_proxy_async_smem();  // the warp's reads of the stage's previous tile come first
+        mbar_expect_tx(&bars[s], wd.stage_bytes);
+        if constexpr (PLAIN) {
+            bulk_copy_g2s(dst, sp.b64 + jbase, wd.stage_bytes, &bars[s]);
+        } else {
+            const uint32_t plane = wd.J * 4u;  // x | y | z arrays of J floats
+            bulk_copy_g2s(dst, sp.b_soa + jbase, plane, &bars[s]);
+            bulk_copy_g2s(dst + plane, sp.b_soa + sp.b_soa_stride + jbase, plane, &bars[s]);
+            bulk_copy_g2s(dst + 2 * plane, sp.b_soa + 2ull * sp.b_soa_stride + jbase, plane, &bars[s]);
+        }
+    };
+
+    // ---- prologue: the first S tiles of the warp
+    Cursor prod;
+    draw_next(wd, prod);
+    uint32_t issued = 0;
+    for (; issued < S && prod.valid; ++issued) {
+        issue(issued, prod);
+        advance(wd, prod);
+    }
+
+    // ---- consumer state
+    int cur_sub = -1;
+    uint32_t cur_q = 0xffffffffu;
+    ItemGeom g{};
+    unsigned long long* cur_hist = nullptr;  // the histogram this warp's counters belong to
+    uint32_t j_since_flush = 0;
+    u64 ax2[PLAIN ? 1 : R], ay2[PLAIN ? 1 : R], az2[PLAIN ? 1 : R];
+    double dx[PLAIN ? R : 1], dy[PLAIN ? R : 1], dz[PLAIN ? R : 1];
+    uint32_t ibase = 0;
+    bool aborted = false;
+
+    uint32_t seq = 0;
+    for (; seq < issued; ++seq) {
+        // ---- wait for tile seq
+        const uint32_t s = seq % S;
+        const bool ok = mbar_wait_bounded(&bars[s], (seq / S) & 1u, wd.wait_limit_ns);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (lane == 0) {
+                ctl[kCtlAbort] = 1;
+                atomicOr(wd.stats + kStatError, (unsigned long long)kErrWaitTimeout);
+            }
+            aborted = true;
+            break;
+        }
+        if (ctl[kCtlAbort]) { aborted = true; break; }
+        const volatile TileMeta* vm = meta + s;
+        const TileMeta tm{vm->q, vm->t};
+
+        if (tm.q != cur_q) {
+            // ---- a new item (warp-uniform)
+            Cursor c;
+            load_item(wd, tm.q, c);
+            const SubProblem& sp = sub_of(wd, c.sub);
+            unsigned long long* tgt = sp.hist;
+            if (sp.row_seg) tgt += (size_t)__ldg(sp.row_seg + c.g.i0 / kSegAlign) * sp.row_stride;
+            if (c.sub != cur_sub || tgt != cur_hist) {
+                if (cur_sub >= 0) {
+                    // queued pairs belong to the previous sub-problem and histogram
+                    if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
+                    if (tgt != cur_hist) {
+                        warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
+                        j_since_flush = 0;
+                    }
+                }
+                cur_sub = c.sub;
+                cur_hist = tgt;
+            }
+            cur_q = tm.q;
+            g = c.g;
+            if (lane == 0)
+                atomicAdd(wd.stats + kStatPairs,
+                          (unsigned long long)item_pairs(g, sp.na, sp.nb, sp.auto_mode != 0, wd.I, wd.Jc));
+            ibase = g.i0 + (uint32_t)lane;
+            if (wd.prune) {
+                const float4 sph = warp_sphere<R>(sp.a_caps + g.i0 / kCapPoints);
+                if (lane == 0) {
+                    PruneSlot* ps = sptr<PruneSlot>(wd.off_icap + (uint32_t)warp * kPruneSlotBytes);
+                    ps->sphere = sph;
+                    ps->b_caps = sp.b_caps;
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t i = ibase + 32u * r;
+                if constexpr (PLAIN) {
+                    const Point64 p = ldg_point(sp.a64 + i);
+                    dx[r] = p.x;
+                    dy[r] = p.y;
+                    dz[r] = p.z;
+                } else {
+                    const float4 p = __ldg(sp.a32 + i);
+                    ax2[r] = pack2(p.x, p.x);
+                    ay2[r] = pack2(p.y, p.y);
+                    az2[r] = pack2(p.z, p.z);
+                }
+            }
+        }
+
+        // ---- merge the 16-bit counters before any can wrap: a lane adds at most
+        // R per j to one row, plus at most 2 per queue drain (at most one drain
+        // per slow group), so merging every flush_limit j-points keeps every
+        // counter below 2^16
+        if (j_since_flush + wd.J > wd.flush_limit) {
+            if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
+            warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
+            j_since_flush = 0;
+        }
+        j_since_flush += wd.J;
+
+        const SubProblem& sp = sub_of(wd, cur_sub);
+        const uint32_t na = sp.na, nb = sp.nb;
+        const uint32_t jbase = g.j0 + tm.t * wd.J;
+        const int J = (int)wd.J;
+        // tiles that meet the diagonal: j > i (auto counts) or j != i (full square without self pairs)
+        int diag = kDiagNone;
+        if (jbase < g.i0 + IB) {
+            if (sp.auto_mode) diag = kDiagAbove;
+            else if (sp.no_self && jbase + wd.J > g.i0) diag = kDiagOffSelf;
+        }
+        // tiles holding padding (points past na or nb) are masked where padding could
+        // look in range (need_idx) and whenever overflow is counted
+        const bool edge = jbase + wd.J > nb || g.i0 + IB > na;
+        const bool masked = diag != kDiagNone || (edge && (wd.need_idx || check));
+        const uint32_t stage_off = stage_base + s * wd.stage_bytes;
+
+        if constexpr (PLAIN) {
+            const Point64* sj = sptr<const Point64>(stage_off);
+            const double* cthr = sptr<const double>(wd.off_cthr);
+            const int ne = wd.ne;
+            for (int jj = 0; jj < J; ++jj) {
+                const Point64 b = sj[jj];
+                const uint32_t jg = jbase + (uint32_t)jj;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t ig = ibase + 32u * r;
+                    const bool valid = ig < na && jg < nb && (!masked || (diag == kDiagAbove ? jg > ig
+                                                                          : (diag == kDiagOffSelf ? jg != ig : true)));
+                    if (wd.euclid) {
+                        // 3-D: h = number of edges m with d^2 >= S_m (S increasing); d^2 >= S_B is overflow
+                        const double ex = __dsub_rn(dx[r], b.x), ey = __dsub_rn(dy[r], b.y), ez = __dsub_rn(dz[r], b.z);
+                        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+                        if (d2 < wd.cos_last && valid) {
+                            int lo = 0, hi = ne;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (d2 >= cthr[mid]) lo = mid + 1; else hi = mid;
+                            }
+                            hist_inc<T>(hc, lo);
+                        } else if (check && valid) {
+                            hist_inc<T>(hc, ne);
+                        }
+                        continue;
+                    }
+                    const double d = __dadd_rn(__dadd_rn(__dmul_rn(dx[r], b.x), __dmul_rn(dy[r], b.y)),
+                                               __dmul_rn(dz[r], b.z));
+                    if (d > wd.cos_last && valid) {
+                        // h = number of edges m with d <= C_m (C decreasing)
+                        int lo = 0, hi = ne;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (cthr[mid] >= d) lo = mid + 1; else hi = mid;
+                        }
+                        hist_inc<T>(hc, lo);
+                    } else if (check && valid) {
+                        hist_inc<T>(hc, ne);
+                    }
+                }
+            }
+        } else {
+            // Fast loop: the screen values of a group of U j-points and the lane's R
+            // i-points (packed FMA); one bit per group says whether some pair of the
+            // lane may be in range (angles: some e >= 0; 3-D: some e' <= 0).  The loop
+            // does not branch per group: after kMaskGroups groups one warp reduction
+            // names the groups that take the slow path, which recomputes their values.
+            const float* sx = sptr<const float>(stage_off);
+            const float* sy = sx + J;
+            const float* sz = sy + J;
+            // angles: -T; 3-D: -H (the host passes +H for the 3-D variant)
+            const float t0 = EUCLID ? -wd.neg_fast_t : wd.neg_fast_t;
+            const u64 nt2 = pack2(t0, t0);
+            constexpr int CH = kMaskGroups * U;                     // j-points per mask chunk
+            static_assert(kMaskGroups <= 32, "one mask bit per group");
+#pragma unroll 1
+            for (int jc = 0; jc < J; jc += CH) {
+                if (wd.prune && prune_chunk(wd, jbase + (uint32_t)jc, IB * CH)) continue;
+                uint32_t lane_mask = 0;
+#pragma unroll 4
+                for (int gi = 0; gi < kMaskGroups; ++gi) {
+                    float e[R][U];
+                    if constexpr (EUCLID) {
+                        euclid_group2<R, U>(e, ax2, ay2, az2, sx, sy, sz, jc + gi * U, nt2);
+                        // OR of the sign bits: 1 when some e' <= 0 (e' = -0 cannot occur)
+                        lane_mask = __funnelshift_l(lop_tree<U * R, true>(reinterpret_cast<const uint32_t*>(&e[0][0])),
+                                                    lane_mask, 1);
+                    } else {
+                        screen_group2<R, U>(e, ax2, ay2, az2, sx, sy, sz, jc + gi * U, nt2);
+                        // (~AND) >> 31: 1 when some screen value of the group is >= 0
+                        lane_mask = __funnelshift_l(~lop_tree<U * R, false>(reinterpret_cast<const uint32_t*>(&e[0][0])),
+                                                    lane_mask, 1);
+                    }
+                }
+                uint32_t m = __reduce_or_sync(0xffffffffu, lane_mask);  // bit kMaskGroups - 1 - gi: group gi
+                if (check) {
+                    // overflow counted: the lane's pairs of every group the fast loop
+                    // rejected are overflow; masked tiles take every group slowly
+                    if (masked) m = 0xffffffffu;
+                    const uint32_t nfast = (uint32_t)kMaskGroups - (uint32_t)__popc(m);
+                    if (nfast) red_add_shared(hc.addr + ((uint32_t)wd.ne << row_shift<T>()), hc.inc * nfast * (uint32_t)(U * R));
+                }
+#pragma unroll 1
+                while (m) {
+                    const int gi = kMaskGroups - __ffs(m);  // lowest set bit first
+                    m &= m - 1u;
+                    const int jj = jc + gi * U;
+                    if constexpr (EUCLID) {
+                        if (masked) slow_group_euclid<T, R, U, true>(wd, cur_sub, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc);
+                        else slow_group_euclid<T, R, U, false>(wd, cur_sub, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc);
+                    } else {
+                        if (masked) slow_group<T, R, U, true>(wd, cur_sub, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc);
+                        else slow_group<T, R, U, false>(wd, cur_sub, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc);
+                    }
+                    maybe_drain<T>(wd, cur_sub, hc);
+                }
+            }
+        }
+
+        // ---- refill this stage with tile seq + S
+        __syncwarp();
+        if (prod.valid && !ctl[kCtlAbort]) {
+            issue(seq + S, prod);
+            ++issued;
+            advance(wd, prod);
+        }
+    }
+
+    // ---- merge this warp's columns (skipped after an abort: outputs are invalid)
+    if (!aborted && cur_sub >= 0) {
+        if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
+        warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
+    }
+    if (wd.prune && lane == 0) {
+        const unsigned long long np = sptr<PruneSlot>(wd.off_icap + (uint32_t)warp * kPruneSlotBytes)->pruned;
+        if (np) atomicAdd(wd.stats + kStatPruned, np);
+    }
+    // ---- after an abort, wait (bounded) for this warp's copies still in flight
+    if (aborted && lane == 0) {
+        for (uint32_t s2 = seq; s2 < issued; ++s2) {
+            if ((wd.flags & TPCF_F_TEST_WAIT_TIMEOUT) && s2 == 0) continue;
+            (void)mbar_wait_bounded(&bars[s2 % S], (s2 / S) & 1u, wd.wait_limit_ns);
+        }
+    }
+}
+
+// ============================================================== finalize
+// out[h] = acc[h] for h < nedges (underflow and bins).  Overflow: without
+// count_over, out[nedges] = total - sum, or UINT64_MAX (and kErrBadHist in the
+// error word) when the sum exceeds the total; with count_over (the kernel
+// counted it), out[nedges] = acc[nedges] and the whole sum must equal the
+// total (else kErrBadHist and overflow UINT64_MAX).  acc and out may alias.
+__device__ void finalize_one(const unsigned long long* acc, int nedges, unsigned long long* out,
+                             unsigned long long total, int count_over, unsigned long long* err_word,
+                             unsigned long long* part) {
+    const int nsum = count_over ? nedges + 1 : nedges;
+    unsigned long long s = 0;
+    for (int h = threadIdx.x; h < nsum; h += blockDim.x) s += acc[h];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    const unsigned long long sum = part[0];
+    const unsigned long long over = count_over ? acc[nedges] : 0ull;
+    __syncthreads();  // every thread has read acc before out (possibly the same memory) is written
+    for (int h = threadIdx.x; h < nedges; h += blockDim.x) out[h] = acc[h];
+    if (threadIdx.x == 0) {
+        const bool bad = count_over ? sum != total : sum > total;
+        if (bad) {
+            atomicOr(err_word, (unsigned long long)kErrBadHist);
+            out[nedges] = ~0ull;  // sentinel
+        } else {
+            out[nedges] = count_over ? over : total - sum;
+        }
+    }
+}
+
+__global__ void finalize_kernel(unsigned long long* acc, int nedges, unsigned long long* out,
+                                unsigned long long total, int count_over, unsigned long long* err_word) {
+    __shared__ unsigned long long part[256];
+    finalize_one(acc, nedges, out, total, count_over, err_word, part);
+}
+
+// Batched finalize: block b turns accumulator row b (stride acc_stride words)
+// into histogram b of `out` (stride out_stride words) with pair total totals[b].
+__global__ void finalize_batch_kernel(const unsigned long long* acc, int acc_stride, int nedges,
+                                      unsigned long long* out, int out_stride, const unsigned long long* totals,
+                                      int count_over, unsigned long long* err_word) {
+    __shared__ unsigned long long part[256];
+    finalize_one(acc + (size_t)blockIdx.x * acc_stride, nedges, out + (size_t)blockIdx.x * out_stride,
+                 totals[blockIdx.x], count_over, err_word, part);
+}
+
+cudaError_t launch_finalize_batch(const unsigned long long* acc, int acc_stride, int nedges,
+                                  unsigned long long* out, int out_stride, const unsigned long long* totals,
+                                  int count, int count_over, unsigned long long* err_word, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    finalize_batch_kernel<<<count, 256, 0, stream>>>(acc, acc_stride, nedges, out, out_stride, totals, count_over,
+                                                     err_word);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long long* out,
+                            unsigned long long total, int count_over, unsigned long long* err_word,
+                            cudaStream_t stream) {
+    finalize_kernel<<<1, 256, 0, stream>>>(acc, nedges, out, total, count_over, err_word);
+    return cudaGetLastError();
+}
+
+// ============================================================== launchers
+// Fills the block constants of the work description (shared-memory offsets of
+// the shape, merge interval) and launches.
+template <int T, int R, int MODE>
+static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t stream) {
+    WorkDesc wd = wd_in;
+    const SmemLayout L = smem_layout(MODE, T, (int)wd.J, (int)wd.stages, wd.nedges_max);
+    wd.off_ctl = L.ctl;
+    wd.off_bars = L.bars;
+    wd.off_meta = L.meta;
+    wd.off_stage = L.stage;
+    wd.off_hist = L.hist;
+    wd.off_cthr = L.cos_thr;
+    wd.off_lo = L.lo;
+    wd.off_hi = L.hi;
+    wd.off_c32 = L.cos32;
+    wd.off_zlo = L.zlo;
+    wd.off_zhi = L.zhi;
+    wd.off_lut = L.lut;
+    wd.off_queue = L.queue;
+    wd.off_icap = L.icap;
+    wd.stage_bytes = wd.J * staged_point_bytes(MODE);
+    // 16-bit counters: a lane adds at most R per j to one row plus at most 2 per
+    // queue drain (at most one drain per slow group of 32 / R j-points), so
+    // merging every 65535 / (R + 2) - J j-points (checked per tile) keeps every
+    // counter below 2^16
+    wd.flush_limit = 0xffffu / (uint32_t)(R + 2) - wd.J;
+    if (L.total > sh.smem || wd.I != 32u * (uint32_t)R) return cudaErrorInvalidValue;
+    count_kernel<T, R, MODE><<<sh.blocks, T, sh.smem, stream>>>(wd);
+    return cudaGetLastError();
+}
+
+// The limit is raised to the device's opt-in maximum rather than to `bytes`:
+// the attribute belongs to the kernel, not to a launch, so a smaller value set
+// by one host thread could otherwise undercut a concurrent launch of another.
+template <int T, int R, int MODE>
+static cudaError_t set_smem_t(size_t bytes) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > (size_t)optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(count_kernel<T, R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+#define TPCF_SHAPES(X) X(128, 8) X(256, 8) X(512, 8) X(256, 16)
+
+cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int mode, int nedges, cudaStream_t stream) {
+    (void)nedges;
+#define X(T_, R_)                                                                      \
+    if (sh.threads == T_ && sh.ipt == R_) {                                            \
+        if (mode == kModePlain) return launch_t<T_, R_, kModePlain>(wd, sh, stream);   \
+        if (mode == kModeEuclid) return launch_t<T_, R_, kModeEuclid>(wd, sh, stream); \
+        return launch_t<T_, R_, kModeScreen>(wd, sh, stream);                          \
+    }
+    TPCF_SHAPES(X)
+#undef X
+    return cudaErrorInvalidConfiguration;
+}
+
+cudaError_t count_set_smem_limit(int mode, int threads, int ipt, size_t bytes) {
+#define X(T_, R_)                                                              \
+    if (threads == T_ && ipt == R_) {                                          \
+        if (mode == kModePlain) return set_smem_t<T_, R_, kModePlain>(bytes);  \
+        if (mode == kModeEuclid) return set_smem_t<T_, R_, kModeEuclid>(bytes); \
+        return set_smem_t<T_, R_, kModeScreen>(bytes);                         \
+    }
+    TPCF_SHAPES(X)
+#undef X
+    return cudaErrorInvalidConfiguration;
+}
+
+bool count_shape_supported(int threads, int ipt) {
+#define X(T_, R_) if (threads == T_ && ipt == R_) return true;
+    TPCF_SHAPES(X)
+#undef X
+    return false;
+}
+
+size_t count_smem_bytes(int mode, int threads, int ipt, int jtile, int stages, int nedges) {
+    (void)ipt;
+    return smem_layout(mode, threads, jtile, stages, nedges).total;
+}
+
+}  // namespace tpcf

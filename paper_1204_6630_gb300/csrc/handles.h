@@ -68,7 +68,7 @@ struct tpcf_catalog {
     uint32_t n_pad = 0;
     tpcf::Point64* d64 = nullptr;
     float4* d32 = nullptr;
-    float4* d32x2 = nullptr;        // (x,x,y,y),(z,z,0,0) per point for the packed screen
+    float* soa = nullptr;           // FP32 points as x | y | z arrays of n_pad floats (the staged j-tiles)
     float4* caps = nullptr;         // bounding sphere of each kCapPoints-point group (spatial pruning)
     std::vector<uint64_t> offsets;  // segments (empty = one segment), input order
     std::vector<uint64_t> seg_start;  // device position of each segment's first point (multiples of

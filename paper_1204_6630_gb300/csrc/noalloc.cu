@@ -154,7 +154,7 @@ extern "C" int tpcf_count_auto_noalloc(const double* xyz_dev, uint64_t n, const 
     const unsigned long long total = (unsigned long long)n * (n ? n - 1 : 0) / 2;
     if (cudaMemsetAsync(acc + kNoAllocWords - 1, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return TPCF_ECUDA;
-    if (launch_finalize(acc, nedges, (unsigned long long*)hist_dev, total, acc + kNoAllocWords - 1, st) !=
+    if (launch_finalize(acc, nedges, (unsigned long long*)hist_dev, total, 0, acc + kNoAllocWords - 1, st) !=
         cudaSuccess)
         return TPCF_ECUDA;
     return TPCF_OK;

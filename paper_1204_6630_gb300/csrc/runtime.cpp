@@ -572,7 +572,9 @@ static int euclid_set(tpcf_ctx* ctx, tpcf_bins* b, int key, const tpcf::BinsDev*
         }
         const double SB = b->cos_thr[ne - 1];
         const double zmax = std::pow(std::sqrt(SB * (1.0 + 1e-15)) + 2.001 * u * M, 2) * (1.0 + 2.01 * u);
-        const float H = round_up_f32(zmax * (1.0 + 6.1 * u) + 1e-300);
+        // (at least 2^-100: then an in-range pair's fast-test value H - z', which
+        // exceeds 3u H, is a positive normal float, never zero)
+        const float H = round_up_f32(std::max(zmax * (1.0 + 6.1 * u) + 1e-300, 0x1p-100));
         // LUT: cells of constant ratio from zmin = min S / 64 up past 2 H
         int32_t b0;
         int shift;
@@ -660,7 +662,7 @@ extern "C" int tpcf_bins_destroy(tpcf_bins* b) { return bins_destroy_impl(b); }
 // ====================================================================== catalogs
 size_t tpcf::catalog_bytes(uint64_t n) {
     const uint64_t n_pad = ((n + kPad - 1) / kPad + 1) * kPad;
-    return (size_t)n_pad * (sizeof(Point64) + 3 * sizeof(float4));
+    return (size_t)n_pad * (sizeof(Point64) + sizeof(float4) + 3 * sizeof(float));
 }
 
 int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int where, const uint64_t* offsets,
@@ -732,7 +734,7 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
     };
     if (alloc((void**)&c->d64, (size_t)c->n_pad * sizeof(Point64)) != cudaSuccess ||
         alloc((void**)&c->d32, (size_t)c->n_pad * sizeof(float4)) != cudaSuccess ||
-        alloc((void**)&c->d32x2, (size_t)c->n_pad * 2 * sizeof(float4)) != cudaSuccess ||
+        alloc((void**)&c->soa, (size_t)c->n_pad * 3 * sizeof(float)) != cudaSuccess ||
         alloc((void**)&c->caps, (size_t)(c->n_pad / kCapPoints) * sizeof(float4)) != cudaSuccess)
         return fail_with(TPCF_ENOMEM, "device allocation failed");
     const double* in = xyz;
@@ -775,7 +777,7 @@ int tpcf::catalog_create_impl(tpcf_ctx* ctx, const double* xyz, uint64_t n, int 
     }
     uint32_t nl = 0;
     cudaError_t e = launch_prepare(in, (uint32_t)n, seg, seg_delta, sort ? 1 : 0, euclid ? 1 : 0, err + 2, c->d64,
-                                   c->d32, c->d32x2, c->caps, c->n_pad, keys, vals, n_pow2, err, err + 1, st, &nl);
+                                   c->d32, c->soa, c->caps, c->n_pad, keys, vals, n_pow2, err, err + 1, st, &nl);
     ctx->launches.fetch_add(nl);
     if (e != cudaSuccess) return fail_with(TPCF_ECUDA, cudaGetErrorString(e));
     unsigned long long hw[2] = {0, 0};
@@ -821,7 +823,7 @@ extern "C" int tpcf_catalog_create_3d(tpcf_ctx* ctx, const double* xyz, uint64_t
 int tpcf::catalog_destroy_impl(tpcf_catalog* c) {
     if (!c) return TPCF_EINVAL;
     cudaSetDevice(c->ctx->cfg.device);
-    void* bufs[5] = {c->d64, c->d32, c->d32x2, c->seg_of_block, c->caps};
+    void* bufs[5] = {c->d64, c->d32, c->soa, c->seg_of_block, c->caps};
     if (c->stream_ordered) {
         for (void* p : bufs)
             if (p) cudaFreeAsync(p, c->free_stream);
@@ -855,28 +857,28 @@ struct SubSpec {
 
 int kernel_mode(const tpcf_config& cfg, bool euclid) {
     if (cfg.precision == TPCF_PLAIN_FP64) return kModePlainFP64;
-    if (euclid) return kModeEuclidScreen;
-    return (cfg.flags & TPCF_F_PACKED_FMA) ? kModeScreenPacked : kModeScreenScalar;
+    return euclid ? kModeEuclidScreen : kModeScreenScalar;
 }
 
-// Shape for T threads x R i-points, j-tile J (0: default) and S stages (0:
-// deepest that fits); false when it does not fit shared memory.
+// Shape for T threads x R i-points, j-tile J (0: default) and S stages per
+// warp (0: default); false when it does not fit shared memory.  Every warp
+// works on items of its own 32 R i-points x Jc = 4096 j-points, streamed in
+// tiles of J j-points through a ring of S stages.
 bool shape_for(tpcf_ctx* ctx, int mode, int nedges, int T, int R, int Jreq, int Sreq, Shape* sh) {
     if (!count_shape_supported(T, R)) return false;
-    const int I = T * R;
-    int J = Jreq ? Jreq : 1024;
-    if (J > I) J = I;
-    // (a tile is a whole number of the fast loop's 32-group mask chunks: 128 j)
-    if ((int)kPad % J != 0 || (int)kPad % I != 0 || J % 128 != 0 || I % J != 0) return false;
-    // six stages by default: warps drift apart by up to five tiles before the
-    // fastest waits for a stage the slowest still reads (measured: 374 ms vs
-    // 380 ms with four at the 1M + 1M octant workload)
-    constexpr int kDefaultStages = 6;
-    int S = Sreq ? Sreq : kDefaultStages;
+    const int I = 32 * R;
+    constexpr int kChunk = 4096;
+    // two stages of 256 j-points by default (a warp's tile of 256 x 256 pairs takes
+    // tens of microseconds, its copy from L2 about one: double buffering hides it);
+    // the all-binary64 kernel stages 32-byte points in tiles of 128
+    int J = Jreq ? Jreq : (mode == kModePlainFP64 ? 128 : 256);
+    // (a tile is a whole number of the fast loop's mask chunks and of 128-point pruning groups)
+    if ((int)kPad % J != 0 || J % 128 != 0 || kChunk % J != 0 || kChunk % I != 0) return false;
+    int S = Sreq ? Sreq : 2;
     if (S < 2 || S > 16) return false;
     size_t smem = count_smem_bytes(mode, T, R, J, S, nedges);
-    while (smem > ctx->smem_optin && ((S > 2 && Sreq == 0) || (J > 256 && Jreq == 0))) {
-        if (S > 2 && Sreq == 0) --S; else { J /= 2; S = Sreq ? Sreq : kDefaultStages; }
+    while (smem > ctx->smem_optin && J > 128 && Jreq == 0) {
+        J /= 2;
         smem = count_smem_bytes(mode, T, R, J, S, nedges);
     }
     if (smem > ctx->smem_optin) return false;
@@ -886,7 +888,7 @@ bool shape_for(tpcf_ctx* ctx, int mode, int nedges, int T, int R, int Jreq, int 
     sh->stages = S;
     sh->smem = smem;
     sh->blocks = ctx->num_sms;  // one persistent block per SM
-    sh->jchunk = I;
+    sh->jchunk = kChunk;
     return true;
 }
 
@@ -928,7 +930,7 @@ uint64_t range_pairs(const SubProblem& sp, uint64_t lo, uint64_t hi, uint32_t I,
 // histogram); returns the number of items.
 uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const BinsDev* bins_dev, const Shape& sh,
                     unsigned long long* acc, size_t acc_stride, std::vector<SubProblem>& subs) {
-    const uint32_t I = (uint32_t)(sh.threads * sh.ipt), Jc = (uint32_t)sh.jchunk;
+    const uint32_t I = 32u * (uint32_t)sh.ipt, Jc = (uint32_t)sh.jchunk;
     subs.assign(nsub, SubProblem());
     uint64_t items = 0;
     size_t hist_base = 0;
@@ -938,7 +940,8 @@ uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const BinsDev
         memset(&sp, 0, sizeof sp);
         sp.a32 = p.a->d32 + p.a_off;
         sp.b32 = p.b->d32 + p.b_off;
-        sp.b32x2 = p.b->d32x2 + 2ull * p.b_off;
+        sp.b_soa = p.b->soa + p.b_off;
+        sp.b_soa_stride = p.b->n_pad;
         sp.a64 = p.a->d64 + p.a_off;
         sp.b64 = p.b->d64 + p.b_off;
         sp.a_caps = p.a->caps + p.a_off / kCapPoints;  // sub-ranges start on kSegAlign boundaries
@@ -1029,11 +1032,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         max_n = std::max<uint64_t>(max_n, std::max(specs[s].na, specs[s].nb));
     }
     Shape sh;
-    bool fits = choose_shape(ctx, mode, ne, all_pairs, max_n, &sh);
-    if (!fits && mode == kModeScreenPacked) {  // the packed stage layout is twice as large
-        mode = kModeScreenScalar;
-        fits = choose_shape(ctx, mode, ne, all_pairs, max_n, &sh);
-    }
+    const bool fits = choose_shape(ctx, mode, ne, all_pairs, max_n, &sh);
     if (!fits)
         return ctx->fail(TPCF_EINVAL, "no kernel shape fits (threads=%d ipt=%d jtile=%d)",
                          ctx->cfg.threads, ctx->cfg.ipt, ctx->cfg.jtile);
@@ -1108,7 +1107,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
             wd.item_hi = items * (ctx->cfg.shard_index + 1) / ctx->cfg.shard_count;
         }
         wd.stats = stat_w;
-        wd.I = (uint32_t)(shp.threads * shp.ipt);
+        wd.I = 32u * (uint32_t)shp.ipt;
         wd.J = (uint32_t)shp.jtile;
         wd.Jc = (uint32_t)shp.jchunk;
         wd.stages = (uint32_t)shp.stages;
@@ -1139,7 +1138,9 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         // 1e-12) makes the binary64 d^2 (relative error < 1e-15) >= S_B.
         wd.prune = 0u;
         wd.prune_thr = INFINITY;
-        if ((ctx->cfg.flags & TPCF_F_PRUNE) && (mode == kModeScreenScalar || mode == kModeEuclidScreen)) {
+        // (not with a counted overflow row: skipped blocks would have to be counted)
+        if ((ctx->cfg.flags & TPCF_F_PRUNE) && !(ctx->cfg.flags & TPCF_F_CHECK_OVERFLOW) &&
+            (mode == kModeScreenScalar || mode == kModeEuclidScreen)) {
             double thr;
             if (bh->euclid) {
                 thr = std::sqrt(bh->cos_last) * (1.0 + 1e-12) * kCapScale3d;
@@ -1167,7 +1168,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     };
 
     // ---- optional autotuning: time every fitting shape on a bounded window of the
-    // work (about 8 items per SM, the same window of the walk for every shape),
+    // work (about 4 items per warp, the same window of the walk for every shape),
     // keep the one with the least time per pair
     if ((ctx->cfg.flags & TPCF_F_AUTOTUNE) && ctx->cfg.threads == 0 && ctx->cfg.jtile == 0) {
         const std::array<int, 5> key{mode, ne, nsub, ilog2_u64(all_pairs + 1), ilog2_u64(max_n + 1)};
@@ -1177,7 +1178,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
             sh = it->second;
         } else {
             const int cand_t[3] = {128, 256, 512};
-            const int cand_j[3] = {256, 512, 1024};
+            const int cand_j[3] = {128, 256, 512};
             double best = 1e300;
             Shape best_sh = sh;
             cudaEvent_t a0, a1;
@@ -1188,7 +1189,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
                     Shape c;
                     if (!shape_for(ctx, mode, ne, cand_t[ti], 8, cand_j[ji], 0, &c)) continue;
                     if (setup(c) != TPCF_OK) continue;
-                    const uint64_t window = (uint64_t)ctx->num_sms * 8;
+                    const uint64_t window = (uint64_t)ctx->num_sms * (uint64_t)(c.threads / 32) * 4;
                     if (wd.item_hi - wd.item_lo > window) wd.item_hi = wd.item_lo + window;
                     uint64_t wpairs = 0;
                     for (int s2 = 0; s2 < nsub; ++s2)
@@ -1258,19 +1259,22 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     }
     if (stats) cudaEventRecord(t1, st);
 
-    // ---- finalize: overflow of each histogram = its pair total - sum of the other entries
+    // ---- finalize: overflow of each histogram = its pair total - sum of the other
+    // entries, or (counted overflow) a check that the entries sum to the total
+    const int count_over = (ctx->cfg.flags & TPCF_F_CHECK_OVERFLOW) ? 1 : 0;
     if (use_slot) {
         for (int s2 = 0; s2 < H; ++s2) {
             unsigned long long* a = acc + (size_t)s2 * acc_stride;
             unsigned long long* dst = where == TPCF_DEVICE ? outs[s2] : a;
-            if (launch_finalize(a, ne, dst, totals[s2], stat_w + kStatError, st) != cudaSuccess)
+            if (launch_finalize(a, ne, dst, totals[s2], count_over, stat_w + kStatError, st) != cudaSuccess)
                 return release(ctx->fail(TPCF_ECUDA, "finalize launch failed"));
             ++launches;
         }
     } else {
         // device outputs must be one contiguous array (outs[h] = outs[0] + h * (ne + 1))
         unsigned long long* dst = where == TPCF_DEVICE ? outs[0] : acc;
-        if (launch_finalize_batch(acc, (int)acc_stride, ne, dst, ne + 1, dev_totals, H, stat_w + kStatError, st) !=
+        if (launch_finalize_batch(acc, (int)acc_stride, ne, dst, ne + 1, dev_totals, H, count_over, stat_w + kStatError,
+                                  st) !=
             cudaSuccess)
             return abort_capture(ctx->fail(TPCF_ECUDA, "finalize launch failed"));
         ++launches;
@@ -1310,6 +1314,7 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
             stats->pruned_pairs = hs[kStatPruned];
         }
         if (errw & kErrWaitTimeout) rc = ctx->fail(TPCF_ETIMEOUT, "a bounded device wait timed out");
+        else if (errw & kErrBadHist) rc = ctx->fail(TPCF_ECUDA, "histogram does not add up to its pair total");
         else if (errw) rc = ctx->fail(TPCF_ECUDA, "device error word 0x%llx", errw);
     }
     ctx->launches.fetch_add(launches);

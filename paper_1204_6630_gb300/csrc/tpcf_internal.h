@@ -68,7 +68,8 @@ struct BinsDev {
 struct SubProblem {
     const float4* a32;    // FP32 screen copy of A (padded to kPad)
     const float4* b32;
-    const float4* b32x2;  // B as (x,x,y,y),(z,z,0,0): two float4 per point (packed FMA)
+    const float* b_soa;   // B's FP32 points as x | y | z arrays (the sub-range's first point)
+    uint32_t b_soa_stride;  // floats between B's x, y and z arrays (its padded size)
     const Point64* a64;   // binary64 copy of A (padded)
     const Point64* b64;
     uint32_t na, nb;      // real point counts
@@ -108,10 +109,10 @@ struct WorkDesc {
     SubProblem sub[kMaxInlineSub];   // used when sub_dev == nullptr
     const SubProblem* sub_dev;       // device array of nsub sub-problems (batched launches)
     int nsub;
-    uint64_t item_lo, item_hi;       // walk positions of this launch (shards, serving quanta)
+    uint64_t item_lo, item_hi;       // walk positions of this launch (shards)
     unsigned long long* stats;       // kStatWords words
-    uint32_t I, J, Jc;               // i-block, j-tile, j-chunk sizes (points)
-    uint32_t stages;                 // shared-memory pipeline depth S (2..16)
+    uint32_t I, J, Jc;               // i-block (one warp's 32 R points), j-tile, j-chunk sizes (points)
+    uint32_t stages;                 // stages of each warp's shared-memory ring S (2..16)
     uint32_t flags;                  // TPCF_F_* subset used on the device
     uint32_t force_idx;              // 1: always check indices (sub-ranges of segmented catalogs)
     int nedges_max;                  // largest B + 1 over the sub-problems (shared-memory sizing)
@@ -131,8 +132,8 @@ struct WorkDesc {
     uint32_t prune;                  // 1: skip (warp, 128-j chunk) blocks proven beyond the range
     float prune_thr;                 // sphere-gap threshold of the pruning test (see prune_block)
     // ... and the shared-memory layout of the shape (set by the launcher).
-    uint32_t off_bars, off_ctl, off_stage, off_hist, off_cthr, off_lo, off_hi, off_c32, off_zlo, off_zhi,
-        off_lut, off_queue, off_prod, off_icap, off_items;
+    uint32_t off_ctl, off_bars, off_meta, off_stage, off_hist, off_cthr, off_lo, off_hi, off_c32, off_zlo, off_zhi,
+        off_lut, off_queue, off_icap;
     uint32_t stage_bytes;            // J * bytes per staged point
     uint32_t flush_limit;            // j-points between merges of the 16-bit counters
 };
@@ -140,31 +141,33 @@ struct WorkDesc {
 // Kernel shape selected on the host.
 struct Shape {
     int threads;   // T
-    int ipt;       // R
+    int ipt;       // R (a warp's items hold 32 R i-points)
     int jtile;     // J
     int jchunk;    // Jc
-    int stages;    // S
+    int stages;    // S (per warp)
     int blocks;    // grid size
     size_t smem;   // dynamic shared memory bytes
 };
 
-// Kernel variants (mode argument of the launchers): FP32 screen with scalar
-// FMA, all-binary64 comparator, FP32 screen with packed FP32x2 FMA.
-enum { kModeScreenScalar = 0, kModePlainFP64 = 1, kModeScreenPacked = 2, kModeEuclidScreen = 3 };
+// Kernel variants (mode argument of the launchers): FP32 screen of angles,
+// all-binary64 comparator, FP32 screen of distances (3-D variant).
+enum { kModeScreenScalar = 0, kModePlainFP64 = 1, kModeEuclidScreen = 3 };
 
 // Launchers (kernels.cu).  All are asynchronous in `stream` and return a
 // cudaError_t from the launch.
 cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int mode, int nedges,
                          cudaStream_t stream);
+// count_over = 1: the kernel counted the overflow row (TPCF_F_CHECK_OVERFLOW);
+// the finalize then checks that the histogram sums to the pair total.
 cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long long* out,
-                            unsigned long long total, unsigned long long* err_word,
+                            unsigned long long total, int count_over, unsigned long long* err_word,
                             cudaStream_t stream);
 cudaError_t launch_finalize_batch(const unsigned long long* acc, int acc_stride, int nedges,
                                   unsigned long long* out, int out_stride, const unsigned long long* totals,
-                                  int count, unsigned long long* err_word, cudaStream_t stream);
+                                  int count, int count_over, unsigned long long* err_word, cudaStream_t stream);
 cudaError_t launch_prepare(const double* xyz_in, uint32_t n, const uint32_t* seg_of_point,
                            const uint32_t* seg_delta, int sort, int euclid, unsigned long long* bbox,
-                           Point64* out64, float4* out32, float4* out32x2, float4* caps, uint32_t n_pad,
+                           Point64* out64, float4* out32, float* out_soa, float4* caps, uint32_t n_pad,
                            unsigned long long* key_scratch, uint32_t* val_scratch,
                            uint32_t n_pow2, unsigned long long* err_word, unsigned long long* eps_word,
                            cudaStream_t stream, uint32_t* launches);

@@ -108,8 +108,9 @@ def test_octant_small_w_matches_oracle(ctxs, small):
 
 
 # ------------------------------------------------------------------ ragged sizes and shapes
-SHAPES = [dict(threads=128, ipt=8, jtile=256), dict(threads=256, ipt=8, jtile=2048),
-          dict(threads=512, ipt=8, jtile=1024), dict(threads=256, ipt=16, jtile=512)]
+# (j-tiles of each warp's ring: every shape fits both the FP32 and the binary64 staging)
+SHAPES = [dict(threads=128, ipt=8, jtile=512), dict(threads=256, ipt=8, jtile=256),
+          dict(threads=512, ipt=8, jtile=128), dict(threads=256, ipt=16, jtile=256)]
 
 
 @pytest.mark.parametrize("shape", range(len(SHAPES)))
