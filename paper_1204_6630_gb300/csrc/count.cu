@@ -159,7 +159,9 @@ enum KernelMode { kModeScreen = 0, kModePlain = 1, kModeEuclid = 3 };
 
 // Block-wide control words (int32): the abort flag and each warp's queue length.
 enum Ctl { kCtlAbort = 0, kCtlQueue = 8, kCtlWords = 48 };
-constexpr int kQueuePerWarp = 64;   // band pairs per warp awaiting the binary64 recheck
+// Per-warp queue of unsettled pairs of the current tile (32-bit codes): at most
+// 31 left from earlier groups plus one per lane and round.
+constexpr int kUQueue = 64;
 constexpr int kMaskGroups = 32;     // fast loop: groups per warp reduction of the slow-group mask
 constexpr uint32_t kPruneSlotBytes = 32;  // float4 i-sphere, B's sphere pointer, pruned pair slots (u64)
 
@@ -178,7 +180,7 @@ struct SmemLayout {
     uint32_t cos_thr;   // nedges doubles
     uint32_t lo, hi, cos32, zlo, zhi;  // nedges floats each
     uint32_t lut;       // kLutCells 16-bit entries (screen kernels)
-    uint32_t queue;     // W * kQueuePerWarp unsettled pairs (i, j) (uint2, screen kernels)
+    uint32_t queue;     // W * kUQueue unsettled-pair codes (uint32, screen kernels)
     uint32_t icap;      // W pruning slots: the warp's i-sphere, B's sphere array, pruned pair slots
     uint32_t total;
 };
@@ -211,7 +213,7 @@ __host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S,
     off = align_up(off, 16);
     L.lut = off; off += plain ? 0u : (uint32_t)kLutCells * 2;
     off = align_up(off, 16);
-    L.queue = off; off += plain ? 0u : W * kQueuePerWarp * 8;
+    L.queue = off; off += plain ? 0u : W * kUQueue * 4;
     off = align_up(off, 16);
     L.icap = off; off += W * kPruneSlotBytes;
     L.total = off;
@@ -401,8 +403,7 @@ __device__ void warp_flush_hist(const HistCol& hc, int nedges, bool count_over, 
         uint32_t mine = (ld_shared_u32(a) >> sh) & 0xffffu;
         if (mine) red_add_shared(a, 0u - (mine << sh));
         if (h == nedges && !count_over) break;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+        mine = __reduce_add_sync(0xffffffffu, mine);
         if (lane == 0 && mine != 0) atomicAdd(out + h, (unsigned long long)mine);
     }
 }
@@ -462,14 +463,6 @@ __device__ __forceinline__ Resolved resolve_f32(const WorkDesc& wd, float c, int
     int h = nb_;
     for (int m = nb_; m < na_; ++m) h += (c <= c32[m]);
     return Resolved{-1, nb_, na_, h};
-}
-
-__device__ __forceinline__ uint32_t queue_off(const WorkDesc& wd, int warp) {
-    return wd.off_queue + (uint32_t)warp * kQueuePerWarp * 8;
-}
-
-__device__ __forceinline__ uint32_t queue_count_off(const WorkDesc& wd, int warp) {
-    return wd.off_ctl + (uint32_t)(kCtlQueue + warp) * 4;
 }
 
 // Screen value of pair (ig, jg) recomputed from the FP32 copies, bit-identical
@@ -554,16 +547,30 @@ __device__ __forceinline__ int euclid_band_index(const WorkDesc& wd, const SubPr
     return h;
 }
 
-// Histogram index of a queued pair (its LUT cell left edges open): the chord
-// refinement where the catalogs allow it (angles), the FP32 comparison with
-// the open edges' screen bounds, else the binary64 recomputation in the
-// definition's order.  Band statistics are added to *band, *mism.
-__device__ __forceinline__ int classify_unsettled(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg,
-                                                  uint32_t* band, uint32_t* mism) {
-    const SubProblem& sp = sub_of(wd, sub);
-    if (wd.euclid) {
-        const float4 a = __ldg(sp.a32 + ig), b = __ldg(sp.b32 + jg);
-        const float z = euclid_z(a.x, a.y, a.z, b.x, b.y, b.z);
+// ---- unsettled pairs
+// A pair whose LUT cell leaves edges open is queued by its warp as a 32-bit
+// code lane | r << 5 | j << 10 (the lane holding the i-point, its register r,
+// the j-point's offset in the staged tile) and classified later, 32 at a time
+// with one pair per lane: the i-point comes from its lane by shuffles, the
+// j-point from the tile (the warp empties its queue before leaving a tile).
+//
+// Histogram index of an unsettled pair (FP32 a, b; indices ig, jg).  Angles:
+// the screen value and LUT entry are recomputed (bit-identical to the slow
+// path's), the chord refinement decides the edges the entry leaves open where
+// the catalogs allow it: z = fl32(|a' - b'|^2) is within 4u|a - b| + O(u |a -
+// b|^2) of 2 (1 - d) (bounds zlo, zhi: runtime.cpp), far tighter than the
+// screen value at the small and moderate angles of a histogram range; z-space
+// bounds increase with the edge index, so a binary search over [P, Q) finds
+// nb = #{crossed} and the pair is settled when z is also below zlo[nb].  Then
+// the FP32 comparison with the open edges' screen bounds, else the binary64
+// recomputation in the definition's order.  3-D: the z-space bounds of the
+// open edges, else binary64.  Band statistics are added to band, mism.
+template <bool EUCLID>
+__device__ __forceinline__ int classify_unsettled(const WorkDesc& wd, const SubProblem& sp, float ax, float ay,
+                                                  float az, float bx, float by, float bz, uint32_t ig, uint32_t jg,
+                                                  uint32_t& band, uint32_t& mism) {
+    if constexpr (EUCLID) {
+        const float z = euclid_z(ax, ay, az, bx, by, bz);
         const int ent = ld_shared_s16(euclid_cell_addr(wd, z, smem_addr(dyn_smem) + wd.off_lut));
         if (ent >= 0) return ent == (int)kLutSkip ? wd.ne : ent;  // settled (not expected)
         int lo = 0, hi = 0;
@@ -571,124 +578,108 @@ __device__ __forceinline__ int classify_unsettled(const WorkDesc& wd, int sub, u
         if (h0 >= 0) return h0;
         uint32_t mm;
         const int h = euclid_band_index(wd, sp, ig, jg, z, lo, hi, &mm);
-        *band += 1;
-        *mism += mm;
+        band += 1;
+        mism += mm;
         return h;
-    }
-    const float e = screen_value(wd, sp, ig, jg);
-    const int ent = lut_entry(wd, e);
-    if (ent >= 0) return ent == (int)kLutSkip ? wd.ne : ent;  // settled (not expected)
-    const Resolved rs = resolve_f32(wd, e, lut_P(ent), lut_Q(ent, wd.ne));
-    if (rs.h >= 0) return rs.h;
-    uint32_t mm;
-    const int h = band_index(wd, sp, ig, jg, rs.nbv, rs.nav, rs.h32, &mm);
-    *band += 1;
-    *mism += mm;
-    return h;
-}
-
-// One warp classifies its queued pairs (i, j) and adds each to the lane's
-// own histogram column; the warp's band statistics go to the call's
-// statistics words; ends with the warp's queue empty.
-template <int T>
-__device__ __noinline__ void warp_drain_queue(const WorkDesc& wd, int sub, HistCol hc) {
-    const int warp = (int)(threadIdx.x >> 5);
-    const uint2* wq = sptr<const uint2>(queue_off(wd, warp));
-    volatile int* wq_count = sptr<volatile int>(queue_count_off(wd, warp));
-    uint32_t band = 0, mism = 0;
-    __syncwarp();
-    const int n = min(*wq_count, kQueuePerWarp);
-    for (int k = (int)(threadIdx.x & 31); k < n; k += 32) {
-        const uint2 q = wq[k];
-        hist_inc<T>(hc, classify_unsettled(wd, sub, q.x, q.y, &band, &mism));
-    }
-    const unsigned long long b = warp_sum(band), m = warp_sum(mism);
-    if ((threadIdx.x & 31) == 0) {
-        if (b) atomicAdd(wd.stats + kStatBand, b);
-        if (m) atomicAdd(wd.stats + kStatMismatch, m);
-        *wq_count = 0;
-    }
-    __syncwarp();
-}
-
-// A pair that the queue cannot take (full) is classified at once (rare, out of line).
-template <int T>
-__device__ __noinline__ void classify_now(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg, HistCol hc) {
-    uint32_t band = 0, mism = 0;
-    hist_inc<T>(hc, classify_unsettled(wd, sub, ig, jg, &band, &mism));
-    if (band) atomicAdd(wd.stats + kStatBand, 1ull);
-    if (mism) atomicAdd(wd.stats + kStatMismatch, 1ull);
-}
-
-// An unsettled pair (divergent: executed by the lanes holding one): queued
-// for the warp's drain, one shared atomic for all active lanes.
-template <int T>
-__device__ __forceinline__ void queue_pair(const WorkDesc& wd, int sub, uint32_t ig, uint32_t jg, const HistCol& hc) {
-    const uint32_t act = __activemask();
-    const uint32_t lane = threadIdx.x & 31u;
-    const int leader = __ffs(act) - 1;
-    int base = 0;
-    if ((int)lane == leader) base = atomicAdd(sptr<int>(queue_count_off(wd, (int)(threadIdx.x >> 5))), __popc(act));
-    base = __shfl_sync(act, base, leader);
-    const int pos = base + __popc(act & ((1u << lane) - 1u));
-    if (pos < kQueuePerWarp)
-        sptr<uint2>(queue_off(wd, (int)(threadIdx.x >> 5)))[pos] = make_uint2(ig, jg);
-    else
-        classify_now<T>(wd, sub, ig, jg, hc);
-}
-
-// An unsettled pair of the slow path (a = the i-point, b = the j-point, FP32):
-// its screen value and LUT entry are recomputed (bit-identical to the
-// slow path's), then the chord refinement decides the edges the entry leaves
-// open: z = fl32(|a' - b'|^2) is within 4u|a - b| + O(u |a-b|^2) of
-// 2 (1 - d) (bounds zlo, zhi: runtime.cpp), far tighter than the screen
-// value at the small and moderate angles of a histogram range.  Z-space
-// bounds increase with the edge index, so a binary search over [P, Q) finds
-// nb = #{crossed}; the pair is settled when z is also below zlo[nb].  Pairs
-// left in a chord band (or catalogs outside the chord bound's norm
-// tolerance) are queued for the binary64 recheck.
-template <int T>
-__device__ __forceinline__ void unsettled_pair(const WorkDesc& wd, int sub, float ax, float ay, float az, float bx,
-                                               float by, float bz, uint32_t ig, uint32_t jg, const HistCol& hc) {
-    if (wd.chord_ok) {
+    } else {
         const float e = fmaf(az, bz, fmaf(ay, by, fmaf(ax, bx, wd.neg_fast_t)));
         const int ent = lut_entry(wd, e);
-        const float z = euclid_z(ax, ay, az, bx, by, bz);
-        const float* zlo = sptr<const float>(wd.off_zlo);
-        const float* zhi = sptr<const float>(wd.off_zhi);
-        int lo = lut_P(ent), hi = lut_Q(ent, wd.ne);
-        const int Q = hi;
-        while (lo < hi) {  // first m in [P, Q) with z < zhi[m]
-            const int mid = (lo + hi) >> 1;
-            if (z >= zhi[mid]) lo = mid + 1; else hi = mid;
+        if (ent >= 0) return ent == (int)kLutSkip ? wd.ne : ent;  // settled (not expected)
+        const int P = lut_P(ent), Q = lut_Q(ent, wd.ne);
+        if (wd.chord_ok) {
+            const float z = euclid_z(ax, ay, az, bx, by, bz);
+            const float* zlo = sptr<const float>(wd.off_zlo);
+            const float* zhi = sptr<const float>(wd.off_zhi);
+            int lo = P, hi = Q;
+            while (lo < hi) {  // first m in [P, Q) with z < zhi[m]
+                const int mid = (lo + hi) >> 1;
+                if (z >= zhi[mid]) lo = mid + 1; else hi = mid;
+            }
+            if (lo == Q || z < zlo[lo]) return lo;
         }
-        if (lo == Q || z < zlo[lo]) {
-            hist_inc<T>(hc, lo);
-            return;
-        }
+        const Resolved rs = resolve_f32(wd, e, P, Q);
+        if (rs.h >= 0) return rs.h;
+        uint32_t mm;
+        const int h = band_index(wd, sp, ig, jg, rs.nbv, rs.nav, rs.h32, &mm);
+        band += 1;
+        mism += mm;
+        return h;
     }
-    queue_pair<T>(wd, sub, ig, jg, hc);
 }
 
-// After a slow group: drain the warp's queue once it is half full.
-template <int T>
-__device__ __forceinline__ void maybe_drain(const WorkDesc& wd, int sub, const HistCol& hc) {
-    __syncwarp();
-    if (*sptr<volatile int>(queue_count_off(wd, (int)(threadIdx.x >> 5))) >= kQueuePerWarp / 2)
-        warp_drain_queue<T>(wd, sub, hc);
+// The lane's i-points as scalars (register halves of the (a, a) pairs) and the
+// staged tile: what classifying a queued pair needs.
+template <int R>
+struct PairSource {
+    float x[R], y[R], z[R];
+    const float *sx, *sy, *sz;
+    uint32_t i0, jbase;
+};
+
+// Classifies the n <= 32 codes at q, one per lane, into the lanes' own columns.
+template <int T, int R, bool EUCLID>
+__device__ __forceinline__ void drain_batch(const WorkDesc& wd, const SubProblem& sp, const uint32_t* q, uint32_t n,
+                                            const PairSource<R>& ps, const HistCol& hc, uint32_t& band,
+                                            uint32_t& mism) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const bool has = lane < n;
+    const uint32_t code = has ? q[lane] : 0u;
+    const int l = (int)(code & 31u), r = (int)((code >> 5) & 31u);
+    const uint32_t jo = code >> 10;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+        const float x = __shfl_sync(0xffffffffu, ps.x[rr], l);
+        const float y = __shfl_sync(0xffffffffu, ps.y[rr], l);
+        const float z = __shfl_sync(0xffffffffu, ps.z[rr], l);
+        if (rr == r) {
+            ax = x;
+            ay = y;
+            az = z;
+        }
+    }
+    if (has) {
+        const uint32_t ig = ps.i0 + (uint32_t)l + 32u * (uint32_t)r, jg = ps.jbase + jo;
+        hist_inc<T>(hc, classify_unsettled<EUCLID>(wd, sp, ax, ay, az, ps.sx[jo], ps.sy[jo], ps.sz[jo], ig, jg,
+                                                   band, mism));
+    }
+}
+
+// Queues the lane's unsettled pairs of a group (bit U R - 1 - k for pair k =
+// r U + u of the group at tile offset jj), one per lane and round (a ballot
+// gives each lane its slot), and classifies every full batch of 32 (taken from
+// the top of the queue); on return the warp's queue length qn (warp-uniform)
+// is below 32.  nbatch counts the batches (each adds at most one to every
+// lane's counters).
+template <int T, int R, int U, bool EUCLID>
+__device__ __forceinline__ void enqueue_unsettled(const WorkDesc& wd, const SubProblem& sp, uint32_t um, int jj,
+                                                  uint32_t* q, uint32_t& qn, uint32_t& nbatch,
+                                                  const PairSource<R>& ps, const HistCol& hc, uint32_t& band,
+                                                  uint32_t& mism) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t below = (1u << lane) - 1u;
+    uint32_t act = __ballot_sync(0xffffffffu, um != 0u);
+    while (act) {
+        if (um) {
+            const int b = 31 - __clz(um);
+            um &= ~(1u << b);
+            const int k = U * R - 1 - b;
+            q[qn + (uint32_t)__popc(act & below)] = lane | ((uint32_t)(k / U) << 5) | ((uint32_t)(jj + k % U) << 10);
+        }
+        qn += (uint32_t)__popc(act);
+        if (qn >= 32) {
+            __syncwarp();
+            qn -= 32;
+            drain_batch<T, R, EUCLID>(wd, sp, q + qn, 32u, ps, hc, band, mism);
+            ++nbatch;
+            __syncwarp();  // the batch is read before later codes overwrite it
+        }
+        act = __ballot_sync(0xffffffffu, um != 0u);
+    }
 }
 
 // Diagonal handling of a tile (warp-uniform): none, keep j > i, keep j != i.
 enum { kDiagNone = 0, kDiagAbove = 1, kDiagOffSelf = 2 };
-
-// Element k of a register array without dynamic indexing (no local memory).
-template <int R>
-__device__ __forceinline__ float pick(const float (&v)[R], int k) {
-    float x = v[0];
-#pragma unroll
-    for (int r = 1; r < R; ++r) x = (k == r) ? v[r] : x;
-    return x;
-}
 
 // Which pairs of a group may be counted: bit r * U + u for i-point r and
 // j-point u (sub-problem bounds, then the diagonal rule of the tile).
@@ -778,13 +769,13 @@ __device__ __forceinline__ void euclid_group2(float (&e)[R][U], const u64 (&ax)[
 // i-point r (shared loads and reductions stay in program order).  Pairs
 // beyond the range land in the skip code or (TPCF_F_CHECK_OVERFLOW) the
 // overflow row; on masked tiles, pairs that must not be counted (padding,
-// j <= i on the diagonal) are forced to the skip code.  Unsettled entries
-// (bit 31) go through unsettled_pair, one per iteration of the lane.
+// j <= i on the diagonal) are forced to the skip code.  Returns the lane's
+// unsettled pairs (bit 31 of the entry), pair k = r U + u at bit U R - 1 - k.
 template <int T, int R, int U, bool MASKED>
-__device__ __forceinline__ void slow_group(const WorkDesc& wd, int sub, const u64 (&ax2)[R], const u64 (&ay2)[R],
-                                           const u64 (&az2)[R], const float* sx, const float* sy, const float* sz,
-                                           int jj, uint32_t ibase, uint32_t jbase, int diag, uint32_t na,
-                                           uint32_t nb, const HistCol& hc) {
+__device__ __forceinline__ uint32_t slow_group(const WorkDesc& wd, const u64 (&ax2)[R], const u64 (&ay2)[R],
+                                               const u64 (&az2)[R], const float* sx, const float* sy,
+                                               const float* sz, int jj, uint32_t ibase, uint32_t jbase, int diag,
+                                               uint32_t na, uint32_t nb, const HistCol& hc) {
     static_assert(U * R <= 32, "one bit per pair of the group");
     float e[R][U];
     screen_group2<R, U>(e, ax2, ay2, az2, sx, sy, sz, jj, pack2(wd.neg_fast_t, wd.neg_fast_t));
@@ -814,37 +805,21 @@ __device__ __forceinline__ void slow_group(const WorkDesc& wd, int sub, const u6
             }
         }
     }
-    if (__any_sync(0xffffffffu, um != 0u)) {
-        float fx[R], fy[R], fz[R];  // the i-points as scalars (register halves)
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            fx[r] = lo_of(ax2[r]);
-            fy[r] = lo_of(ay2[r]);
-            fz[r] = lo_of(az2[r]);
-        }
-        while (um) {  // one iteration per unsettled pair of the lane
-            const int k = U * R - 1 - (31 - __clz(um));
-            um &= ~(1u << (U * R - 1 - k));
-            const int r = k / U, u = k % U;
-            const int j = jj + u;
-            unsettled_pair<T>(wd, sub, pick(fx, r), pick(fy, r), pick(fz, r), sx[j], sy[j], sz[j],
-                              ibase + 32u * (uint32_t)r, jbase + (uint32_t)j, hc);
-        }
-    }
+    return um;
 }
 
 // Slow path of the 3-D variant for a group of U j: z = fl32(|a' - b'|^2) is
 // recomputed for all R pairs of every lane, its constant-ratio LUT cell gives
 // a settled row (one shared load, one reduction) or the edges left open,
-// which the z-space bounds decide inline or the binary64 recheck (queue)
-// settles.  Same load-before-reduction pipelining and masking as the angular
+// which the warp's queue of unsettled pairs settles.  Same
+// load-before-reduction pipelining, masking and return value as the angular
 // slow path.
 template <int T, int R, int U, bool MASKED>
-__device__ __forceinline__ void slow_group_euclid(const WorkDesc& wd, int sub, const u64 (&ax2)[R],
-                                                  const u64 (&ay2)[R], const u64 (&az2)[R], const float* sx,
-                                                  const float* sy, const float* sz, int jj, uint32_t ibase,
-                                                  uint32_t jbase, int diag, uint32_t na, uint32_t nb,
-                                                  const HistCol& hc) {
+__device__ __forceinline__ uint32_t slow_group_euclid(const WorkDesc& wd, const u64 (&ax2)[R],
+                                                      const u64 (&ay2)[R], const u64 (&az2)[R], const float* sx,
+                                                      const float* sy, const float* sz, int jj, uint32_t ibase,
+                                                      uint32_t jbase, int diag, uint32_t na, uint32_t nb,
+                                                      const HistCol& hc) {
     static_assert(U * R <= 32, "one bit per pair of the group");
     const uint32_t lut_base = smem_addr(dyn_smem) + wd.off_lut;
     float fx[R], fy[R], fz[R];
@@ -884,20 +859,7 @@ __device__ __forceinline__ void slow_group_euclid(const WorkDesc& wd, int sub, c
             }
         }
     }
-    if (__any_sync(0xffffffffu, um != 0u)) {
-        while (um) {  // one iteration per unsettled pair of the lane
-            const int k = U * R - 1 - (31 - __clz(um));
-            um &= ~(1u << (U * R - 1 - k));
-            const int r = k / U, u = k % U;
-            const uint32_t ig = ibase + 32u * (uint32_t)r, jg = jbase + (uint32_t)(jj + u);
-            const float z = euclid_z(pick(fx, r), pick(fy, r), pick(fz, r), sx[jj + u], sy[jj + u], sz[jj + u]);
-            const int x = ld_shared_s16(euclid_cell_addr(wd, z, lut_base));
-            int lo = 0, hi = 0;
-            const int h = euclid_resolve(wd, z, x, &lo, &hi);
-            if (h >= 0) hist_inc<T>(hc, h);
-            else queue_pair<T>(wd, sub, ig, jg, hc);
-        }
-    }
+    return um;
 }
 
 // ============================================================== spatial pruning
@@ -1049,10 +1011,11 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     uint32_t cur_q = 0xffffffffu;
     ItemGeom g{};
     unsigned long long* cur_hist = nullptr;  // the histogram this warp's counters belong to
-    uint32_t j_since_flush = 0;
+    uint32_t inc_bound = 0;  // bound on the increments of any of the lane's counters since its merge
     u64 ax2[PLAIN ? 1 : R], ay2[PLAIN ? 1 : R], az2[PLAIN ? 1 : R];
     double dx[PLAIN ? R : 1], dy[PLAIN ? R : 1], dz[PLAIN ? R : 1];
     uint32_t ibase = 0;
+    uint32_t band_cnt = 0, mism_cnt = 0;  // pairs rechecked in binary64 / whose FP32-only bin differed
     bool aborted = false;
 
     uint32_t seq = 0;
@@ -1080,13 +1043,9 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             unsigned long long* tgt = sp.hist;
             if (sp.row_seg) tgt += (size_t)__ldg(sp.row_seg + c.g.i0 / kSegAlign) * sp.row_stride;
             if (c.sub != cur_sub || tgt != cur_hist) {
-                if (cur_sub >= 0) {
-                    // queued pairs belong to the previous sub-problem and histogram
-                    if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
-                    if (tgt != cur_hist) {
-                        warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
-                        j_since_flush = 0;
-                    }
+                if (cur_sub >= 0 && tgt != cur_hist) {
+                    warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
+                    inc_bound = 0;
                 }
                 cur_sub = c.sub;
                 cur_hist = tgt;
@@ -1123,16 +1082,17 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             }
         }
 
-        // ---- merge the 16-bit counters before any can wrap: a lane adds at most
-        // R per j to one row, plus at most 2 per queue drain (at most one drain
-        // per slow group), so merging every flush_limit j-points keeps every
-        // counter below 2^16
-        if (j_since_flush + wd.J > wd.flush_limit) {
-            if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
+        // ---- merge the 16-bit counters before any can wrap: during a tile a lane
+        // adds one for each of its R J pairs that it settles itself (or, with
+        // TPCF_F_CHECK_OVERFLOW, that the fast loop rejects) plus one per queue
+        // batch of the warp (each pair is queued at most once: at most R J + 1
+        // batches), so at most 2 R J + 1; after the tile, the R J and the
+        // batches that actually ran are added to the bound
+        if (inc_bound + 2u * R * wd.J + 1u > 0xffffu) {
             warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
-            j_since_flush = 0;
+            inc_bound = 0;
         }
-        j_since_flush += wd.J;
+        uint32_t nbatch = 0;
 
         const SubProblem& sp = sub_of(wd, cur_sub);
         const uint32_t na = sp.na, nb = sp.nb;
@@ -1206,6 +1166,20 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             const float t0 = EUCLID ? -wd.neg_fast_t : wd.neg_fast_t;
             const u64 nt2 = pack2(t0, t0);
             constexpr int CH = kMaskGroups * U;                     // j-points per mask chunk
+            uint32_t* uq = sptr<uint32_t>(wd.off_queue) + (uint32_t)warp * kUQueue;
+            uint32_t qn = 0;  // codes in the warp's queue of unsettled pairs
+            PairSource<R> src;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                src.x[r] = lo_of(ax2[r]);
+                src.y[r] = lo_of(ay2[r]);
+                src.z[r] = lo_of(az2[r]);
+            }
+            src.sx = sx;
+            src.sy = sy;
+            src.sz = sz;
+            src.i0 = g.i0;
+            src.jbase = jbase;
             static_assert(kMaskGroups <= 32, "one mask bit per group");
 #pragma unroll 1
             for (int jc = 0; jc < J; jc += CH) {
@@ -1239,17 +1213,27 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                     const int gi = kMaskGroups - __ffs(m);  // lowest set bit first
                     m &= m - 1u;
                     const int jj = jc + gi * U;
+                    uint32_t um;
                     if constexpr (EUCLID) {
-                        if (masked) slow_group_euclid<T, R, U, true>(wd, cur_sub, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc);
-                        else slow_group_euclid<T, R, U, false>(wd, cur_sub, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc);
+                        um = masked ? slow_group_euclid<T, R, U, true>(wd, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc)
+                                    : slow_group_euclid<T, R, U, false>(wd, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc);
                     } else {
-                        if (masked) slow_group<T, R, U, true>(wd, cur_sub, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc);
-                        else slow_group<T, R, U, false>(wd, cur_sub, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc);
+                        um = masked ? slow_group<T, R, U, true>(wd, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc)
+                                    : slow_group<T, R, U, false>(wd, ax2, ay2, az2, sx, sy, sz, jj, ibase, jbase, diag, na, nb, hc);
                     }
-                    maybe_drain<T>(wd, cur_sub, hc);
+                    enqueue_unsettled<T, R, U, EUCLID>(wd, sp, um, jj, uq, qn, nbatch, src, hc, band_cnt, mism_cnt);
                 }
             }
+            // the queue's last codes, before the warp leaves the tile
+            if (qn) {
+                __syncwarp();
+                drain_batch<T, R, EUCLID>(wd, sp, uq, qn, src, hc, band_cnt, mism_cnt);
+                ++nbatch;
+                __syncwarp();
+            }
         }
+
+        inc_bound += (uint32_t)R * wd.J + nbatch;
 
         // ---- refill this stage with tile seq + S
         __syncwarp();
@@ -1261,9 +1245,13 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     }
 
     // ---- merge this warp's columns (skipped after an abort: outputs are invalid)
-    if (!aborted && cur_sub >= 0) {
-        if constexpr (!PLAIN) warp_drain_queue<T>(wd, cur_sub, hc);
-        warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
+    if (!aborted && cur_sub >= 0) warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
+    if constexpr (!PLAIN) {
+        const unsigned long long b = warp_sum(band_cnt), mm = warp_sum(mism_cnt);
+        if (lane == 0) {
+            if (b) atomicAdd(wd.stats + kStatBand, b);
+            if (mm) atomicAdd(wd.stats + kStatMismatch, mm);
+        }
     }
     if (wd.prune && lane == 0) {
         const unsigned long long np = sptr<PruneSlot>(wd.off_icap + (uint32_t)warp * kPruneSlotBytes)->pruned;
@@ -1365,11 +1353,8 @@ static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t
     wd.off_queue = L.queue;
     wd.off_icap = L.icap;
     wd.stage_bytes = wd.J * staged_point_bytes(MODE);
-    // 16-bit counters: a lane adds at most R per j to one row plus at most 2 per
-    // queue drain (at most one drain per slow group of 32 / R j-points), so
-    // merging every 65535 / (R + 2) - J j-points (checked per tile) keeps every
-    // counter below 2^16
-    wd.flush_limit = 0xffffu / (uint32_t)(R + 2) - wd.J;
+    // the 16-bit counters' merge interval is bounded in the kernel, per tile
+    wd.flush_limit = 0xffffu;
     if (L.total > sh.smem || wd.I != 32u * (uint32_t)R) return cudaErrorInvalidValue;
     count_kernel<T, R, MODE><<<sh.blocks, T, sh.smem, stream>>>(wd);
     return cudaGetLastError();
