@@ -778,7 +778,7 @@ __device__ __forceinline__ uint32_t slow_group(const WorkDesc& wd, const u64 (&a
                                                uint32_t na, uint32_t nb, const HistCol& hc) {
     static_assert(U * R <= 32, "one bit per pair of the group");
     float e[R][U];
-    screen_group2<R, U>(e, ax2, ay2, az2, sx, sy, sz, jj, pack2(wd.neg_fast_t, wd.neg_fast_t));
+    screen_group2<R, U>(e, ax2, ay2, az2, sx, sy, sz, jj, wd.neg_fast_t2);  // as the fast loop
     uint32_t valid = ~0u;
     if constexpr (MASKED) valid = valid_pairs<R, U>(ibase, jbase + (uint32_t)jj, na, nb, diag);
     const uint32_t lut_adj = smem_addr(dyn_smem) + wd.off_lut - 0x4B000000u * 2u;  // + 2 bits(f): entry
@@ -1162,9 +1162,8 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             const float* sx = sptr<const float>(stage_off);
             const float* sy = sx + J;
             const float* sz = sy + J;
-            // angles: -T; 3-D: -H (the host passes +H for the 3-D variant)
-            const float t0 = EUCLID ? -wd.neg_fast_t : wd.neg_fast_t;
-            const u64 nt2 = pack2(t0, t0);
+            // angles: (-T, -T); 3-D: (-H, -H), read from the kernel parameter
+            const u64 nt2 = wd.neg_fast_t2;
             constexpr int CH = kMaskGroups * U;                     // j-points per mask chunk
             uint32_t* uq = sptr<uint32_t>(wd.off_queue) + (uint32_t)warp * kUQueue;
             uint32_t qn = 0;  // codes in the warp's queue of unsettled pairs

@@ -1118,6 +1118,12 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
         wd.euclid = bh->euclid ? 1u : 0u;
         wd.neg_fast_t = bh->euclid ? bh->fast_t : -bh->fast_t;  // 3-D: +H, angular: -T
         wd.lut_scale = bh->lut_scale;
+        {
+            const float t = -bh->fast_t;  // the fast loop's packed offset: -T (angles), -H (3-D)
+            uint32_t b;
+            memcpy(&b, &t, 4);
+            wd.neg_fast_t2 = ((unsigned long long)b << 32) | b;
+        }
         wd.cos_last = bh->cos_last;
         wd.zbits0 = bh->zbits0;
         wd.zshift = bh->zshift;

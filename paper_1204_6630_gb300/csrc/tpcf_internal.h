@@ -122,6 +122,7 @@ struct WorkDesc {
     // (set by the runtime) ...
     int ne;                          // B + 1
     float neg_fast_t;                // -T (screen offset)
+    unsigned long long neg_fast_t2;  // the packed pair (-T, -T) (3-D: (-H, -H)): an FP32x2 operand
     float lut_scale;                 // 2^-q (LUT span)
     uint32_t need_idx;               // 1: check i < na, j < nb for every slow pair
     uint32_t chord_ok;               // 1: every catalog of the launch has | |v|^2 - 1 | <= kChordEpsRef
