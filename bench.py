@@ -376,7 +376,7 @@ def run_gpu(args):
         try:
             import hashlib
             rec = json.load(open(prof))
-            src = os.path.join(ROOT, "paper_1204_6630_gb300", "csrc", "kernels.cu")
+            src = os.path.join(ROOT, "paper_1204_6630_gb300", "csrc", "count.cu")
             sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
             if rec.get("kernel_source_sha256_16") == sha and args.n == 1_000_000:
                 traffic = rec.get("dram_bytes_per_launch")
