@@ -769,7 +769,7 @@ def main():
     ap.add_argument("--workload", default="octant_precision",
                     choices=["octant_precision", "jackknife", "serving", "large", "box3d"])
     ap.add_argument("--jobs", type=int, default=2000, help="serving: number of jobs")
-    ap.add_argument("--workers", type=int, default=4, help="serving: jobs in flight")
+    ap.add_argument("--workers", type=int, default=0, help="serving: job slots (0: the server's default, 32)")
     ap.add_argument("--sub", type=int, default=100_000, help="large: subsample points per catalog")
     ap.add_argument("--count-only", type=int, default=0, metavar="N",
                     help="profiling helper: one fused counting launch on the N-point octant workload")

@@ -139,7 +139,8 @@ typedef struct tpcf_config {
     uint32_t shard_count;      /* number of shards (0 or 1 = no split); histograms of all
                                   shards sum to the unsplit result exactly */
     uint32_t wait_timeout_us;  /* limit of every device-side wait; 0 -> 2,000,000 us */
-    int server_workers;        /* job server: jobs in flight at once, one CUDA stream each (0 -> 4) */
+    int server_workers;        /* job server: jobs admitted at once (slots: catalogs resident on the
+                                  device, work in the running steps) (0 -> 32) */
 } tpcf_config;
 
 typedef struct tpcf_stats {
@@ -367,14 +368,26 @@ int tpcf_correlate(tpcf_ctx *ctx, const double *d_xyz, uint64_t nd, const double
  *
  * tpcf_submit copies the job's arrays (the caller may free them on return)
  * and queues it; *job_id receives an id > 0.  The context's server starts on
- * the first submit with cfg.server_workers worker threads, each owning a CUDA
- * stream, so up to that many jobs run on the device at once.  Admission: a job
- * needs an estimated amount of device memory (both prepared catalogs, the
- * preparation scratch and the bins); queued jobs start in submission order,
- * except that a job that does not fit the memory left under
+ * the first submit.  Admission: a job needs one of cfg.server_workers slots
+ * and an estimated amount of device memory (both prepared catalogs, the
+ * preparation scratch, bins and accumulators); queued jobs are admitted in
+ * submission order, except that a job that does not fit the memory left under
  * cfg.hbm_budget_bytes lets later jobs that fit go first.  A job that alone
- * exceeds the budget is refused with TPCF_EBUDGET.  Job buffers are allocated
- * and freed in stream order (no device-wide synchronization between jobs).
+ * exceeds the budget is refused with TPCF_EBUDGET.  An admitted job's catalogs
+ * and bins are prepared on the device (preparation workers, their own
+ * streams) and stay resident until it completes.
+ * Continuous batching: the counting work of all admitted jobs runs as a
+ * sequence of steps, each one launch of a multi-job kernel over slices of
+ * many jobs' work items (each job with its own bins and histograms; a step
+ * that holds a single job launches the one-job kernel); a step gives every
+ * job with little work left all of it and fills the rest of its pair budget
+ * in admission order, and a job admitted while steps run joins the next
+ * step.  Two steps are in flight, on two streams, so that the blocks of one
+ * start on the SMs the other's blocks leave.  Each job's histograms equal those of a lone tpcf_correlate
+ * call (every pair is counted once, whatever step it lands in).  Jobs with
+ * more edges than the multi-job kernel's shared memory holds are counted
+ * alone by their preparation worker.  Job buffers are allocated and freed in
+ * stream order (no device-wide synchronization between jobs).
  * Validation as tpcf_submit returns: TPCF_EINVAL for NULL arrays, bad edges or
  * estimator, TPCF_EOVERFLOW for catalogs above TPCF_MAX_POINTS; bad points are
  * found when the job runs and reported by tpcf_poll.
@@ -408,9 +421,11 @@ typedef struct tpcf_result {
     int nedges;
     double submit_ms;  /* submission time, ms since the server started */
     double queued_ms;  /* submit -> start on a worker */
-    double run_ms;     /* start -> done (upload, preparation, counting, estimator) */
+    double run_ms;     /* admission -> done (upload, preparation, counting, estimator) */
     double latency_ms; /* submit -> done */
-    double kernel_ms;  /* device time of the counting launch */
+    double kernel_ms;  /* device time of the counting steps that held the job's work (from
+                          each step's start on its stream to its end: steps overlap, so
+                          the sum can exceed the job's wall time) */
     uint64_t pairs;    /* pairs visited */
 } tpcf_result;
 

@@ -158,7 +158,8 @@ __device__ __forceinline__ uint32_t lop_tree(const uint32_t* v) {
 enum KernelMode { kModeScreen = 0, kModePlain = 1, kModeEuclid = 3 };
 
 // Block-wide control words (int32): the abort flag and each warp's queue length.
-enum Ctl { kCtlAbort = 0, kCtlQueue = 8, kCtlWords = 48 };
+enum Ctl { kCtlAbort = 0, kCtlChunk = 1, kCtlQueue = 8, kCtlWords = 48 };
+
 // Per-warp queue of unsettled pairs of the current tile (32-bit codes): at most
 // 31 left from earlier groups plus one per lane and round.
 constexpr int kUQueue = 64;
@@ -182,6 +183,8 @@ struct SmemLayout {
     uint32_t lut;       // kLutCells 16-bit entries (screen kernels)
     uint32_t queue;     // W * kUQueue unsettled-pair codes (uint32, screen kernels)
     uint32_t icap;      // W pruning slots: the warp's i-sphere, B's sphere array, pruned pair slots
+    uint32_t bwd;       // serving steps: the block's current job (WorkDesc) and its item counter
+    uint32_t counter;
     uint32_t total;
 };
 
@@ -216,6 +219,10 @@ __host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S,
     L.queue = off; off += plain ? 0u : W * kUQueue * 4;
     off = align_up(off, 16);
     L.icap = off; off += W * kPruneSlotBytes;
+    off = align_up(off, 16);
+    L.bwd = off; off += (uint32_t)sizeof(WorkDesc);
+    off = align_up(off, 8);
+    L.counter = off; off += 8;
     L.total = off;
     return L;
 }
@@ -297,29 +304,57 @@ __device__ bool load_item(const WorkDesc& wd, uint32_t q, Cursor& c) {
     return c.t < c.g.t_end;
 }
 
-// The warp's next item with countable tiles (drawing again past empty ones);
-// called by every lane of the warp (lane 0 draws, the position is broadcast).
-__device__ void draw_next(const WorkDesc& wd, Cursor& c) {
-    const uint32_t q_end = (uint32_t)wd.item_hi;
+// The last items of a launch's range are drawn in parts.  Items differ in
+// cost by an order of magnitude (an i-block and a j-chunk inside one dense
+// cluster send most pairs to the slow path), so a warp that starts a whole
+// item just before the range runs out can hold its block, and the launch, for
+// the time of many average items.  The last kTailRounds items per warp of the
+// launch are therefore handed out as kTailParts consecutive tile ranges each.
+constexpr uint32_t kTailRounds = 8, kTailParts = 4;
+
+// The warp's next item (or part) with countable tiles, drawing again past
+// empty ones; called by every lane of the warp (lane 0 draws a position from
+// `counter`, the position is broadcast).  Positions below `whole` are whole
+// items, the rest kTailParts parts of each of the last `tail` items.
+__device__ void draw_next(const WorkDesc& wd, Cursor& c, unsigned long long* counter) {
+    const uint64_t n = wd.item_hi - wd.item_lo;
+    const uint64_t tail = umin64(n, (uint64_t)gridDim.x * (blockDim.x / 32u) * kTailRounds);
+    const uint64_t whole = n - tail, end = whole + tail * kTailParts;
     while (true) {
-        uint32_t q = 0;
-        if ((threadIdx.x & 31) == 0) q = (uint32_t)wd.item_lo + (uint32_t)atomicAdd(wd.stats + kStatNextItem, 1ull);
-        q = __shfl_sync(0xffffffffu, q, 0);
-        if (q >= q_end) {
+        unsigned long long p = 0;
+        if ((threadIdx.x & 31) == 0) p = atomicAdd(counter, 1ull);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        if (p >= end) {
             c.valid = false;
             return;
         }
-        if (load_item(wd, q, c)) {
-            c.valid = true;
-            return;
+        const uint64_t k = p < whole ? p : whole + (p - whole) / kTailParts;
+        if (!load_item(wd, (uint32_t)(wd.item_lo + k), c)) continue;
+        if (p >= whole) {
+            const uint32_t part = (uint32_t)((p - whole) % kTailParts), nt = c.g.t_end - c.g.t_first;
+            const uint32_t t0 = c.g.t_first + nt * part / kTailParts, t1 = c.g.t_first + nt * (part + 1) / kTailParts;
+            if (t0 == t1) continue;
+            c.t = t0;
+            c.g.t_end = t1;
         }
+        // the pairs of the tiles drawn (a whole item's or a part's), counted once
+        if ((threadIdx.x & 31) == 0) {
+            const SubProblem& sp = sub_of(wd, c.sub);
+            const uint64_t j0 = c.g.j0;
+            atomicAdd(wd.stats + kStatPairs,
+                      (unsigned long long)span_pairs(c.g.i0, wd.I, j0 + (uint64_t)c.t * wd.J,
+                                                     j0 + (uint64_t)c.g.t_end * wd.J, sp.na, sp.nb,
+                                                     sp.auto_mode != 0));
+        }
+        c.valid = true;
+        return;
     }
 }
 
-__device__ __forceinline__ void advance(const WorkDesc& wd, Cursor& c) {
+__device__ __forceinline__ void advance(const WorkDesc& wd, Cursor& c, unsigned long long* counter) {
     if (!c.valid) return;
     if (++c.t < c.g.t_end) return;
-    draw_next(wd, c);
+    draw_next(wd, c, counter);
 }
 
 // ============================================================== block helpers
@@ -946,7 +981,15 @@ __device__ __forceinline__ bool prune_chunk(const WorkDesc& wd, uint32_t jg0, ui
 // waits for another.  Every wait is bounded; a timeout sets the block's abort
 // word and the call's error word, after which no copy is issued, warps leave
 // their loops and each waits (bounded) for its own copies in flight.
-template <int T, int R, int MODE>
+//
+// MULTI (serving): the launch is one step of the job server, a list of slices
+// of many jobs' item ranges (each job with its own catalogs, bins and
+// histograms).  Every block walks the slices in order, copying a slice's job
+// description into shared memory; its warps draw the slice's items from the
+// slice's counter, shared by all blocks.  When a block moves to another job,
+// its warps merge their counters into the previous job's histograms and the
+// block loads the new job's bins and LUT.
+template <int T, int R, int MODE, bool MULTI>
 __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ WorkDesc wd) {
     constexpr bool PLAIN = MODE == kModePlain;
     constexpr bool EUCLID = MODE == kModeEuclid;
@@ -965,48 +1008,42 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         uint32_t* hist = sptr<uint32_t>(wd.off_hist);
         for (int k = tid; k < (wd.nedges_max + 1) * (T / 2); k += T) hist[k] = 0;
     }
-    load_bins<T>(sub_of(wd, 0).bins, wd, PLAIN);
-    uint64_t* bars = sptr<uint64_t>(wd.off_bars) + (uint32_t)warp * S;
-    TileMeta* meta = sptr<TileMeta>(wd.off_meta) + (uint32_t)warp * S;
-    const uint32_t stage_base = wd.off_stage + (uint32_t)warp * S * wd.stage_bytes;
+    if constexpr (!MULTI) load_bins<T>(sub_of(wd, 0).bins, wd, PLAIN);
+    // the warp's S barriers, stage records and stages (recomputed where used: no registers held)
+#define TPCF_BARS (sptr<uint64_t>(wd.off_bars) + (uint32_t)warp * S)
+#define TPCF_META (sptr<TileMeta>(wd.off_meta) + (uint32_t)warp * S)
+#define TPCF_STAGE_BASE (wd.off_stage + (uint32_t)warp * S * wd.stage_bytes)
     if (lane == 0) {
-        for (uint32_t s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        for (uint32_t s = 0; s < S; ++s) mbar_init(&TPCF_BARS[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
     const HistCol hc = hist_col<T>(wd);
 
     // Lane 0 copies the tile at cursor p into stage seq % S and records it there.
-    auto issue = [&](uint32_t seq, const Cursor& p) {
+    auto issue = [&](const WorkDesc& wdi, uint32_t seq, const Cursor& p) {
         if (lane != 0) return;
         if ((wd.flags & TPCF_F_TEST_WAIT_TIMEOUT) && seq == 0) return;  // test hook: never issued
         const uint32_t s = seq % S;
-        const SubProblem& sp = sub_of(wd, p.sub);
+        const SubProblem& sp = sub_of(wdi, p.sub);
         const uint32_t jbase = p.g.j0 + p.t * wd.J;
-        meta[s] = TileMeta{p.q, p.t};
-        unsigned char* dst = sptr<unsigned char>(stage_base + s * wd.stage_bytes);
+        TPCF_META[s] = TileMeta{p.q, p.t};
+        unsigned char* dst = sptr<unsigned char>(TPCF_STAGE_BASE + s * wd.stage_bytes);
+        uint64_t* bar = &TPCF_BARS[s];
         fence_proxy_async_smem();  // the warp's reads of the stage's previous tile come first
-        mbar_expect_tx(&bars[s], wd.stage_bytes);
+        mbar_expect_tx(bar, wd.stage_bytes);
         if constexpr (PLAIN) {
-            bulk_copy_g2s(dst, sp.b64 + jbase, wd.stage_bytes, &bars[s]);
+            bulk_copy_g2s(dst, sp.b64 + jbase, wd.stage_bytes, bar);
         } else {
             const uint32_t plane = wd.J * 4u;  // x | y | z arrays of J floats
-            bulk_copy_g2s(dst, sp.b_soa + jbase, plane, &bars[s]);
-            bulk_copy_g2s(dst + plane, sp.b_soa + sp.b_soa_stride + jbase, plane, &bars[s]);
-            bulk_copy_g2s(dst + 2 * plane, sp.b_soa + 2ull * sp.b_soa_stride + jbase, plane, &bars[s]);
+            bulk_copy_g2s(dst, sp.b_soa + jbase, plane, bar);
+            bulk_copy_g2s(dst + plane, sp.b_soa + sp.b_soa_stride + jbase, plane, bar);
+            bulk_copy_g2s(dst + 2 * plane, sp.b_soa + 2ull * sp.b_soa_stride + jbase, plane, bar);
         }
     };
 
-    // ---- prologue: the first S tiles of the warp
-    Cursor prod;
-    draw_next(wd, prod);
-    uint32_t issued = 0;
-    for (; issued < S && prod.valid; ++issued) {
-        issue(issued, prod);
-        advance(wd, prod);
-    }
-
-    // ---- consumer state
+    // ---- the warp's state (kept across the pieces of a multi-job launch)
+    uint32_t seq = 0, issued = 0;  // tiles consumed / issued so far (tile k: stage k % S)
     int cur_sub = -1;
     uint32_t cur_q = 0xffffffffu;
     ItemGeom g{};
@@ -1018,11 +1055,23 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     uint32_t band_cnt = 0, mism_cnt = 0;  // pairs rechecked in binary64 / whose FP32-only bin differed
     bool aborted = false;
 
-    uint32_t seq = 0;
+    // The warp's loop over the items of work description wd (this parameter
+    // shadows the launch's: it is the launch's own or a job's copy in shared
+    // memory): the first S tiles, then each tile in turn, its stage refilled with
+    // the tile S ahead; returns with every issued tile consumed (or after an abort).
+    auto run_items = [&](const WorkDesc& wd) {
+    if (aborted || ctl[kCtlAbort]) return;
+    // (single launches draw from the launch's statistics word: no pointer held in registers)
+    Cursor prod;
+    draw_next(wd, prod, MULTI ? wd.item_counter : wd.stats + kStatNextItem);
+    for (; issued < seq + S && prod.valid; ++issued) {
+        issue(wd, issued, prod);
+        advance(wd, prod, MULTI ? wd.item_counter : wd.stats + kStatNextItem);
+    }
     for (; seq < issued; ++seq) {
         // ---- wait for tile seq
         const uint32_t s = seq % S;
-        const bool ok = mbar_wait_bounded(&bars[s], (seq / S) & 1u, wd.wait_limit_ns);
+        const bool ok = mbar_wait_bounded(&TPCF_BARS[s], (seq / S) & 1u, wd.wait_limit_ns);
         if (__any_sync(0xffffffffu, !ok)) {
             if (lane == 0) {
                 ctl[kCtlAbort] = 1;
@@ -1032,7 +1081,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             break;
         }
         if (ctl[kCtlAbort]) { aborted = true; break; }
-        const volatile TileMeta* vm = meta + s;
+        const volatile TileMeta* vm = TPCF_META + s;
         const TileMeta tm{vm->q, vm->t};
 
         if (tm.q != cur_q) {
@@ -1052,9 +1101,6 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             }
             cur_q = tm.q;
             g = c.g;
-            if (lane == 0)
-                atomicAdd(wd.stats + kStatPairs,
-                          (unsigned long long)item_pairs(g, sp.na, sp.nb, sp.auto_mode != 0, wd.I, wd.Jc));
             ibase = g.i0 + (uint32_t)lane;
             if (wd.prune) {
                 const float4 sph = warp_sphere<R>(sp.a_caps + g.i0 / kCapPoints);
@@ -1108,7 +1154,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         // look in range (need_idx) and whenever overflow is counted
         const bool edge = jbase + wd.J > nb || g.i0 + IB > na;
         const bool masked = diag != kDiagNone || (edge && (wd.need_idx || check));
-        const uint32_t stage_off = stage_base + s * wd.stage_bytes;
+        const uint32_t stage_off = TPCF_STAGE_BASE + s * wd.stage_bytes;
 
         if constexpr (PLAIN) {
             const Point64* sj = sptr<const Point64>(stage_off);
@@ -1237,14 +1283,86 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         // ---- refill this stage with tile seq + S
         __syncwarp();
         if (prod.valid && !ctl[kCtlAbort]) {
-            issue(seq + S, prod);
+            issue(wd, seq + S, prod);
             ++issued;
-            advance(wd, prod);
+            advance(wd, prod, MULTI ? wd.item_counter : wd.stats + kStatNextItem);
+        }
+    }
+    };
+
+    if constexpr (!MULTI) {
+        run_items(wd);
+    } else {
+        // ---- serving step: every block walks the step's slices in order; its warps
+        // draw the items of a slice from the slice's counter (shared by all blocks)
+        // until it is exhausted, so a block waits for its own warps only where it
+        // leaves a slice.  Slices that other blocks have already drained are
+        // skipped; the job's bins and LUT are loaded when the block changes job.
+        WorkDesc& bw = *sptr<WorkDesc>(wd.off_bwd);  // the block's current job
+        volatile uint32_t* take_word = sptr<volatile uint32_t>(wd.off_ctl) + kCtlChunk;
+        const WorkDesc* cur_job = nullptr;  // block-uniform
+        for (int si = 0; si < wd.nslices; ++si) {
+            const StepSlice sl = wd.slices[si];
+            const uint32_t n = sl.pos_end - sl.pos_begin;
+            __syncthreads();
+            if (tid == 0)
+                *take_word = (ctl[kCtlAbort] == 0 &&
+                              *reinterpret_cast<volatile unsigned long long*>(wd.slice_ctr + si) < n) ? 1u : 0u;
+            __syncthreads();
+            if (!*take_word) continue;  // block-uniform
+            if (sl.job != cur_job) {
+                // merge the counters into the previous job's histograms (its row count)
+                if (cur_sub >= 0) {
+                    warp_flush_hist<T>(hc, bw.ne, check, cur_hist);
+                    cur_sub = -1;
+                    cur_hist = nullptr;
+                    inc_bound = 0;
+                    cur_q = 0xffffffffu;
+                }
+                __syncthreads();
+                // the job's description, with this launch's layout, counters and limits
+                {
+                    const uint32_t* src = reinterpret_cast<const uint32_t*>(sl.job);
+                    uint32_t* dst = reinterpret_cast<uint32_t*>(&bw);
+                    for (int k = tid; k < (int)(sizeof(WorkDesc) / 4); k += T) dst[k] = src[k];
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    bw.stats = wd.stats;
+                    bw.flags = wd.flags;
+                    bw.wait_limit_ns = wd.wait_limit_ns;
+                    bw.stages = wd.stages;
+                    bw.I = wd.I;
+                    bw.J = wd.J;
+                    bw.Jc = wd.Jc;
+                    bw.nedges_max = wd.nedges_max;
+                    bw.stage_bytes = wd.stage_bytes;
+                    bw.flush_limit = wd.flush_limit;
+                    bw.off_ctl = wd.off_ctl; bw.off_bars = wd.off_bars; bw.off_meta = wd.off_meta;
+                    bw.off_stage = wd.off_stage; bw.off_hist = wd.off_hist; bw.off_cthr = wd.off_cthr;
+                    bw.off_lo = wd.off_lo; bw.off_hi = wd.off_hi; bw.off_c32 = wd.off_c32; bw.off_zlo = wd.off_zlo;
+                    bw.off_zhi = wd.off_zhi; bw.off_lut = wd.off_lut; bw.off_queue = wd.off_queue;
+                    bw.off_icap = wd.off_icap; bw.off_bwd = wd.off_bwd; bw.off_counter = wd.off_counter;
+                }
+                __syncthreads();
+                load_bins<T>(sub_of(bw, 0).bins, bw, PLAIN);
+                cur_job = sl.job;
+            }
+            if (tid == 0) {
+                bw.item_lo = sl.q_begin;
+                bw.item_hi = (uint64_t)sl.q_begin + n;
+                bw.item_counter = wd.slice_ctr + si;
+            }
+            __syncthreads();
+            run_items(bw);
         }
     }
 
     // ---- merge this warp's columns (skipped after an abort: outputs are invalid)
-    if (!aborted && cur_sub >= 0) warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
+    if (!aborted && cur_sub >= 0) {
+        if constexpr (MULTI) warp_flush_hist<T>(hc, sptr<WorkDesc>(wd.off_bwd)->ne, check, cur_hist);
+        else warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
+    }
     if constexpr (!PLAIN) {
         const unsigned long long b = warp_sum(band_cnt), mm = warp_sum(mism_cnt);
         if (lane == 0) {
@@ -1260,9 +1378,12 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     if (aborted && lane == 0) {
         for (uint32_t s2 = seq; s2 < issued; ++s2) {
             if ((wd.flags & TPCF_F_TEST_WAIT_TIMEOUT) && s2 == 0) continue;
-            (void)mbar_wait_bounded(&bars[s2 % S], (s2 / S) & 1u, wd.wait_limit_ns);
+            (void)mbar_wait_bounded(&TPCF_BARS[s2 % S], (s2 / S) & 1u, wd.wait_limit_ns);
         }
     }
+#undef TPCF_BARS
+#undef TPCF_META
+#undef TPCF_STAGE_BASE
 }
 
 // ============================================================== finalize
@@ -1333,7 +1454,7 @@ cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long l
 // ============================================================== launchers
 // Fills the block constants of the work description (shared-memory offsets of
 // the shape, merge interval) and launches.
-template <int T, int R, int MODE>
+template <int T, int R, int MODE, bool MULTI = false>
 static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t stream) {
     WorkDesc wd = wd_in;
     const SmemLayout L = smem_layout(MODE, T, (int)wd.J, (int)wd.stages, wd.nedges_max);
@@ -1351,26 +1472,35 @@ static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t
     wd.off_lut = L.lut;
     wd.off_queue = L.queue;
     wd.off_icap = L.icap;
+    wd.off_bwd = L.bwd;
+    wd.off_counter = L.counter;
     wd.stage_bytes = wd.J * staged_point_bytes(MODE);
     // the 16-bit counters' merge interval is bounded in the kernel, per tile
     wd.flush_limit = 0xffffu;
     if (L.total > sh.smem || wd.I != 32u * (uint32_t)R) return cudaErrorInvalidValue;
-    count_kernel<T, R, MODE><<<sh.blocks, T, sh.smem, stream>>>(wd);
+    count_kernel<T, R, MODE, MULTI><<<sh.blocks, T, sh.smem, stream>>>(wd);
     return cudaGetLastError();
 }
 
 // The limit is raised to the device's opt-in maximum rather than to `bytes`:
 // the attribute belongs to the kernel, not to a launch, so a smaller value set
 // by one host thread could otherwise undercut a concurrent launch of another.
-template <int T, int R, int MODE>
+template <int T, int R, int MODE, bool MULTI = false>
 static cudaError_t set_smem_t(size_t bytes) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if (bytes > (size_t)optin) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(count_kernel<T, R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    return cudaFuncSetAttribute(count_kernel<T, R, MODE, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
+
+cudaError_t launch_count_step(const WorkDesc& wd, const Shape& sh, cudaStream_t stream) {
+    if (sh.threads != 512 || sh.ipt != 8) return cudaErrorInvalidConfiguration;
+    return launch_t<512, 8, kModeScreen, true>(wd, sh, stream);
+}
+
+cudaError_t count_step_set_smem_limit(size_t bytes) { return set_smem_t<512, 8, kModeScreen, true>(bytes); }
 
 #define TPCF_SHAPES(X) X(128, 8) X(256, 8) X(512, 8) X(256, 16)
 

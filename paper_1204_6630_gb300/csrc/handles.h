@@ -131,4 +131,16 @@ int bins_destroy_impl(tpcf_bins* b);
 size_t catalog_bytes(uint64_t n);
 void server_shutdown(tpcf_ctx* ctx);
 
+// Serving steps (runtime.cpp): the step kernel's shape for histograms of up to
+// nedges_max edges, one served job's work description (RR, DR, DD into three
+// histograms of ne + 1 words at acc), and the launch of a step over slices of
+// many jobs (see StepSlice) or over the items of one job.
+bool serving_shape(tpcf_ctx* ctx, int nedges_max, Shape* sh);
+int serving_job_desc(tpcf_ctx* ctx, const tpcf_catalog* d, const tpcf_catalog* r, const tpcf_bins* b,
+                     const Shape& sh, unsigned long long* acc, WorkDesc* out, uint64_t* n_items, uint64_t* totals);
+int serving_launch(tpcf_ctx* ctx, const Shape& sh, int nedges_max, const StepSlice* slices, int nslices,
+                   unsigned long long* slice_ctr, uint32_t positions, unsigned long long* stats, cudaStream_t st);
+int serving_launch_one(tpcf_ctx* ctx, const Shape& sh, const WorkDesc& job, uint32_t q_begin, uint32_t n,
+                       unsigned long long* stats, cudaStream_t st);
+
 }  // namespace tpcf

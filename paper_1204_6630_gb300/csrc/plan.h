@@ -79,21 +79,27 @@ __host__ __device__ inline ItemGeom item_geom(uint64_t local, uint32_t na, uint3
     return g;
 }
 
+// Pairs of i in [i0, i0 + I) and j in [ja, jb), clipped to the catalogs,
+// with j > i in auto mode.
+__host__ __device__ inline uint64_t span_pairs(uint64_t i0, uint32_t I, uint64_t ja, uint64_t jb, uint32_t na,
+                                               uint32_t nb, bool auto_mode) {
+    if (i0 >= na || ja >= nb || jb <= ja) return 0;
+    const uint64_t iend = umin64(i0 + I, na), jend = umin64(jb, nb);
+    const uint64_t nj = jend - ja;
+    if (!auto_mode) return (iend - i0) * nj;
+    uint64_t total = 0;
+    const uint64_t a_end = umin64(iend, ja);  // i < ja: every j of the span is above i
+    if (a_end > i0) total += (a_end - i0) * nj;
+    const uint64_t a = umax64(i0, ja), b = umin64(iend, jend - 1);  // i inside the span
+    if (b > a) total += (b - a) * (jend - 1) - ((a + b - 1) * (b - a)) / 2;
+    return total;
+}
+
 // Pairs an item counts: i in [i0, i0 + I) and j in [j0, j0 + Jc), clipped to
 // the catalogs, with j > i in auto mode.
 __host__ __device__ inline uint64_t item_pairs(const ItemGeom& g, uint32_t na, uint32_t nb,
                                                bool auto_mode, uint32_t I, uint32_t Jc) {
-    if (g.i0 >= na || g.j0 >= nb) return 0;
-    uint64_t i0 = g.i0, j0 = g.j0;
-    uint64_t iend = umin64(i0 + I, na), jend = umin64(j0 + Jc, nb);
-    uint64_t nj = jend - j0;
-    if (!auto_mode) return (iend - i0) * nj;
-    uint64_t total = 0;
-    uint64_t a_end = umin64(iend, j0);  // i < j0: every j of the chunk is above i
-    if (a_end > i0) total += (a_end - i0) * nj;
-    uint64_t a = umax64(i0, j0), b = umin64(iend, jend - 1);  // i inside the chunk
-    if (b > a) total += (b - a) * (jend - 1) - ((a + b - 1) * (b - a)) / 2;
-    return total;
+    return span_pairs(g.i0, I, g.j0, (uint64_t)g.j0 + Jc, na, nb, auto_mode);
 }
 
 // Walk order of one sub-problem's items: position k (0 <= k < n) visits item

@@ -967,6 +967,65 @@ uint64_t build_work(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const BinsDev
     return items;
 }
 
+// The launch constants of a work description: shape, flags, bin scalars, the
+// chord and index rules, spatial pruning (the sub-problems, statistics words
+// and item range are set by the caller).
+void fill_scalars(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const BinsDev* bh, int mode, const Shape& shp,
+                  bool force_idx, int ne, WorkDesc& wd) {
+    wd.I = 32u * (uint32_t)shp.ipt;
+    wd.J = (uint32_t)shp.jtile;
+    wd.Jc = (uint32_t)shp.jchunk;
+    wd.stages = (uint32_t)shp.stages;
+    wd.flags = ctx->cfg.flags;
+    wd.force_idx = force_idx ? 1u : 0u;
+    wd.nedges_max = ne;
+    wd.ne = ne;
+    wd.euclid = bh->euclid ? 1u : 0u;
+    wd.neg_fast_t = bh->euclid ? bh->fast_t : -bh->fast_t;  // 3-D: +H, angular: -T
+    wd.lut_scale = bh->lut_scale;
+    {
+        const float t = -bh->fast_t;  // the fast loop's packed offset: -T (angles), -H (3-D)
+        uint32_t b;
+        memcpy(&b, &t, 4);
+        wd.neg_fast_t2 = ((unsigned long long)b << 32) | b;
+    }
+    wd.cos_last = bh->cos_last;
+    wd.zbits0 = bh->zbits0;
+    wd.zshift = bh->zshift;
+    // zero-vector padding has screen value e = -T: it can look in range only
+    // when T <= 0 (3-D catalogs are padded with a far point instead); sub-ranges
+    // of segmented catalogs are followed by real points
+    wd.need_idx = (force_idx || (!bh->euclid && !(bh->fast_t > 0.f))) ? 1u : 0u;
+    wd.chord_ok = bh->euclid ? 0u : 1u;
+    for (int s2 = 0; s2 < nsub; ++s2)
+        if (!(specs[s2].a->eps_max <= kChordEpsRef && specs[s2].b->eps_max <= kChordEpsRef)) wd.chord_ok = 0u;
+    wd.wait_limit_ns = (uint64_t)ctx->cfg.wait_timeout_us * 1000ull;
+    // Spatial pruning (screen kernels): a block whose spheres are at least
+    // prune_thr apart (scaled space) holds only overflow pairs.  Angular: a
+    // pair of points with | |v|^2 - 1 | <= eps at distance delta has exact
+    // dot <= 1 + eps - delta^2 / 2, at most C_B - 1e-15 (so the binary64
+    // dot, within 3.4e-16 of it, is <= C_B: overflow) once delta >=
+    // sqrt(2 (1 + eps) - 2 (C_B - 1e-15)).  3-D: delta >= sqrt(S_B) (1 +
+    // 1e-12) makes the binary64 d^2 (relative error < 1e-15) >= S_B.
+    wd.prune = 0u;
+    wd.prune_thr = INFINITY;
+    // (not with a counted overflow row: skipped blocks would have to be counted)
+    if ((ctx->cfg.flags & TPCF_F_PRUNE) && !(ctx->cfg.flags & TPCF_F_CHECK_OVERFLOW) &&
+        (mode == kModeScreenScalar || mode == kModeEuclidScreen)) {
+        double thr;
+        if (bh->euclid) {
+            thr = std::sqrt(bh->cos_last) * (1.0 + 1e-12) * kCapScale3d;
+        } else {
+            double eps = 0.0;
+            for (int s2 = 0; s2 < nsub; ++s2) eps = std::max(eps, std::max(specs[s2].a->eps_max, specs[s2].b->eps_max));
+            thr = std::sqrt(std::max(0.0, 2.0 * (1.0 + eps) - 2.0 * (bh->cos_last - 1e-15)));
+        }
+        const float t32 = (float)thr;
+        wd.prune_thr = (double)t32 >= thr ? t32 : std::nextafter(t32, INFINITY);
+        wd.prune = std::isfinite(wd.prune_thr) ? 1u : 0u;
+    }
+}
+
 int ilog2_u64(uint64_t v) { int k = 0; while (v > 1) { v >>= 1; ++k; } return k; }
 
 // What run_counts leaves behind when it captures the counting sequence into a
@@ -1107,58 +1166,8 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
             wd.item_hi = items * (ctx->cfg.shard_index + 1) / ctx->cfg.shard_count;
         }
         wd.stats = stat_w;
-        wd.I = 32u * (uint32_t)shp.ipt;
-        wd.J = (uint32_t)shp.jtile;
-        wd.Jc = (uint32_t)shp.jchunk;
-        wd.stages = (uint32_t)shp.stages;
-        wd.flags = ctx->cfg.flags;
-        wd.force_idx = force_idx ? 1u : 0u;
-        wd.nedges_max = ne;
-        wd.ne = ne;
-        wd.euclid = bh->euclid ? 1u : 0u;
-        wd.neg_fast_t = bh->euclid ? bh->fast_t : -bh->fast_t;  // 3-D: +H, angular: -T
-        wd.lut_scale = bh->lut_scale;
-        {
-            const float t = -bh->fast_t;  // the fast loop's packed offset: -T (angles), -H (3-D)
-            uint32_t b;
-            memcpy(&b, &t, 4);
-            wd.neg_fast_t2 = ((unsigned long long)b << 32) | b;
-        }
-        wd.cos_last = bh->cos_last;
-        wd.zbits0 = bh->zbits0;
-        wd.zshift = bh->zshift;
-        // zero-vector padding has screen value e = -T: it can look in range only
-        // when T <= 0 (3-D catalogs are padded with a far point instead); sub-ranges
-        // of segmented catalogs are followed by real points
-        wd.need_idx = (force_idx || (!bh->euclid && !(bh->fast_t > 0.f))) ? 1u : 0u;
-        wd.chord_ok = bh->euclid ? 0u : 1u;
-        for (int s2 = 0; s2 < nsub; ++s2)
-            if (!(specs[s2].a->eps_max <= kChordEpsRef && specs[s2].b->eps_max <= kChordEpsRef)) wd.chord_ok = 0u;
-        wd.wait_limit_ns = (uint64_t)ctx->cfg.wait_timeout_us * 1000ull;
-        // Spatial pruning (screen kernels): a block whose spheres are at least
-        // prune_thr apart (scaled space) holds only overflow pairs.  Angular: a
-        // pair of points with | |v|^2 - 1 | <= eps at distance delta has exact
-        // dot <= 1 + eps - delta^2 / 2, at most C_B - 1e-15 (so the binary64
-        // dot, within 3.4e-16 of it, is <= C_B: overflow) once delta >=
-        // sqrt(2 (1 + eps) - 2 (C_B - 1e-15)).  3-D: delta >= sqrt(S_B) (1 +
-        // 1e-12) makes the binary64 d^2 (relative error < 1e-15) >= S_B.
-        wd.prune = 0u;
-        wd.prune_thr = INFINITY;
-        // (not with a counted overflow row: skipped blocks would have to be counted)
-        if ((ctx->cfg.flags & TPCF_F_PRUNE) && !(ctx->cfg.flags & TPCF_F_CHECK_OVERFLOW) &&
-            (mode == kModeScreenScalar || mode == kModeEuclidScreen)) {
-            double thr;
-            if (bh->euclid) {
-                thr = std::sqrt(bh->cos_last) * (1.0 + 1e-12) * kCapScale3d;
-            } else {
-                double eps = 0.0;
-                for (int s2 = 0; s2 < nsub; ++s2) eps = std::max(eps, std::max(specs[s2].a->eps_max, specs[s2].b->eps_max));
-                thr = std::sqrt(std::max(0.0, 2.0 * (1.0 + eps) - 2.0 * (bh->cos_last - 1e-15)));
-            }
-            const float t32 = (float)thr;
-            wd.prune_thr = (double)t32 >= thr ? t32 : std::nextafter(t32, INFINITY);
-            wd.prune = std::isfinite(wd.prune_thr) ? 1u : 0u;
-        }
+        wd.item_counter = stat_w + kStatNextItem;
+        fill_scalars(ctx, specs, nsub, bh, mode, shp, force_idx, ne, wd);
         return TPCF_OK;
     };
     auto launch = [&](const Shape& shp) -> cudaError_t {
@@ -1330,6 +1339,97 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
 }
 
 }  // namespace
+
+// ====================================================================== serving steps
+// Shape of a serving step (the multi-job kernel exists for 512 x 8): j-tiles of
+// 256 points, or 128 where the step's histograms need the shared memory;
+// false when neither fits.
+bool tpcf::serving_shape(tpcf_ctx* ctx, int nedges_max, Shape* sh) {
+    return shape_for(ctx, kModeScreenScalar, nedges_max, 512, 8, 0, 2, sh);
+}
+
+// Work description of one served job for the serving-step kernel: the
+// sub-problems RR, DR and DD of catalogs (d, r) with bins b, accumulating
+// into three histograms of ne + 1 words at acc (in that order); also the
+// job's item count and the three histograms' pair totals.
+int tpcf::serving_job_desc(tpcf_ctx* ctx, const tpcf_catalog* d, const tpcf_catalog* r, const tpcf_bins* b,
+                           const Shape& sh, unsigned long long* acc, WorkDesc* out, uint64_t* n_items,
+                           uint64_t* totals) {
+    if (b->euclid || d->euclid || r->euclid) return TPCF_EINVAL;
+    SubSpec specs[3] = {{r, r, true, (uint32_t)r->n, (uint32_t)r->n, 0, 0},
+                        {d, r, false, (uint32_t)d->n, (uint32_t)r->n, 0, 0},
+                        {d, d, true, (uint32_t)d->n, (uint32_t)d->n, 0, 0}};
+    std::vector<SubProblem> subs;
+    const uint64_t items = build_work(ctx, specs, 3, b->dev_desc, sh, acc, (size_t)b->nedges + 1, subs);
+    if (items > 0xffff0000ull) return TPCF_EOVERFLOW;
+    WorkDesc wd;
+    memset(&wd, 0, sizeof wd);
+    for (int k = 0; k < 3; ++k) wd.sub[k] = subs[k];
+    wd.sub_dev = nullptr;
+    wd.nsub = 3;
+    wd.item_lo = 0;
+    wd.item_hi = items;
+    fill_scalars(ctx, specs, 3, &b->host, kModeScreenScalar, sh, false, b->nedges, wd);
+    *out = wd;
+    *n_items = items;
+    for (int k = 0; k < 3; ++k) totals[k] = full_pairs(specs[k]);
+    return TPCF_OK;
+}
+
+// One serving step: slices (device, sorted by position) of `positions` work
+// items in all, into the jobs' own accumulators; slice_ctr: one device counter
+// per slice and stats: kStatWords device words, all zeroed by the caller.
+int tpcf::serving_launch(tpcf_ctx* ctx, const Shape& sh, int nedges_max, const StepSlice* slices, int nslices,
+                         unsigned long long* slice_ctr, uint32_t positions, unsigned long long* stats,
+                         cudaStream_t st) {
+    WorkDesc wd;
+    memset(&wd, 0, sizeof wd);
+    wd.stats = stats;
+    wd.item_counter = stats + kStatNextItem;
+    wd.slices = slices;
+    wd.slice_ctr = slice_ctr;
+    wd.nslices = nslices;
+    wd.step_positions = positions;
+    wd.I = 32u * (uint32_t)sh.ipt;
+    wd.J = (uint32_t)sh.jtile;
+    wd.Jc = (uint32_t)sh.jchunk;
+    wd.stages = (uint32_t)sh.stages;
+    wd.flags = ctx->cfg.flags;
+    wd.nedges_max = nedges_max;
+    wd.wait_limit_ns = (uint64_t)ctx->cfg.wait_timeout_us * 1000ull;
+    Shape s2 = sh;  // (no more blocks than the step has items for their warps)
+    const uint64_t warps = (uint64_t)sh.threads / 32;
+    const uint64_t need = ((uint64_t)positions + warps - 1) / warps;
+    if ((uint64_t)s2.blocks > need) s2.blocks = (int)std::max<uint64_t>(1, need);
+    if (count_step_set_smem_limit(sh.smem) != cudaSuccess) return TPCF_ECUDA;
+    if (launch_count_step(wd, s2, st) != cudaSuccess) return TPCF_ECUDA;
+    ctx->launches.fetch_add(1);
+    return TPCF_OK;
+}
+
+// One serving step that holds the items [q_begin, q_begin + n) of a single
+// job (job: its work description from serving_job_desc): the one-job kernel,
+// which reads the description from its parameter; stats: kStatWords device
+// words zeroed by the caller (its item counter included).
+int tpcf::serving_launch_one(tpcf_ctx* ctx, const Shape& sh, const WorkDesc& job, uint32_t q_begin, uint32_t n,
+                             unsigned long long* stats, cudaStream_t st) {
+    WorkDesc wd = job;
+    wd.item_lo = q_begin;
+    wd.item_hi = (uint64_t)q_begin + n;
+    wd.stats = stats;
+    wd.item_counter = stats + kStatNextItem;
+    wd.slices = nullptr;
+    wd.slice_ctr = nullptr;
+    wd.nslices = 0;
+    Shape s2 = sh;
+    const uint64_t warps = (uint64_t)sh.threads / 32;
+    const uint64_t need = ((uint64_t)n + warps - 1) / warps;
+    if ((uint64_t)s2.blocks > need) s2.blocks = (int)std::max<uint64_t>(1, need);
+    if (count_set_smem_limit(kModeScreenScalar, sh.threads, sh.ipt, sh.smem) != cudaSuccess) return TPCF_ECUDA;
+    if (launch_count(wd, s2, kModeScreenScalar, wd.ne, st) != cudaSuccess) return TPCF_ECUDA;
+    ctx->launches.fetch_add(1);
+    return TPCF_OK;
+}
 
 // ====================================================================== counting ABI
 extern "C" int tpcf_count_auto(tpcf_ctx* ctx, const tpcf_catalog* cat, const tpcf_bins* bins,

@@ -1,21 +1,35 @@
-// Pair-count job server: tpcf_submit / tpcf_poll / tpcf_cancel.
+// Pair-count job server: tpcf_submit / tpcf_poll / tpcf_cancel, with
+// continuous batching.
 //
-// Jobs (a data and a random catalog plus bin edges, all host arrays copied at
-// submission) wait in a queue until the device memory they need fits in the
-// context's budget; then one of the server's worker threads runs the whole
-// path on its own CUDA stream: upload and preparation of both catalogs,
-// thresholds, one fused DD/DR/RR launch, and the estimator.  Several jobs are
-// in flight at once, so their kernels overlap on the device and a job that
-// arrives while others run starts as soon as a worker and memory are free
-// (the admission decision is made again whenever a job finishes).  Buffers of
-// running jobs are allocated and freed in stream order, so one job's
-// completion never synchronizes the device under the others.
+// A submitted job (a data and a random catalog plus bin edges, host arrays
+// copied at submission) waits in a queue until one of the server's slots
+// (cfg.server_workers jobs in flight) and the device memory it needs (within
+// cfg.hbm_budget_bytes) are free.  It is then admitted: a preparation worker
+// uploads and prepares both catalogs and the bins on its own stream and builds
+// the job's work description (the items of its DD, DR and RR) and
+// accumulators in device memory, which stay resident until the job completes.
+//
+// One scheduler thread runs the counting work of all admitted jobs as a
+// sequence of steps.  A step is one launch of the serving-step kernel over
+// slices of many jobs' item ranges, each job with its own bins and
+// histograms: a step gives every job with little work left all of it, then
+// fills a pair budget with the others in admission order.  A job admitted
+// while a step runs joins the next one, so its work overlaps the work already
+// on the device instead of waiting for it.  Up to two steps are queued on the
+// device; the finalize (overflow = pair total - sum of the other entries) and
+// the copy of a job's histograms follow its last step on the same stream, and
+// the estimator runs on the host.  Every item of a job is counted exactly
+// once, whichever steps it lands in, so a job's histograms are those of a lone
+// call.  Jobs whose histograms do not fit the step kernel's shared memory are
+// counted alone by their preparation worker.
 //
 // Paper: the three histograms of Eq. 1 for each job (Section 1), counted as in
-// Section 3; the queue and admission logic have no counterpart in the paper.
+// Section 3; admission, batching and scheduling have no counterpart in the
+// paper.
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -33,10 +47,18 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// A step gives all of its remaining items to a job with at most this many
+// pairs left, and fills up to kStepPairs pairs in all.
+constexpr double kSmallJobPairs = 2e10;
+constexpr double kStepPairs = 1.5e11;
+constexpr int kStepsInFlight = 2;
+constexpr int kDefaultSlots = 32;
+constexpr int kPrepWorkers = 4;
+
 }  // namespace
 
 struct Job {
-    enum State { kQueued, kRunning, kDone };
+    enum State { kQueued, kPreparing, kActive, kDone };
     uint64_t id = 0;
     std::vector<double> d, r, edges;
     int estimator = TPCF_LS_EXACT;
@@ -48,31 +70,103 @@ struct Job {
     std::vector<double> w;
     double t_submit = 0, t_start = 0, t_done = 0, kernel_ms = 0;
     uint64_t pairs = 0;
+    // while admitted
+    int slot = -1;                        // index of the job's pinned result buffer
+    uint64_t nd = 0, nr = 0;
+    tpcf_catalog *cd = nullptr, *cr = nullptr;
+    tpcf_bins* b = nullptr;
+    void* dev = nullptr;                  // accumulators, pair totals, work description
+    unsigned long long* acc = nullptr;    // RR | DR | DD, ne + 1 words each
+    unsigned long long* dtot = nullptr;   // their pair totals
+    WorkDesc* dwd = nullptr;              // its work description on the device (step slices point here)
+    WorkDesc hwd{};                       // and on the host (steps that hold only this job)
+    Shape sh{};                           // the shape the description was built for
+    uint64_t n_items = 0, next = 0;       // items of the job / scheduled so far
+    double pairs_per_item = 0;
+    int inflight = 0;                     // steps with slices of the job that have not finished
+    bool solo = false;                    // counted alone (outside the steps)
+};
+
+// One step on the device: its slices, the jobs it holds, those it completes.
+struct Step {
+    int buf = 0;                          // index of its slice / statistics buffers and stream
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaEvent_t kdone = nullptr;          // its counting launch has finished
+    std::vector<std::shared_ptr<Job>> jobs, finals;
 };
 
 class JobServer {
   public:
-    JobServer(tpcf_ctx* ctx, int workers, size_t budget) : ctx_(ctx), budget_(budget) {
+    JobServer(tpcf_ctx* ctx, int slots, size_t budget) : ctx_(ctx), budget_(budget), slots_(slots) {
         t0_ = std::chrono::steady_clock::now();
-        for (int i = 0; i < workers; ++i) {
-            cudaStream_t s = nullptr;
-            cudaSetDevice(ctx->cfg.device);
-            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-            streams_.push_back(s);
+        cudaSetDevice(ctx->cfg.device);
+        // one compute stream per step in flight: a step's blocks start on the SMs that
+        // the previous step's blocks leave, so the end of one launch (its last,
+        // slowest items) overlaps the start of the next
+        for (int k = 0; k < kStepsInFlight; ++k)
+            ok_ = (k == 0 || ok_) && cudaStreamCreateWithFlags(&streams_[k], cudaStreamNonBlocking) == cudaSuccess;
+        // frees of finished jobs go on a stream with no work queued: the host has seen every
+        // step that used the memory finish, and an allocation that reuses it (a new job's,
+        // on a preparation stream) then waits for no running step
+        ok_ = ok_ && cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking) == cudaSuccess;
+        // pinned result buffers (one per slot: 3 histograms of up to TPCF_MAX_EDGES + 1 words) and
+        // per-step-buffer slices and statistics words
+        const size_t res_words = 3 * (size_t)(TPCF_MAX_EDGES + 1);
+        ok_ = ok_ && cudaHostAlloc((void**)&h_res_, (size_t)slots * res_words * 8, cudaHostAllocDefault) == cudaSuccess;
+        for (int k = 0; k < kStepsInFlight && ok_; ++k) {
+            ok_ = cudaHostAlloc((void**)&h_slices_[k], (size_t)slots * sizeof(StepSlice), cudaHostAllocDefault) ==
+                      cudaSuccess &&
+                  cudaHostAlloc((void**)&h_stats_[k], kStatWords * 8, cudaHostAllocDefault) == cudaSuccess &&
+                  dev_malloc((void**)&d_slices_[k], (size_t)slots * sizeof(StepSlice)) == cudaSuccess &&
+                  dev_malloc((void**)&d_stats_[k], (kStatWords + (size_t)slots) * 8) == cudaSuccess;
         }
-        for (int i = 0; i < workers; ++i) threads_.emplace_back([this, i] { worker(i); });
+        for (int k = 0; k < slots; ++k) free_slots_.push_back(k);
+        // preparation streams at the highest priority: a new job's preparation kernels run as
+        // soon as a step's blocks leave the SMs
+        int lo_prio = 0, hi_prio = 0;
+        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+        for (int i = 0; i < kPrepWorkers; ++i) {
+            cudaStream_t s = nullptr;
+            cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, hi_prio);
+            prep_streams_.push_back(s);
+        }
+        for (int i = 0; i < kPrepWorkers; ++i) prep_threads_.emplace_back([this, i] { prep_worker(i); });
+        sched_thread_ = std::thread([this] { scheduler(); });
     }
 
     ~JobServer() {
         {
             std::lock_guard<std::mutex> g(mu_);
             stop_ = true;
+            // queued jobs are dropped; admitted ones run to completion
+            for (auto& j : queue_) {
+                j->state = Job::kDone;
+                j->status = TPCF_ECANCELED;
+            }
+            queue_.clear();
         }
-        cv_work_.notify_all();
-        for (auto& t : threads_) t.join();
-        for (auto s : streams_) cudaStreamDestroy(s);
+        cv_prep_.notify_all();
+        cv_sched_.notify_all();
+        for (auto& t : prep_threads_) t.join();
+        sched_thread_.join();
+        cudaSetDevice(ctx_->cfg.device);
+        for (int k = 0; k < kStepsInFlight; ++k)
+            if (streams_[k]) cudaStreamSynchronize(streams_[k]);
+        if (stream_) cudaStreamSynchronize(stream_);
+        for (int k = 0; k < kStepsInFlight; ++k) {
+            if (d_slices_[k]) cudaFree(d_slices_[k]);
+            if (d_stats_[k]) cudaFree(d_stats_[k]);
+            if (h_slices_[k]) cudaFreeHost(h_slices_[k]);
+            if (h_stats_[k]) cudaFreeHost(h_stats_[k]);
+        }
+        if (h_res_) cudaFreeHost(h_res_);
+        for (auto s : prep_streams_) cudaStreamDestroy(s);
+        for (int k = 0; k < kStepsInFlight; ++k)
+            if (streams_[k]) cudaStreamDestroy(streams_[k]);
+        if (stream_) cudaStreamDestroy(stream_);
     }
 
+    bool ok() const { return ok_; }
     size_t budget() const { return budget_; }
 
     int submit(const tpcf_job* job, uint64_t* id) {
@@ -81,10 +175,13 @@ class JobServer {
         j->r.assign(job->r_xyz, job->r_xyz + 3 * job->nr);
         j->edges.assign(job->edges_rad, job->edges_rad + job->nedges);
         j->estimator = job->estimator;
+        j->nd = job->nd;
+        j->nr = job->nr;
         const uint64_t nmax = job->nd > job->nr ? job->nd : job->nr;
         uint64_t n_pow2 = 2048;
         while (n_pow2 < nmax) n_pow2 <<= 1;
-        // both catalogs, the preparation scratch of one (staging + sort keys), bins and accumulators
+        // both catalogs, the preparation scratch of one (staging + sort keys), bins, accumulators
+        // and the work description
         j->bytes = catalog_bytes(job->nd) + catalog_bytes(job->nr) + nmax * 24 + n_pow2 * 12 + (1u << 20);
         if (j->bytes > budget_) return TPCF_EBUDGET;
         std::lock_guard<std::mutex> g(mu_);
@@ -94,7 +191,7 @@ class JobServer {
         jobs_[j->id] = j;
         queue_.push_back(j);
         *id = j->id;
-        cv_work_.notify_one();
+        try_admit();
         return TPCF_OK;
     }
 
@@ -142,95 +239,372 @@ class JobServer {
             j->status = TPCF_ECANCELED;
             j->t_start = j->t_done = ms_since(t0_);
             cv_done_.notify_all();
-        } else if (j->state == Job::kRunning) {
-            j->cancel = true;  // the device work finishes; its result is dropped
+        } else if (j->state != Job::kDone) {
+            j->cancel = true;  // work already on the device finishes; its result is dropped
         }
         return TPCF_OK;
     }
 
   private:
-    // First queued job (in submission order) whose memory fits the budget.
-    std::shared_ptr<Job> take_admissible() {
-        for (auto q = queue_.begin(); q != queue_.end(); ++q) {
-            if (in_use_ + (*q)->bytes <= budget_) {
-                std::shared_ptr<Job> j = *q;
-                queue_.erase(q);
-                return j;
+    // Admits queued jobs (in submission order; a job that does not fit the
+    // memory left lets later ones that fit go first) while slots are free.
+    // Called with mu_ held.
+    void try_admit() {
+        bool any = false;
+        for (auto q = queue_.begin(); q != queue_.end() && !free_slots_.empty();) {
+            std::shared_ptr<Job> j = *q;
+            if (in_use_ + j->bytes > budget_) {
+                ++q;
+                continue;
             }
+            q = queue_.erase(q);
+            in_use_ += j->bytes;
+            j->slot = free_slots_.back();
+            free_slots_.pop_back();
+            j->state = Job::kPreparing;
+            j->t_start = ms_since(t0_);
+            prep_queue_.push_back(j);
+            any = true;
         }
-        return nullptr;
+        if (any) cv_prep_.notify_all();
     }
 
-    void worker(int idx) {
+    uint64_t* res_buf(const Job& j) const { return h_res_ + (size_t)j.slot * 3 * (TPCF_MAX_EDGES + 1); }
+
+    // Ends a job (mu_ held): results from the pinned buffer when it completed,
+    // device memory released, the budget and slot given back.
+    void finish(Job& j, int status) {
+        const int ne = (int)j.edges.size();
+        if (status == TPCF_OK && j.cancel) status = TPCF_ECANCELED;
+        if (status == TPCF_OK && !j.solo) {
+            const uint64_t* h = res_buf(j);
+            j.rr.assign(h, h + ne + 1);
+            j.dr.assign(h + (ne + 1), h + 2 * (ne + 1));
+            j.dd.assign(h + 2 * (ne + 1), h + 3 * (ne + 1));
+        }
+        if (status == TPCF_OK) {
+            j.w.assign(ne - 1, NAN);
+            if (j.nd >= 2 && j.nr >= 2)
+                tpcf_estimate(j.dd.data() + 1, j.dr.data() + 1, j.rr.data() + 1, ne - 1, j.nd, j.nr, j.estimator,
+                              j.w.data());
+        }
+        release(j);
+        j.status = status;
+        j.state = Job::kDone;
+        j.t_done = ms_since(t0_);
+        std::vector<double>().swap(j.d);
+        std::vector<double>().swap(j.r);
+        cv_done_.notify_all();
+        try_admit();
+    }
+
+    // Device memory of a job (every step that used it has finished: freed on the
+    // idle free stream), and its budget and slot.
+    void release(Job& j) {
         cudaSetDevice(ctx_->cfg.device);
-        cudaStream_t st = streams_[idx];
+        if (j.cd) {
+            j.cd->free_stream = stream_;
+            catalog_destroy_impl(j.cd);
+            j.cd = nullptr;
+        }
+        if (j.cr) {
+            j.cr->free_stream = stream_;
+            catalog_destroy_impl(j.cr);
+            j.cr = nullptr;
+        }
+        if (j.b) {  // the bins' upload finished during preparation: no synchronization needed
+            if (j.b->dev_buf) cudaFreeAsync(j.b->dev_buf, stream_);
+            delete j.b;
+            j.b = nullptr;
+        }
+        if (j.dev) {
+            cudaFreeAsync(j.dev, stream_);
+            j.dev = nullptr;
+        }
+        if (j.slot >= 0) {
+            free_slots_.push_back(j.slot);
+            j.slot = -1;
+        }
+        in_use_ -= j.bytes;
+        j.bytes = 0;
+    }
+
+    // ---------------------------------------------------------------- preparation
+    void prep_worker(int idx) {
+        cudaSetDevice(ctx_->cfg.device);
+        cudaStream_t st = prep_streams_[idx];
         for (;;) {
             std::shared_ptr<Job> j;
             {
                 std::unique_lock<std::mutex> g(mu_);
-                cv_work_.wait(g, [&] { return stop_ || (j = take_admissible()) != nullptr; });
-                if (!j) return;  // stopping
-                in_use_ += j->bytes;
-                j->state = Job::kRunning;
-                j->t_start = ms_since(t0_);
+                cv_prep_.wait(g, [&] { return stop_ || !prep_queue_.empty(); });
+                if (prep_queue_.empty()) return;  // stopping
+                j = prep_queue_.front();
+                prep_queue_.pop_front();
             }
-            run(*j, st);
-            {
-                std::lock_guard<std::mutex> g(mu_);
-                in_use_ -= j->bytes;
-                if (j->cancel) j->status = TPCF_ECANCELED;
-                j->state = Job::kDone;
-                j->t_done = ms_since(t0_);
+            const int rc = prepare(*j, st);
+            std::lock_guard<std::mutex> g(mu_);
+            if (rc != TPCF_OK || j->cancel || j->solo) {
+                finish(*j, rc);
+            } else {
+                j->state = Job::kActive;
+                active_.push_back(j);
+                cv_sched_.notify_all();
             }
-            cv_done_.notify_all();
-            cv_work_.notify_all();  // memory freed: queued jobs may fit now
         }
     }
 
-    void run(Job& j, cudaStream_t st) {
+    // Catalogs, bins, accumulators and the work description of a job (its own
+    // stream, synchronously); a job whose histograms do not fit the step kernel
+    // is counted here alone.
+    int prepare(Job& j, cudaStream_t st) {
         const int ne = (int)j.edges.size();
-        const uint64_t nd = j.d.size() / 3, nr = j.r.size() / 3;
-        tpcf_catalog *cd = nullptr, *cr = nullptr;
-        tpcf_bins* b = nullptr;
+        int rc = catalog_create_impl(ctx_, j.d.data(), j.nd, TPCF_HOST, nullptr, 0, st, true, &j.cd);
+        if (rc == TPCF_OK) rc = catalog_create_impl(ctx_, j.r.data(), j.nr, TPCF_HOST, nullptr, 0, st, true, &j.cr);
+        if (rc == TPCF_OK) rc = bins_create_impl(ctx_, j.edges.data(), ne, st, true, &j.b);
+        if (rc != TPCF_OK) return rc;
+        uint64_t totals[3] = {0, 0, 0};
+        Shape sh;
+        j.solo = !serving_shape(ctx_, ne, &sh);
+        if (!j.solo) {
+            const size_t acc_b = 3ull * (ne + 1) * 8, tot_b = 3 * 8;
+            const size_t off_wd = (acc_b + tot_b + 255) / 256 * 256;
+            if (dev_malloc_async(&j.dev, off_wd + sizeof(WorkDesc), st) != cudaSuccess) return TPCF_ENOMEM;
+            j.acc = (unsigned long long*)j.dev;
+            j.dtot = j.acc + 3 * (ne + 1);
+            j.dwd = (WorkDesc*)((char*)j.dev + off_wd);
+            WorkDesc wd;
+            rc = serving_job_desc(ctx_, j.cd, j.cr, j.b, sh, j.acc, &wd, &j.n_items, totals);
+            if (rc != TPCF_OK) return rc;
+            j.hwd = wd;
+            j.sh = sh;
+            if (cudaMemsetAsync(j.acc, 0, acc_b, st) != cudaSuccess ||
+                cudaMemcpyAsync(j.dtot, totals, tot_b, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(j.dwd, &wd, sizeof wd, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return TPCF_ECUDA;
+            j.pairs = totals[0] + totals[1] + totals[2];
+            j.pairs_per_item = j.n_items ? (double)j.pairs / (double)j.n_items : 0.0;
+            // a job without items (every histogram empty) needs no step
+            if (j.n_items == 0) {
+                uint64_t* h = res_buf(j);
+                memset(h, 0, 3ull * (ne + 1) * 8);
+                j.solo = false;
+            }
+            return TPCF_OK;
+        }
+        // counted alone
         j.dd.assign(ne + 1, 0);
         j.dr.assign(ne + 1, 0);
         j.rr.assign(ne + 1, 0);
-        int rc = catalog_create_impl(ctx_, j.d.data(), nd, TPCF_HOST, nullptr, 0, st, true, &cd);
-        if (rc == TPCF_OK) rc = catalog_create_impl(ctx_, j.r.data(), nr, TPCF_HOST, nullptr, 0, st, true, &cr);
-        if (rc == TPCF_OK) rc = bins_create_impl(ctx_, j.edges.data(), ne, st, true, &b);
         tpcf_stats stats;
         memset(&stats, 0, sizeof stats);
-        if (rc == TPCF_OK)
-            rc = tpcf_count_all(ctx_, cd, cr, b, st, j.dd.data(), j.dr.data(), j.rr.data(), TPCF_HOST, &stats);
-        if (rc == TPCF_OK) {
-            j.w.assign(ne - 1, NAN);
-            if (nd >= 2 && nr >= 2)
-                tpcf_estimate(j.dd.data() + 1, j.dr.data() + 1, j.rr.data() + 1, ne - 1, nd, nr, j.estimator,
-                              j.w.data());
-            j.kernel_ms = stats.kernel_ms;
-            j.pairs = stats.pairs;
-        }
-        if (b) bins_destroy_impl(b);
-        if (cd) catalog_destroy_impl(cd);
-        if (cr) catalog_destroy_impl(cr);
+        rc = tpcf_count_all(ctx_, j.cd, j.cr, j.b, st, j.dd.data(), j.dr.data(), j.rr.data(), TPCF_HOST, &stats);
+        j.kernel_ms = stats.kernel_ms;
+        j.pairs = stats.pairs;
         cudaStreamSynchronize(st);
-        j.status = rc;
-        // the host copies of the inputs are no longer needed
-        std::vector<double>().swap(j.d);
-        std::vector<double>().swap(j.r);
+        return rc;
+    }
+
+    // ---------------------------------------------------------------- steps
+    // Builds and launches the next step (mu_ held); false when no admitted job
+    // has work left to schedule.
+    bool launch_step() {
+        std::vector<std::shared_ptr<Job>> pick;
+        std::vector<uint64_t> take;
+        double used = 0;
+        auto consider = [&](bool small_pass) {
+            for (auto& j : active_) {
+                if (j->cancel || j->next >= j->n_items) continue;
+                if (std::find(pick.begin(), pick.end(), j) != pick.end()) continue;
+                const uint64_t left = j->n_items - j->next;
+                const double left_pairs = (double)left * j->pairs_per_item;
+                uint64_t n = 0;
+                if (small_pass) {
+                    if (left_pairs <= kSmallJobPairs) n = left;
+                } else if (used < kStepPairs) {
+                    const double room = kStepPairs - used;
+                    n = j->pairs_per_item > 0 ? (uint64_t)std::ceil(room / j->pairs_per_item) : left;
+                    n = std::max<uint64_t>(1, std::min(n, left));
+                }
+                if (n == 0) continue;
+                pick.push_back(j);
+                take.push_back(n);
+                used += (double)n * j->pairs_per_item;
+                if ((int)pick.size() >= slots_) return;
+            }
+        };
+        consider(true);
+        consider(false);
+        if (pick.empty()) return false;
+
+        Step step;
+        step.buf = step_seq_++ % kStepsInFlight;
+        StepSlice* hs = h_slices_[step.buf];
+        uint32_t pos = 0;
+        int ne_max = 2;
+        for (size_t k = 0; k < pick.size(); ++k) {
+            Job& j = *pick[k];
+            hs[k].job = j.dwd;
+            hs[k].q_begin = (uint32_t)j.next;
+            hs[k].pos_begin = pos;
+            pos += (uint32_t)take[k];
+            hs[k].pos_end = pos;
+            hs[k].pad = 0;
+            j.next += take[k];
+            ++j.inflight;
+            ne_max = std::max(ne_max, (int)j.edges.size());
+            step.jobs.push_back(pick[k]);
+            if (j.next == j.n_items) step.finals.push_back(pick[k]);
+        }
+        Shape sh;
+        int rc = serving_shape(ctx_, ne_max, &sh) ? TPCF_OK : TPCF_EINVAL;
+        cudaStream_t ss = streams_[step.buf];
+        cudaEventCreate(&step.t0);
+        cudaEventCreate(&step.t1);
+        cudaEventCreateWithFlags(&step.kdone, cudaEventDisableTiming);
+        cudaEventRecord(step.t0, ss);
+        if (rc == TPCF_OK &&
+            (cudaMemcpyAsync(d_slices_[step.buf], hs, pick.size() * sizeof(StepSlice), cudaMemcpyHostToDevice,
+                             ss) != cudaSuccess ||
+             cudaMemsetAsync(d_stats_[step.buf], 0, (kStatWords + pick.size()) * 8, ss) != cudaSuccess))
+            rc = TPCF_ECUDA;
+        // a step of one job runs the one-job kernel (its description in the
+        // kernel parameter), a step of several the step kernel
+        if (rc == TPCF_OK && pick.size() == 1)
+            rc = serving_launch_one(ctx_, pick[0]->sh, pick[0]->hwd, hs[0].q_begin, pos, d_stats_[step.buf], ss);
+        else if (rc == TPCF_OK)
+            rc = serving_launch(ctx_, sh, ne_max, d_slices_[step.buf], (int)pick.size(),
+                                d_stats_[step.buf] + kStatWords, pos, d_stats_[step.buf], ss);
+        cudaEventRecord(step.kdone, ss);
+        // the jobs this step completes: overflow from the pair totals, histograms to the host,
+        // once the previous step (on the other stream, possibly with slices of the same jobs)
+        // has counted too
+        if (rc == TPCF_OK && !step.finals.empty() && !steps_.empty() &&
+            cudaStreamWaitEvent(ss, steps_.back().kdone, 0) != cudaSuccess)
+            rc = TPCF_ECUDA;
+        for (auto& jp : step.finals) {
+            Job& j = *jp;
+            const int ne = (int)j.edges.size();
+            if (rc == TPCF_OK &&
+                (launch_finalize_batch(j.acc, ne + 1, ne, j.acc, ne + 1, j.dtot, 3,
+                                       (ctx_->cfg.flags & TPCF_F_CHECK_OVERFLOW) ? 1 : 0,
+                                       d_stats_[step.buf] + kStatError, ss) != cudaSuccess ||
+                 cudaMemcpyAsync(res_buf(j), j.acc, 3ull * (ne + 1) * 8, cudaMemcpyDeviceToHost, ss) != cudaSuccess))
+                rc = TPCF_ECUDA;
+        }
+        if (rc == TPCF_OK &&
+            cudaMemcpyAsync(h_stats_[step.buf], d_stats_[step.buf], kStatWords * 8, cudaMemcpyDeviceToHost, ss) !=
+                cudaSuccess)
+            rc = TPCF_ECUDA;
+        cudaEventRecord(step.t1, ss);
+        step_rc_.push_back(rc);
+        steps_.push_back(std::move(step));
+        return true;
+    }
+
+    // The oldest step has finished (mu_ held): job bookkeeping, completions.
+    void complete_step() {
+        Step step = std::move(steps_.front());
+        steps_.pop_front();
+        int rc = step_rc_.front();
+        step_rc_.pop_front();
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, step.t0, step.t1);
+        const unsigned long long err = h_stats_[step.buf][kStatError];
+        if (rc == TPCF_OK && (err & kErrWaitTimeout)) rc = TPCF_ETIMEOUT;
+        else if (rc == TPCF_OK && err) rc = TPCF_ECUDA;
+        for (auto& jp : step.jobs) {
+            Job& j = *jp;
+            --j.inflight;
+            j.kernel_ms += ms;
+            if (rc != TPCF_OK) {
+                j.status = rc;
+                j.next = j.n_items;  // nothing more is scheduled for it
+            }
+        }
+        for (auto& jp : step.jobs) {
+            Job& j = *jp;
+            if (j.state == Job::kDone || j.inflight > 0) continue;
+            if (j.next >= j.n_items || j.cancel) {
+                active_.erase(std::remove(active_.begin(), active_.end(), jp), active_.end());
+                finish(j, j.status != TPCF_OK ? j.status : TPCF_OK);
+            }
+        }
+        cudaEventDestroy(step.t0);
+        cudaEventDestroy(step.t1);
+        cudaEventDestroy(step.kdone);
+    }
+
+    // Jobs without items and cancelled jobs that hold no step (mu_ held).
+    void settle_idle_jobs() {
+        for (auto it = active_.begin(); it != active_.end();) {
+            Job& j = **it;
+            if (j.inflight == 0 && (j.n_items == 0 || (j.cancel && j.next < j.n_items) ||
+                                    (j.next >= j.n_items && j.status != TPCF_OK))) {
+                std::shared_ptr<Job> keep = *it;
+                it = active_.erase(it);
+                finish(j, j.status);
+            } else {
+                ++it;
+            }
+        }
+    }
+
+    void scheduler() {
+        cudaSetDevice(ctx_->cfg.device);
+        std::unique_lock<std::mutex> g(mu_);
+        for (;;) {
+            settle_idle_jobs();
+            while ((int)steps_.size() < kStepsInFlight && launch_step()) {
+            }
+            if (steps_.empty()) {
+                const bool idle_stop = stop_ && active_.empty() && prep_queue_.empty() && preparing() == 0;
+                if (idle_stop) return;
+                cv_sched_.wait_for(g, std::chrono::milliseconds(50));
+                continue;
+            }
+            cudaEvent_t ev = steps_.front().t1;
+            g.unlock();
+            cudaEventSynchronize(ev);
+            g.lock();
+            complete_step();
+        }
+    }
+
+    int preparing() const {
+        int n = 0;
+        for (auto& kv : jobs_)
+            if (kv.second->state == Job::kPreparing) ++n;
+        return n;
     }
 
     tpcf_ctx* ctx_;
     size_t budget_;
+    int slots_;
+    bool ok_ = false;
     size_t in_use_ = 0;
     bool stop_ = false;
     uint64_t next_id_ = 1;
+    uint64_t step_seq_ = 0;
     std::mutex mu_;
-    std::condition_variable cv_work_, cv_done_;
-    std::deque<std::shared_ptr<Job>> queue_;
+    std::condition_variable cv_prep_, cv_sched_, cv_done_;
+    std::deque<std::shared_ptr<Job>> queue_, prep_queue_;
+    std::vector<std::shared_ptr<Job>> active_;
+    std::deque<Step> steps_;
+    std::deque<int> step_rc_;
+    std::vector<int> free_slots_;
     std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs_;
-    std::vector<std::thread> threads_;
-    std::vector<cudaStream_t> streams_;
+    std::vector<std::thread> prep_threads_;
+    std::thread sched_thread_;
+    std::vector<cudaStream_t> prep_streams_;
+    cudaStream_t streams_[kStepsInFlight] = {nullptr, nullptr};
+    cudaStream_t stream_ = nullptr;       // frees of finished jobs' memory
+    uint64_t* h_res_ = nullptr;
+    StepSlice* h_slices_[kStepsInFlight] = {nullptr, nullptr};
+    StepSlice* d_slices_[kStepsInFlight] = {nullptr, nullptr};
+    unsigned long long* h_stats_[kStepsInFlight] = {nullptr, nullptr};
+    unsigned long long* d_stats_[kStepsInFlight] = {nullptr, nullptr};
     std::chrono::steady_clock::time_point t0_;
 };
 
@@ -247,8 +621,8 @@ JobServer* server_of(tpcf_ctx* ctx) {
             budget = (size_t)120 << 30;
             if ((double)budget > 0.8 * (double)free_b) budget = (size_t)(0.8 * (double)free_b);
         }
-        const int workers = ctx->cfg.server_workers > 0 ? ctx->cfg.server_workers : 4;
-        ctx->server = new JobServer(ctx, workers, budget);
+        const int slots = ctx->cfg.server_workers > 0 ? ctx->cfg.server_workers : kDefaultSlots;
+        ctx->server = new JobServer(ctx, slots, budget);
     }
     return ctx->server;
 }
@@ -279,7 +653,9 @@ extern "C" int tpcf_submit(tpcf_ctx* ctx, const tpcf_job* job, uint64_t* job_id)
         return ctx->fail(TPCF_EINVAL, "submit: unknown estimator");
     if (job->nd > TPCF_MAX_POINTS || job->nr > TPCF_MAX_POINTS)
         return ctx->fail(TPCF_EOVERFLOW, "submit: catalog too large");
-    const int rc = server_of(ctx)->submit(job, job_id);
+    JobServer* srv = server_of(ctx);
+    if (!srv->ok()) return ctx->fail(TPCF_ENOMEM, "submit: the job server could not allocate its buffers");
+    const int rc = srv->submit(job, job_id);
     if (rc == TPCF_EBUDGET) return ctx->fail(rc, "submit: the job alone exceeds the device-memory budget");
     return rc;
 }

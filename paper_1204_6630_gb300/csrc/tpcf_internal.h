@@ -105,12 +105,31 @@ enum StatWord { kStatPairs = 0, kStatBand = 1, kStatMismatch = 2, kStatError = 3
 // Device error word bits.
 enum : uint32_t { kErrWaitTimeout = 1u, kErrBadHist = 2u, kErrBadPoint = 4u, kErrSortOverflow = 8u };
 
+struct WorkDesc;
+
+// One slice of a serving step: positions [pos_begin, pos_end) of the step are
+// the job's walk positions q_begin, q_begin + 1, ... (job: the device copy of
+// the job's work description).
+struct StepSlice {
+    const WorkDesc* job;
+    uint32_t q_begin;
+    uint32_t pos_begin, pos_end;
+    uint32_t pad;
+};
+
 struct WorkDesc {
     SubProblem sub[kMaxInlineSub];   // used when sub_dev == nullptr
     const SubProblem* sub_dev;       // device array of nsub sub-problems (batched launches)
     int nsub;
     uint64_t item_lo, item_hi;       // walk positions of this launch (shards)
     unsigned long long* stats;       // kStatWords words
+    unsigned long long* item_counter;  // the counter items are drawn with (stats + kStatNextItem)
+    // serving steps (the multi-job kernel): the step's slices, sorted by position,
+    // and one item counter per slice (zeroed before the launch)
+    const StepSlice* slices;
+    unsigned long long* slice_ctr;
+    int nslices;
+    uint32_t step_positions;
     uint32_t I, J, Jc;               // i-block (one warp's 32 R points), j-tile, j-chunk sizes (points)
     uint32_t stages;                 // stages of each warp's shared-memory ring S (2..16)
     uint32_t flags;                  // TPCF_F_* subset used on the device
@@ -134,7 +153,7 @@ struct WorkDesc {
     float prune_thr;                 // sphere-gap threshold of the pruning test (see prune_block)
     // ... and the shared-memory layout of the shape (set by the launcher).
     uint32_t off_ctl, off_bars, off_meta, off_stage, off_hist, off_cthr, off_lo, off_hi, off_c32, off_zlo, off_zhi,
-        off_lut, off_queue, off_icap;
+        off_lut, off_queue, off_icap, off_bwd, off_counter;
     uint32_t stage_bytes;            // J * bytes per staged point
     uint32_t flush_limit;            // j-points between merges of the 16-bit counters
 };
@@ -158,6 +177,9 @@ enum { kModeScreenScalar = 0, kModePlainFP64 = 1, kModeEuclidScreen = 3 };
 // cudaError_t from the launch.
 cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int mode, int nedges,
                          cudaStream_t stream);
+// One serving step (FP32 screen of angles, shape 512 x 8): wd holds the launch
+// layout, the statistics words and the step's slices.
+cudaError_t launch_count_step(const WorkDesc& wd, const Shape& sh, cudaStream_t stream);
 // count_over = 1: the kernel counted the overflow row (TPCF_F_CHECK_OVERFLOW);
 // the finalize then checks that the histogram sums to the pair total.
 cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long long* out,
@@ -176,5 +198,6 @@ size_t count_smem_bytes(int mode, int threads, int ipt, int jtile, int stages, i
 bool count_shape_supported(int threads, int ipt);
 bool derive_cos_thresholds(const double* edges, int nedges, double* cos_thr);
 cudaError_t count_set_smem_limit(int mode, int threads, int ipt, size_t bytes);
+cudaError_t count_step_set_smem_limit(size_t bytes);
 
 }  // namespace tpcf

@@ -32,7 +32,7 @@ def T():
 def job_bytes(nd, nr):
     """The server's admission estimate of one job (kept in step with the library)."""
     def cat(n):
-        return ((n + 4095) // 4096 + 1) * 4096 * 80
+        return ((n + 4095) // 4096 + 1) * 4096 * 60
     n = max(nd, nr)
     p2 = 2048
     while p2 < n:
