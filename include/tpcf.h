@@ -278,7 +278,8 @@ int tpcf_count_all(tpcf_ctx *ctx, const tpcf_catalog *d, const tpcf_catalog *r,
  * data points of segment p, DR_p = cross count of data segment p with random
  * segment p, RR_p = auto count of random segment p.  hists: P * 3 * (B + 2)
  * uint64, histogram (p, k) at offset (3 p + k) (B + 2) with k = 0 DD, 1 DR,
- * 2 RR; host or device as `where` (see above). */
+ * 2 RR; host or device as `where` (see above).  P is at most 21845 (one
+ * launch holds at most 65535 sub-problems); more returns TPCF_EINVAL. */
 int tpcf_count_patches(tpcf_ctx *ctx, const tpcf_catalog *d, const tpcf_catalog *r,
                        const tpcf_bins *bins, void *stream, uint64_t *hists, int where,
                        tpcf_stats *st);

@@ -167,9 +167,13 @@ constexpr int kMaskGroups = 32;     // fast loop: groups per warp reduction of t
 constexpr uint32_t kPruneSlotBytes = 32;  // float4 i-sphere, B's sphere pointer, pruned pair slots (u64)
 
 // One stage of a warp's ring: which item (walk position) and tile it holds.
+// Stage record: the item (walk position, sub-problem, first i and j) and tile
+// a stage holds, written by the warp's producer lane with the copy, so the
+// consumer needs no item arithmetic of its own.
 struct TileMeta {
     uint32_t q;
-    uint32_t t;
+    uint32_t t_sub;  // tile | sub-problem << 16
+    uint32_t i0, j0;
 };
 
 struct SmemLayout {
@@ -202,7 +206,7 @@ __host__ __device__ inline SmemLayout smem_layout(int mode, int T, int J, int S,
     L.ctl = off; off += kCtlWords * 4;
     off = align_up(off, 8);
     L.bars = off; off += W * (uint32_t)S * 8;
-    L.meta = off; off += W * (uint32_t)S * 8;
+    L.meta = off; off += W * (uint32_t)S * (uint32_t)sizeof(TileMeta);
     off = align_up(off, 128);
     L.stage = off; off += W * (uint32_t)S * (uint32_t)J * staged_point_bytes(mode);
     L.hist = off; off += (uint32_t)(nedges + 1) * (uint32_t)(T / 2) * 4;
@@ -304,22 +308,60 @@ __device__ bool load_item(const WorkDesc& wd, uint32_t q, Cursor& c) {
     return c.t < c.g.t_end;
 }
 
-// The last items of a launch's range are drawn in parts.  Items differ in
-// cost by an order of magnitude (an i-block and a j-chunk inside one dense
-// cluster send most pairs to the slow path), so a warp that starts a whole
-// item just before the range runs out can hold its block, and the launch, for
-// the time of many average items.  The last kTailRounds items per warp of the
-// launch are therefore handed out as kTailParts consecutive tile ranges each.
-constexpr uint32_t kTailRounds = 8, kTailParts = 4;
+// Whether the item with first points i0 (of A) and j0 (of B) is heavy: at
+// least a quarter of its j-chunk's kCapPoints-point groups come within
+// near_thr of one of its i-groups, so that a large part of its pairs may take
+// the slow path (an i-block and a j-chunk inside one dense cluster cost an
+// order of magnitude more than an average item).  Called by every lane of the
+// warp; one compiled body with explicitly rounded arithmetic and an integer
+// reduction, so an item gets the same answer at every call.
+__device__ __noinline__ bool heavy_item(const WorkDesc& wd, const SubProblem& sp, uint32_t i0, uint32_t j0) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t ng = wd.Jc / kCapPoints, ni = wd.I / kCapPoints;
+    uint32_t near = 0;
+    for (uint32_t k = lane; k < ng; k += 32) {
+        const uint32_t j = j0 + k * kCapPoints;
+        if (j >= sp.nb) break;
+        const float4 jc = __ldg(sp.b_caps + j / kCapPoints);
+        if (!(jc.w > -1e29f)) continue;  // an empty group
+        bool nr = false;
+        for (uint32_t a = 0; a < ni; ++a) {
+            const uint32_t i = i0 + a * kCapPoints;
+            if (i >= sp.na) break;
+            const float4 ic = __ldg(sp.a_caps + i / kCapPoints);
+            if (!(ic.w > -1e29f)) continue;
+            const float dx = __fsub_rn(ic.x, jc.x), dy = __fsub_rn(ic.y, jc.y), dz = __fsub_rn(ic.z, jc.z);
+            const float D = __fsqrt_rn(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
+            nr |= __fsub_rn(__fsub_rn(D, ic.w), jc.w) < wd.near_thr;
+        }
+        near += nr ? 1u : 0u;
+    }
+    near = __reduce_add_sync(0xffffffffu, near);
+    return 4u * near >= ng;
+}
+
+// Order of a launch's items.  A warp that starts a heavy item near the end of
+// the range would hold its block, and the launch, for the time of many
+// average items; running all heavy items together, on the other hand, would
+// load the slow path's shared-memory pipes while the FMA pipes idle.  So only
+// the heavy items among the last L of the range are moved to the front; the
+// rest of the range follows in walk order, then the light items of the last
+// L, of which the last `tail` are handed out as kTailParts consecutive tile
+// ranges each.  Draw positions:
+//   [0, L)                     heavy items of the last L (light ones skipped),
+//   [L, n)                     items 0 .. n - L - 1, all,
+//   [n, n + L - tail)          light items of the last L but the last `tail`,
+//   then kTailParts parts of each light item of the last `tail`.
+// L = kLateRounds and tail = kTailRounds items per warp of the launch (at most n).
+constexpr uint32_t kLateRounds = 64, kTailRounds = 8, kTailParts = 4;
 
 // The warp's next item (or part) with countable tiles, drawing again past
-// empty ones; called by every lane of the warp (lane 0 draws a position from
-// `counter`, the position is broadcast).  Positions below `whole` are whole
-// items, the rest kTailParts parts of each of the last `tail` items.
+// empty and skipped ones; called by every lane of the warp (lane 0 draws a
+// position from `counter`, the position is broadcast).
 __device__ void draw_next(const WorkDesc& wd, Cursor& c, unsigned long long* counter) {
-    const uint64_t n = wd.item_hi - wd.item_lo;
-    const uint64_t tail = umin64(n, (uint64_t)gridDim.x * (blockDim.x / 32u) * kTailRounds);
-    const uint64_t whole = n - tail, end = whole + tail * kTailParts;
+    const uint64_t n = wd.item_hi - wd.item_lo, warps = (uint64_t)gridDim.x * (blockDim.x / 32u);
+    const uint64_t L = umin64(n, warps * kLateRounds), tail = umin64(L, warps * kTailRounds);
+    const uint64_t parts_at = n + L - tail, end = parts_at + tail * kTailParts;
     while (true) {
         unsigned long long p = 0;
         if ((threadIdx.x & 31) == 0) p = atomicAdd(counter, 1ull);
@@ -328,10 +370,17 @@ __device__ void draw_next(const WorkDesc& wd, Cursor& c, unsigned long long* cou
             c.valid = false;
             return;
         }
-        const uint64_t k = p < whole ? p : whole + (p - whole) / kTailParts;
+        // k: the item within the range; test: 0 none, 1 heavy only, 2 light only
+        uint64_t k;
+        int test;
+        if (p < L) { k = n - L + p; test = 1; }
+        else if (p < n) { k = p - L; test = 0; }
+        else if (p < parts_at) { k = n - L + (p - n); test = 2; }
+        else { k = n - tail + (p - parts_at) / kTailParts; test = 2; }
         if (!load_item(wd, (uint32_t)(wd.item_lo + k), c)) continue;
-        if (p >= whole) {
-            const uint32_t part = (uint32_t)((p - whole) % kTailParts), nt = c.g.t_end - c.g.t_first;
+        if (test != 0 && heavy_item(wd, sub_of(wd, c.sub), c.g.i0, c.g.j0) != (test == 1)) continue;
+        if (p >= parts_at) {
+            const uint32_t part = (uint32_t)((p - parts_at) % kTailParts), nt = c.g.t_end - c.g.t_first;
             const uint32_t t0 = c.g.t_first + nt * part / kTailParts, t1 = c.g.t_first + nt * (part + 1) / kTailParts;
             if (t0 == t1) continue;
             c.t = t0;
@@ -1027,7 +1076,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         const uint32_t s = seq % S;
         const SubProblem& sp = sub_of(wdi, p.sub);
         const uint32_t jbase = p.g.j0 + p.t * wd.J;
-        TPCF_META[s] = TileMeta{p.q, p.t};
+        TPCF_META[s] = TileMeta{p.q, p.t | ((uint32_t)p.sub << 16), p.g.i0, p.g.j0};
         unsigned char* dst = sptr<unsigned char>(TPCF_STAGE_BASE + s * wd.stage_bytes);
         uint64_t* bar = &TPCF_BARS[s];
         fence_proxy_async_smem();  // the warp's reads of the stage's previous tile come first
@@ -1046,7 +1095,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     uint32_t seq = 0, issued = 0;  // tiles consumed / issued so far (tile k: stage k % S)
     int cur_sub = -1;
     uint32_t cur_q = 0xffffffffu;
-    ItemGeom g{};
+    uint32_t g_i0 = 0, g_j0 = 0;  // first i and j of the item the warp counts
     unsigned long long* cur_hist = nullptr;  // the histogram this warp's counters belong to
     uint32_t inc_bound = 0;  // bound on the increments of any of the lane's counters since its merge
     u64 ax2[PLAIN ? 1 : R], ay2[PLAIN ? 1 : R], az2[PLAIN ? 1 : R];
@@ -1082,28 +1131,29 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         }
         if (ctl[kCtlAbort]) { aborted = true; break; }
         const volatile TileMeta* vm = TPCF_META + s;
-        const TileMeta tm{vm->q, vm->t};
+        const uint32_t tm_q = vm->q, tm_ts = vm->t_sub;
+        const uint32_t tm_t = tm_ts & 0xffffu;
 
-        if (tm.q != cur_q) {
+        if (tm_q != cur_q) {
             // ---- a new item (warp-uniform)
-            Cursor c;
-            load_item(wd, tm.q, c);
-            const SubProblem& sp = sub_of(wd, c.sub);
+            const int c_sub = (int)(tm_ts >> 16);
+            g_i0 = vm->i0;
+            g_j0 = vm->j0;
+            const SubProblem& sp = sub_of(wd, c_sub);
             unsigned long long* tgt = sp.hist;
-            if (sp.row_seg) tgt += (size_t)__ldg(sp.row_seg + c.g.i0 / kSegAlign) * sp.row_stride;
-            if (c.sub != cur_sub || tgt != cur_hist) {
+            if (sp.row_seg) tgt += (size_t)__ldg(sp.row_seg + g_i0 / kSegAlign) * sp.row_stride;
+            if (c_sub != cur_sub || tgt != cur_hist) {
                 if (cur_sub >= 0 && tgt != cur_hist) {
                     warp_flush_hist<T>(hc, wd.ne, check, cur_hist);
                     inc_bound = 0;
                 }
-                cur_sub = c.sub;
+                cur_sub = c_sub;
                 cur_hist = tgt;
             }
-            cur_q = tm.q;
-            g = c.g;
-            ibase = g.i0 + (uint32_t)lane;
+            cur_q = tm_q;
+            ibase = g_i0 + (uint32_t)lane;
             if (wd.prune) {
-                const float4 sph = warp_sphere<R>(sp.a_caps + g.i0 / kCapPoints);
+                const float4 sph = warp_sphere<R>(sp.a_caps + g_i0 / kCapPoints);
                 if (lane == 0) {
                     PruneSlot* ps = sptr<PruneSlot>(wd.off_icap + (uint32_t)warp * kPruneSlotBytes);
                     ps->sphere = sph;
@@ -1142,17 +1192,17 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
 
         const SubProblem& sp = sub_of(wd, cur_sub);
         const uint32_t na = sp.na, nb = sp.nb;
-        const uint32_t jbase = g.j0 + tm.t * wd.J;
+        const uint32_t jbase = g_j0 + tm_t * wd.J;
         const int J = (int)wd.J;
         // tiles that meet the diagonal: j > i (auto counts) or j != i (full square without self pairs)
         int diag = kDiagNone;
-        if (jbase < g.i0 + IB) {
+        if (jbase < g_i0 + IB) {
             if (sp.auto_mode) diag = kDiagAbove;
-            else if (sp.no_self && jbase + wd.J > g.i0) diag = kDiagOffSelf;
+            else if (sp.no_self && jbase + wd.J > g_i0) diag = kDiagOffSelf;
         }
         // tiles holding padding (points past na or nb) are masked where padding could
         // look in range (need_idx) and whenever overflow is counted
-        const bool edge = jbase + wd.J > nb || g.i0 + IB > na;
+        const bool edge = jbase + wd.J > nb || g_i0 + IB > na;
         const bool masked = diag != kDiagNone || (edge && (wd.need_idx || check));
         const uint32_t stage_off = TPCF_STAGE_BASE + s * wd.stage_bytes;
 
@@ -1223,7 +1273,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
             src.sx = sx;
             src.sy = sy;
             src.sz = sz;
-            src.i0 = g.i0;
+            src.i0 = g_i0;
             src.jbase = jbase;
             static_assert(kMaskGroups <= 32, "one mask bit per group");
 #pragma unroll 1

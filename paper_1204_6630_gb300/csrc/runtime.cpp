@@ -1007,6 +1007,10 @@ void fill_scalars(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const BinsDev* 
     // dot, within 3.4e-16 of it, is <= C_B: overflow) once delta >=
     // sqrt(2 (1 + eps) - 2 (C_B - 1e-15)).  3-D: delta >= sqrt(S_B) (1 +
     // 1e-12) makes the binary64 d^2 (relative error < 1e-15) >= S_B.
+    // the gap below which point groups may hold pairs in range: items with many
+    // such groups (dense-cluster items, mostly slow-path pairs) are counted first
+    wd.near_thr = bh->euclid ? (float)(std::sqrt(bh->cos_last) * kCapScale3d)
+                             : (float)std::sqrt(std::max(0.0, 2.0 - 2.0 * bh->cos_last));
     wd.prune = 0u;
     wd.prune_thr = INFINITY;
     // (not with a counted overflow row: skipped blocks would have to be counted)
@@ -1046,6 +1050,8 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
     if (where == TPCF_DEVICE && stats) return ctx->fail(TPCF_EINVAL, "stats need where = TPCF_HOST");
     if (!bins || bins->ctx != ctx) return ctx->fail(TPCF_EINVAL, "bins missing or from another context");
     if (nsub < 1) return ctx->fail(TPCF_EINVAL, "no histogram to count");
+    // (the kernel's stage record holds a sub-problem index in 16 bits)
+    if (nsub > 0xffff) return ctx->fail(TPCF_EINVAL, "more than 65535 sub-problems in one count");
     // histograms: sub-problem s fills nhist of them, from index hist_first[s]; outs has one per histogram
     int H = 0;
     bool any_rows = false;

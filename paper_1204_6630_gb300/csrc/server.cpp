@@ -47,10 +47,13 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
-// A step gives all of its remaining items to a job with at most this many
-// pairs left, and fills up to kStepPairs pairs in all.
+// Jobs with at most kSmallJobPairs pairs left run whole, together, in steps
+// of up to kStepPairs pairs; larger jobs in slices of kSlicePairs pairs (each
+// launch ends with a drain of its last items: about a millisecond, or 1-2 %
+// of a slice of this size, 100 ms on a GB300).
 constexpr double kSmallJobPairs = 2e10;
 constexpr double kStepPairs = 1.5e11;
+constexpr double kSlicePairs = 6e11;
 constexpr int kStepsInFlight = 2;
 constexpr int kDefaultSlots = 32;
 constexpr int kPrepWorkers = 4;
@@ -412,30 +415,35 @@ class JobServer {
     bool launch_step() {
         std::vector<std::shared_ptr<Job>> pick;
         std::vector<uint64_t> take;
+        // A step holds either the jobs with little work left (all of it, in
+        // admission order, up to kStepPairs pairs and the slots: the multi-job
+        // kernel) or a slice of kSlicePairs pairs of the oldest job with more (the
+        // one-job kernel, whose job description is its parameter).  With two
+        // steps in flight on two streams, a short step of small jobs runs beside
+        // the slices of a large one.
         double used = 0;
-        auto consider = [&](bool small_pass) {
+        for (auto& j : active_) {
+            if (j->cancel || j->next >= j->n_items) continue;
+            const uint64_t left = j->n_items - j->next;
+            const double left_pairs = (double)left * j->pairs_per_item;
+            if (left_pairs > kSmallJobPairs) continue;
+            if (!pick.empty() && used + left_pairs > kStepPairs) break;
+            pick.push_back(j);
+            take.push_back(left);
+            used += left_pairs;
+            if ((int)pick.size() >= slots_) break;
+        }
+        if (pick.empty()) {
             for (auto& j : active_) {
                 if (j->cancel || j->next >= j->n_items) continue;
-                if (std::find(pick.begin(), pick.end(), j) != pick.end()) continue;
                 const uint64_t left = j->n_items - j->next;
-                const double left_pairs = (double)left * j->pairs_per_item;
-                uint64_t n = 0;
-                if (small_pass) {
-                    if (left_pairs <= kSmallJobPairs) n = left;
-                } else if (used < kStepPairs) {
-                    const double room = kStepPairs - used;
-                    n = j->pairs_per_item > 0 ? (uint64_t)std::ceil(room / j->pairs_per_item) : left;
-                    n = std::max<uint64_t>(1, std::min(n, left));
-                }
-                if (n == 0) continue;
+                uint64_t n = j->pairs_per_item > 0 ? (uint64_t)std::ceil(kSlicePairs / j->pairs_per_item) : left;
+                n = std::max<uint64_t>(1, std::min(n, left));
                 pick.push_back(j);
                 take.push_back(n);
-                used += (double)n * j->pairs_per_item;
-                if ((int)pick.size() >= slots_) return;
+                break;
             }
-        };
-        consider(true);
-        consider(false);
+        }
         if (pick.empty()) return false;
 
         Step step;

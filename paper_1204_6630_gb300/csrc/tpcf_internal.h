@@ -151,6 +151,8 @@ struct WorkDesc {
     double cos_last;                 // C_B (all-binary64 kernel)
     uint32_t prune;                  // 1: skip (warp, 128-j chunk) blocks proven beyond the range
     float prune_thr;                 // sphere-gap threshold of the pruning test (see prune_block)
+    float near_thr;                  // sphere gap below which two point groups may hold pairs in
+                                     // range (the last edge's chord; scheduling only, see heavy_item)
     // ... and the shared-memory layout of the shape (set by the launcher).
     uint32_t off_ctl, off_bars, off_meta, off_stage, off_hist, off_cthr, off_lo, off_hi, off_c32, off_zlo, off_zhi,
         off_lut, off_queue, off_icap, off_bwd, off_counter;
