@@ -13,11 +13,18 @@ steps (CUDA events, max over ranks).  `e2e` repeats the step through the
 host-array call tpcf_correlate with the catalogs in pinned host memory (copies
 included).  The roofline is that of the counting kernel: 3 FP32 pipe lane
 operations per pair (3 FFMA, the range offset folded into the first), counted
-as 6 flops, against the FP32 peak 152 SMs x 128 lanes x 2 flops x 2.07 GHz.
-The line also carries the all-binary64 kernel on the same catalogs
-(`fp64_plain`) and one launch with spatial pruning (`pruning`, the opt-in
-TPCF_F_PRUNE flag: same histograms, pairs covered per second); neither is the
-brute-force headline.
+as 6 flops, against the FP32 peak derived from the device's SM count x 128
+lanes x 2 flops x the maximum SM clock (nvidia-smi), with the fraction at the
+clock sampled under load and against the measured FMA-chain throughput
+(tpcf_fp32_peak) beside it.  The line also carries the all-binary64 kernel on
+the same catalogs (`fp64_plain`) and one launch with spatial pruning
+(`pruning`, the opt-in TPCF_F_PRUNE flag: same histograms, pairs covered per
+second); neither is the brute-force headline.  After the timed region, compact
+records of the other workloads (skipped with --no-extras): `large` (one fused
+launch of the 4M + 8M full-sphere problem with its roofline fraction, a
+40,000-point oracle check and near-edge pairs), `jackknife` (the 512-patch
+graph against separate calls) and `serving` (a 100-job stream against
+one-at-a-time calls: throughput and p50/p99 latency).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -60,7 +67,6 @@ sys.path.insert(0, ROOT)
 METRIC = "pairs/s (DD+DR+RR)"
 UNIT = "pairs/s"
 FLOPS_PER_PAIR = 6            # 3 FP32 pipe lane-ops (3 FFMA), FMA convention
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.55: SMs x lanes x 2 x max SM clock
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -413,12 +419,45 @@ def run_gpu(args):
         "clocks": csum,
     }
     ctx.close()
+    if rank == 0 and world == 1 and not args.no_extras:
+        line.update(extras(peak_meas["value"] if peak_meas else None))
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def extras(peak_meas) -> dict:
+    """Compact records of the other workloads, after the timed region of the
+    headline: the 4M + 8M full-sphere launch (roofline, 40k-point oracle check,
+    near-edge pairs), the 512-patch jackknife graph against separate calls, and a
+    100-job serving stream against one-at-a-time calls."""
+    lg = large_record(1, 1, 40_000, prune=False, peak_meas=peak_meas)
+    jk = jackknife_record(3, 1, loo=False)
+    sv = serving_record(100, 0, pruned=False)
+    return {
+        "large": {"workload": lg["config"]["workload"], "pairs": lg["config"]["pairs_per_step"],
+                  "kernel_ms": lg["ms_per_step"], "pairs_per_s": lg["value"],
+                  "frac": lg["roofline"]["frac"], "frac_of_measured": lg["roofline"]["frac_of_measured"],
+                  "band_pairs": lg["band"]["pairs"],
+                  "subsample_points": lg["subsample_parity"]["points_per_catalog"],
+                  "subsample_identical_to_oracle": lg["subsample_parity"]["identical_to_oracle"],
+                  "near_edge_pairs": lg["subsample_parity"]["near_edge_pairs"],
+                  "clocks": lg["clocks"]},
+        "jackknife": {"workload": jk["config"]["workload"], "patches": jk["config"]["patches"],
+                      "pairs": jk["config"]["pairs_per_step"], "graph_ms": jk["graph"]["ms"],
+                      "separate_ms": jk["separate"]["ms"], "speedup_vs_separate": jk["speedup_vs_separate"],
+                      "histograms_identical": jk["histograms_identical"]},
+        "serving": {"workload": sv["config"]["workload"], "jobs": sv["config"]["jobs"],
+                    "throughput_vs_serial": sv["throughput_vs_serial"],
+                    "serial_s": sv["serial"]["s"], "served_s": sv["served_burst"]["s"],
+                    "latency_s_poisson": {"served": sv["served_poisson"]["latency_s"],
+                                          "serial": sv["serial"]["latency_s_at_poisson"]},
+                    "arrivals": sv["config"]["arrivals"],
+                    "results_identical_to_lone_calls": sv["results_identical_to_lone_calls"]},
+    }
 
 
 def run_count_only(args):
@@ -441,8 +480,9 @@ def _quantiles(xs):
     return {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)), "max": float(a[-1])}
 
 
-def run_jackknife(args):
-    """Per-patch DD/DR/RR of 512 patches: one captured graph vs separate launches."""
+def jackknife_record(steps: int, warmup: int, loo: bool = True) -> dict:
+    """Per-patch DD/DR/RR of 512 patches: one captured graph vs separate launches
+    (and, with ``loo``, the leave-one-out jackknife, brute force and pruned)."""
     import torch
     from paper_1204_6630_gb300 import synth, tpcf
     d, r, doff, roff = synth.jackknife_patches(seed=0)
@@ -459,11 +499,11 @@ def run_jackknife(args):
         g = ctx.graph(tpcf.TPCF_GRAPH_PATCHES, cd, cr, b)  # autotunes, then captures
         torch.cuda.synchronize()
         create_s = time.perf_counter() - t0
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             g.launch(stream)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         graph_ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.zero_()
             ev[0].record(stream)
             g.launch(stream)
@@ -488,7 +528,7 @@ def run_jackknife(args):
 
         separate()
         sep_ms = []
-        for _ in range(max(1, args.steps // 2)):
+        for _ in range(max(1, steps // 2)):
             flush.zero_()
             torch.cuda.synchronize()
             ev[0].record(stream)
@@ -501,26 +541,16 @@ def run_jackknife(args):
         for o in sub:
             ctx.free(o[0])
             ctx.free(o[1])
-        # leave-one-out jackknife of the full catalogs over the same patches
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        loo, w_loo, cov, jst = ctx.jackknife(cd, cr, b, stream, stats=True)
-        loo_s = time.perf_counter() - t0
-    # the same leave-one-out jackknife with spatial pruning (opt-in): most block
-    # pairs of the full catalogs are farther apart than the 5 deg range
-    with tpcf.Context(flags=tpcf.TPCF_F_PRUNE) as cq:
-        qd, qr, qb = cq.catalog(d, offsets=doff), cq.catalog(r, offsets=roff), cq.bins(edges)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        qloo, qw, qcov, qst = cq.jackknife(qd, qr, qb, stream, stats=True)
-        qloo_s = time.perf_counter() - t0
-    loo_same = (np.array_equal(qloo, loo) and np.array_equal(qw, w_loo, equal_nan=True)
-                and np.array_equal(qcov, cov, equal_nan=True))
-    assert loo_same, "pruned and brute-force leave-one-out results disagree"
+        if loo:
+            # leave-one-out jackknife of the full catalogs over the same patches
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            loo_h, w_loo, cov, jst = ctx.jackknife(cd, cr, b, stream, stats=True)
+            loo_s = time.perf_counter() - t0
     gm, sm = statistics.median(graph_ms), statistics.median(sep_ms)
-    print(json.dumps({
+    rec = {
         "mode": "jackknife", "metric": METRIC, "value": pairs / gm * 1e3, "unit": UNIT,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": gm, "higher_is_better": True,
+        "steps": steps, "warmup": warmup, "ms_per_step": gm, "higher_is_better": True,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "octant jackknife: N_D=2,000,000 (1024 clusters sigma 0.2 deg), N_R=4,000,000, "
                                "512 patches lognormal 1k-200k, 40 linear bins 0-5 deg, seed 0",
@@ -531,24 +561,42 @@ def run_jackknife(args):
                   "launches_per_replay": st["launches"], "band_pairs": st["band_pairs"]},
         "separate": {"ms": sm, "pairs_per_s": pairs / sm * 1e3, "calls": 3 * int(len(nd_p)),
                      "launches": 3 * 2 * int(len(nd_p))},
-        "speedup_vs_separate": sm / gm, "histograms_identical": same,
-        "leave_one_out": {"s": loo_s, "kernel_ms": jst["kernel_ms"], "pairs": jst["pairs"],
-                          "pairs_per_s": jst["pairs"] / loo_s,
-                          "what": "DD/DR/RR of the catalogs without each patch (512 resamplings), w and its "
-                                  "covariance: one launch over every pair of the full catalogs"},
-        "leave_one_out_pruned": {"flag": "TPCF_F_PRUNE", "s": qloo_s, "kernel_ms": qst["kernel_ms"],
-                                 "pairs_covered_per_s": qst["pairs"] / qloo_s,
-                                 "skipped_slots_per_pair": qst["pruned_pairs"] / max(1, qst["pairs"]),
-                                 "identical_to_brute_force": loo_same}}))
+        "speedup_vs_separate": sm / gm, "histograms_identical": same}
+    if loo:
+        # the same leave-one-out jackknife with spatial pruning (opt-in): most block
+        # pairs of the full catalogs are farther apart than the 5 deg range
+        with tpcf.Context(flags=tpcf.TPCF_F_PRUNE) as cq:
+            qd, qr, qb = cq.catalog(d, offsets=doff), cq.catalog(r, offsets=roff), cq.bins(edges)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            qloo, qw, qcov, qst = cq.jackknife(qd, qr, qb, stream, stats=True)
+            qloo_s = time.perf_counter() - t0
+        loo_same = (np.array_equal(qloo, loo_h) and np.array_equal(qw, w_loo, equal_nan=True)
+                    and np.array_equal(qcov, cov, equal_nan=True))
+        assert loo_same, "pruned and brute-force leave-one-out results disagree"
+        rec["leave_one_out"] = {"s": loo_s, "kernel_ms": jst["kernel_ms"], "pairs": jst["pairs"],
+                                "pairs_per_s": jst["pairs"] / loo_s,
+                                "what": "DD/DR/RR of the catalogs without each patch (512 resamplings), w and "
+                                        "its covariance: one launch over every pair of the full catalogs"}
+        rec["leave_one_out_pruned"] = {"flag": "TPCF_F_PRUNE", "s": qloo_s, "kernel_ms": qst["kernel_ms"],
+                                       "pairs_covered_per_s": qst["pairs"] / qloo_s,
+                                       "skipped_slots_per_pair": qst["pruned_pairs"] / max(1, qst["pairs"]),
+                                       "identical_to_brute_force": loo_same}
+    return rec
+
+
+def run_jackknife(args):
+    print(json.dumps(jackknife_record(args.steps, args.warmup)))
     return 0
 
 
-def run_serving(args):
-    """Poisson job stream through the job server vs one-at-a-time calls."""
+def serving_record(njobs: int, workers: int, pruned: bool = True) -> dict:
+    """Poisson job stream through the job server vs one-at-a-time calls (and, with
+    ``pruned``, the same with spatial pruning)."""
     import concurrent.futures as cf
     import torch
     from paper_1204_6630_gb300 import synth, tpcf
-    specs = synth.serving_jobs(args.jobs, seed=0)
+    specs = synth.serving_jobs(njobs, seed=0)
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(os.cpu_count() or 4) as ex:
         jobs = list(ex.map(synth.materialise_job, specs))
@@ -580,7 +628,7 @@ def run_serving(args):
         serial_lat.append(done - a)
 
     def serve(at, flags=0):
-        with tpcf.Context(hbm_budget_bytes=budget, server_workers=args.workers, flags=flags) as ctx:
+        with tpcf.Context(hbm_budget_bytes=budget, server_workers=workers, flags=flags) as ctx:
             ctx.poll(ctx.submit(jobs[0].data, jobs[0].rand, jobs[0].edges), len(jobs[0].edges))
             start = time.perf_counter()
             ids = []
@@ -596,30 +644,19 @@ def run_serving(args):
 
     burst_res, burst_span, burst_lat = serve(np.zeros(len(jobs)))
     pois_res, pois_span, pois_lat = serve(arrivals)
-    # the same stream with spatial pruning (opt-in flag): one-at-a-time and served
-    with tpcf.Context(flags=tpcf.TPCF_F_PRUNE) as ctx:
-        ctx.correlate(jobs[0].data, jobs[0].rand, jobs[0].edges)
-        t0 = time.perf_counter()
-        pser_res = [ctx.correlate(w.data, w.rand, w.edges) for w in jobs]
-        pserial_s = time.perf_counter() - t0
-    pburst_res, pburst_span, pburst_lat = serve(np.zeros(len(jobs)), tpcf.TPCF_F_PRUNE)
-    psame = all(np.array_equal(x[n], y[i]) for x, y in zip(pburst_res, serial_res)
-                for i, n in enumerate(("dd", "dr", "rr"))) and \
-        all(np.array_equal(x[i], y[i]) for x, y in zip(pser_res, serial_res) for i in range(3))
-    assert psame, "pruned results differ from brute-force lone calls"
     same = all(np.array_equal(x[n], y[i]) for x, y in zip(burst_res, serial_res)
                for i, n in enumerate(("dd", "dr", "rr"))) and \
         all(np.array_equal(x[n], y[i]) for x, y in zip(pois_res, serial_res)
             for i, n in enumerate(("dd", "dr", "rr")))
     assert same, "served results differ from lone calls"
     nd = np.array([len(w.data) for w in jobs])
-    print(json.dumps({
+    rec = {
         "mode": "serving", "metric": "jobs/s and pairs/s; p50/p99 job latency", "value": total_pairs / burst_span,
         "unit": UNIT, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"serving: {len(jobs)} jobs, N_D log-uniform [1e3, 1e6], N_R = 2 N_D, caps 5-30 deg, "
                                "128 clusters sigma 0.5 deg, 20-80 linear bins 0-2 deg, seed 0",
                    "jobs": len(jobs), "pairs_total": total_pairs, "nd_median": float(np.median(nd)),
-                   "hbm_budget_gb": budget / 2**30, "workers": args.workers, "generation_s": gen_s,
+                   "hbm_budget_gb": budget / 2**30, "workers": workers, "generation_s": gen_s,
                    "arrival_rate_hz": rate, "arrivals": "Poisson at 0.8 x the serial job rate"},
         "serial": {"s": serial_s, "jobs_per_s": len(jobs) / serial_s, "pairs_per_s": total_pairs / serial_s,
                    "latency_s_at_poisson": _quantiles(serial_lat)},
@@ -627,19 +664,38 @@ def run_serving(args):
                          "pairs_per_s": total_pairs / burst_span, "latency_s": _quantiles(burst_lat)},
         "served_poisson": {"s": pois_span, "jobs_per_s": len(jobs) / pois_span,
                            "pairs_per_s": total_pairs / pois_span, "latency_s": _quantiles(pois_lat)},
-        "throughput_vs_serial": serial_s / burst_span, "results_identical_to_lone_calls": same,
-        "pruned": {"flag": "TPCF_F_PRUNE",
-                   "serial": {"s": pserial_s, "pairs_per_s": total_pairs / pserial_s},
-                   "served_burst": {"s": pburst_span, "pairs_per_s": total_pairs / pburst_span,
-                                    "latency_s": _quantiles(pburst_lat)},
-                   "throughput_vs_pruned_serial": pserial_s / pburst_span,
-                   "throughput_vs_brute_force_serial": serial_s / pburst_span,
-                   "results_identical_to_brute_force": psame}}))
+        "throughput_vs_serial": serial_s / burst_span, "results_identical_to_lone_calls": same}
+    if pruned:
+        # the same stream with spatial pruning (opt-in flag): one-at-a-time and served
+        with tpcf.Context(flags=tpcf.TPCF_F_PRUNE) as ctx:
+            ctx.correlate(jobs[0].data, jobs[0].rand, jobs[0].edges)
+            t0 = time.perf_counter()
+            pser_res = [ctx.correlate(w.data, w.rand, w.edges) for w in jobs]
+            pserial_s = time.perf_counter() - t0
+        pburst_res, pburst_span, pburst_lat = serve(np.zeros(len(jobs)), tpcf.TPCF_F_PRUNE)
+        psame = all(np.array_equal(x[n], y[i]) for x, y in zip(pburst_res, serial_res)
+                    for i, n in enumerate(("dd", "dr", "rr"))) and \
+            all(np.array_equal(x[i], y[i]) for x, y in zip(pser_res, serial_res) for i in range(3))
+        assert psame, "pruned results differ from brute-force lone calls"
+        rec["pruned"] = {"flag": "TPCF_F_PRUNE",
+                         "serial": {"s": pserial_s, "pairs_per_s": total_pairs / pserial_s},
+                         "served_burst": {"s": pburst_span, "pairs_per_s": total_pairs / pburst_span,
+                                          "latency_s": _quantiles(pburst_lat)},
+                         "throughput_vs_pruned_serial": pserial_s / pburst_span,
+                         "throughput_vs_brute_force_serial": serial_s / pburst_span,
+                         "results_identical_to_brute_force": psame}
+    return rec
+
+
+def run_serving(args):
+    print(json.dumps(serving_record(args.jobs, args.workers)))
     return 0
 
 
-def run_large(args):
-    """4M + 8M full-sphere points: timed fused launch, oracle check on a subsample."""
+def large_record(steps: int, warmup: int, sub: int, prune: bool = True, peak_meas=None) -> dict:
+    """4M + 8M full-sphere points: timed fused launch, oracle check (and near-edge
+    pairs) on a random subsample of each catalog; with ``prune`` also one launch
+    with spatial pruning.  peak_meas: the measured FP32 peak (TFLOP/s), if taken."""
     import torch
     import oracle
     from paper_1204_6630_gb300 import synth, tpcf
@@ -651,31 +707,35 @@ def run_large(args):
         cd = ctx.catalog(torch.from_numpy(w.data).cuda(), stream)
         cr = ctx.catalog(torch.from_numpy(w.rand).cuda(), stream)
         b = ctx.bins(w.edges)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             ctx.count_all(cd, cr, b, stream)
         kms = []
         with ClockSampler(0) as clocks:
-            for _ in range(args.steps):
+            for _ in range(steps):
                 (dd, dr, rr), st = ctx.count_all(cd, cr, b, stream, stats=True)
                 kms.append(st["kernel_ms"])
         assert int(dd.sum()) == nd * (nd - 1) // 2 and int(dr.sum()) == nd * nr and int(rr.sum()) == nr * (nr - 1) // 2
         # subsample parity
         g = np.random.default_rng(7)
-        ds = w.data[np.sort(g.choice(nd, args.sub, replace=False))]
-        rs = w.rand[np.sort(g.choice(nr, args.sub, replace=False))]
+        ds = w.data[np.sort(g.choice(nd, sub, replace=False))]
+        rs = w.rand[np.sort(g.choice(nr, sub, replace=False))]
         sdd, sdr, srr = ctx.count_all(ctx.catalog(ds), ctx.catalog(rs), b)
-    # the same counts with spatial pruning (opt-in; not the brute-force headline)
-    with tpcf.Context(flags=tpcf.TPCF_F_PRUNE) as cq:
-        qd = cq.catalog(torch.from_numpy(w.data).cuda(), stream)
-        qr = cq.catalog(torch.from_numpy(w.rand).cuda(), stream)
-        qb = cq.bins(w.edges)
-        cq.count_all(qd, qr, qb, stream)
-        (qdd, qdr, qrr), qst = cq.count_all(qd, qr, qb, stream, stats=True)
-    prune = {"flag": "TPCF_F_PRUNE", "kernel_ms": qst["kernel_ms"],
-             "pairs_covered_per_s": qst["pairs"] / qst["kernel_ms"] * 1e3,
-             "skipped_slots_per_pair": qst["pruned_pairs"] / qst["pairs"],
-             "histograms_identical": all(np.array_equal(x, y) for x, y in zip((qdd, qdr, qrr), (dd, dr, rr)))}
-    assert prune["histograms_identical"], "pruned and brute-force histograms disagree"
+        ctx.free(cd)
+        ctx.free(cr)
+    pr = None
+    if prune:
+        # the same counts with spatial pruning (opt-in; not the brute-force headline)
+        with tpcf.Context(flags=tpcf.TPCF_F_PRUNE) as cq:
+            qd = cq.catalog(torch.from_numpy(w.data).cuda(), stream)
+            qr = cq.catalog(torch.from_numpy(w.rand).cuda(), stream)
+            qb = cq.bins(w.edges)
+            cq.count_all(qd, qr, qb, stream)
+            (qdd, qdr, qrr), qst = cq.count_all(qd, qr, qb, stream, stats=True)
+        pr = {"flag": "TPCF_F_PRUNE", "kernel_ms": qst["kernel_ms"],
+              "pairs_covered_per_s": qst["pairs"] / qst["kernel_ms"] * 1e3,
+              "skipped_slots_per_pair": qst["pruned_pairs"] / qst["pairs"],
+              "histograms_identical": all(np.array_equal(x, y) for x, y in zip((qdd, qdr, qrr), (dd, dr, rr)))}
+        assert pr["histograms_identical"], "pruned and brute-force histograms disagree"
     t0 = time.perf_counter()
     cores = os.cpu_count() or 1
     odd = oracle.count_auto(ds, w.edges, cores)
@@ -683,23 +743,36 @@ def run_large(args):
     orr = oracle.count_auto(rs, w.edges, cores)
     oracle_s = time.perf_counter() - t0
     same = np.array_equal(odd, sdd) and np.array_equal(odr, sdr) and np.array_equal(orr, srr)
+    assert same, "subsample histograms differ from the oracle"
     km = statistics.mean(kms)
     ach = pairs * FLOPS_PER_PAIR / (km / 1e3) / 1e12
-    print(json.dumps({
-        "mode": "large", "metric": METRIC, "value": pairs / km * 1e3, "unit": UNIT, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": km, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+    csum = clocks.summary()
+    sms, max_mhz, _, peak_derived, _ = roofline_peaks(0, csum)
+    rec = {
+        "mode": "large", "metric": METRIC, "value": pairs / km * 1e3, "unit": UNIT, "steps": steps,
+        "warmup": warmup, "ms_per_step": km, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "sphere_large: N_D=4,000,000 (4096 clusters sigma 0.1 deg), N_R=8,000,000 uniform, "
                                "full sphere, 80 log bins 0.005-2 deg, seed 0", "pairs_per_step": pairs,
                    "timed": "fused DD/DR/RR counting launch + finalize on resident catalogs (CUDA events)"},
-        "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ach / FP32_PEAK_TFLOPS},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": peak_derived, "unit": "TFLOP/s",
+                     "frac": ach / peak_derived,
+                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {max_mhz:.0f} MHz",
+                     "peak_measured": peak_meas,
+                     "frac_of_measured": ach / peak_meas if peak_meas else None},
         "band": {"pairs": st["band_pairs"], "fraction": st["band_pairs"] / pairs,
                  "fp32_mismatch": st["band_mismatch"]},
-        "subsample_parity": {"points_per_catalog": args.sub, "identical_to_oracle": same,
-                             "oracle_s": oracle_s, "oracle_threads": cores},
-        "pruning": prune,
-        "clocks": clocks.summary()}))
-    assert same, "subsample histograms differ from the oracle"
+        "subsample_parity": {"points_per_catalog": sub, "identical_to_oracle": same,
+                             "oracle_s": oracle_s, "oracle_threads": cores,
+                             "near_edge_pairs": near_edge_count(ds, rs, w.edges, cores),
+                             "near_edge_tol_rad": 1e-12},
+        "clocks": csum}
+    if pr:
+        rec["pruning"] = pr
+    return rec
+
+
+def run_large(args):
+    print(json.dumps(large_record(args.steps, args.warmup, args.sub)))
     return 0
 
 
@@ -766,6 +839,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-binary64 kernel comparison")
     ap.add_argument("--no-prune", action="store_true", help="skip the spatial-pruning launch of the default line")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the compact large / jackknife / serving records of the default line")
     ap.add_argument("--workload", default="octant_precision",
                     choices=["octant_precision", "jackknife", "serving", "large", "box3d"])
     ap.add_argument("--jobs", type=int, default=2000, help="serving: number of jobs")
