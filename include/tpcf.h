@@ -109,6 +109,9 @@ extern "C" {
 #define TPCF_F_TEST_WAIT_TIMEOUT 0x100u /* test hook: the first j-tile copy of each counting
                                            launch is never issued, so its bounded wait expires
                                            and the call returns TPCF_ETIMEOUT */
+#define TPCF_F_TEST_BAD_TOTAL 0x200u    /* test hook (with TPCF_F_CHECK_OVERFLOW): the finalize
+                                           compares each histogram with its pair total plus one,
+                                           so the check fails and the call returns TPCF_ECUDA */
 
 /* limits */
 #define TPCF_MAX_EDGES 321           /* B + 1 <= 321, i.e. at most 320 bins (per-thread

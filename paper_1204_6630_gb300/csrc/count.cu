@@ -1459,7 +1459,8 @@ __device__ void finalize_one(const unsigned long long* acc, int nedges, unsigned
     __syncthreads();  // every thread has read acc before out (possibly the same memory) is written
     for (int h = threadIdx.x; h < nedges; h += blockDim.x) out[h] = acc[h];
     if (threadIdx.x == 0) {
-        const bool bad = count_over ? sum != total : sum > total;
+        // (count_over 2: a test hook that checks against total + 1, so the check fails)
+        const bool bad = count_over ? sum != (count_over == 2 ? total + 1 : total) : sum > total;
         if (bad) {
             atomicOr(err_word, (unsigned long long)kErrBadHist);
             out[nedges] = ~0ull;  // sentinel

@@ -1282,7 +1282,9 @@ int run_counts(tpcf_ctx* ctx, const SubSpec* specs, int nsub, const tpcf_bins* b
 
     // ---- finalize: overflow of each histogram = its pair total - sum of the other
     // entries, or (counted overflow) a check that the entries sum to the total
-    const int count_over = (ctx->cfg.flags & TPCF_F_CHECK_OVERFLOW) ? 1 : 0;
+    // (2: the test hook that checks against the pair total plus one)
+    const int count_over = (ctx->cfg.flags & TPCF_F_CHECK_OVERFLOW)
+                               ? ((ctx->cfg.flags & TPCF_F_TEST_BAD_TOTAL) ? 2 : 1) : 0;
     if (use_slot) {
         for (int s2 = 0; s2 < H; ++s2) {
             unsigned long long* a = acc + (size_t)s2 * acc_stride;

@@ -35,6 +35,7 @@ TPCF_F_AUTOTUNE = 0x8
 TPCF_F_PRUNE = 0x10
 TPCF_F_CHECK_OVERFLOW = 0x20
 TPCF_F_TEST_WAIT_TIMEOUT = 0x100
+TPCF_F_TEST_BAD_TOTAL = 0x200
 TPCF_MAX_EDGES = 321
 TPCF_GRAPH_AUTO, TPCF_GRAPH_CROSS, TPCF_GRAPH_ALL, TPCF_GRAPH_PATCHES = 0, 1, 2, 3
 
