@@ -127,6 +127,24 @@ def test_ragged_sizes_and_shapes(T, shape, prec):
                                           oracle.count_cross(x, y, edges, THREADS), err_msg=f"cross n={n}")
 
 
+@pytest.mark.parametrize("shape", range(len(SHAPES)))
+@pytest.mark.parametrize("prec", [SCREEN, PLAIN])
+def test_one_bin_holding_every_pair_at_every_shape(T, shape, prec):
+    # edges [0, pi]: every pair lands in one bin, so one lane's 16-bit counter of that row takes
+    # R x J increments per tile (16 x 4096 per item at 256 x 16); the warp must merge it before
+    # it passes 2^16 - 1, or it would carry into its partner's half of the shared word
+    edges = np.array([0.0, math.pi])
+    n = 20_000
+    x = synth.clustered(n, 16, 0.2, synth.Footprint("octant"), seed=11)
+    y = synth.randoms(n + 999, seed=12)
+    with T.Context(precision=prec, **SHAPES[shape]) as ctx:
+        auto, cross = gpu_auto(ctx, x, edges), gpu_cross(ctx, x, y, edges)
+    np.testing.assert_array_equal(auto, [0, n * (n - 1) // 2, 0])
+    np.testing.assert_array_equal(cross, [0, n * (n + 999), 0])
+    np.testing.assert_array_equal(auto, oracle.count_auto(x, edges, THREADS))
+    np.testing.assert_array_equal(cross, oracle.count_cross(x, y, edges, THREADS))
+
+
 def test_empty_catalogs(ctxs):
     edges = synth.linear_edges(0.0, 10.0, 40)
     z = np.zeros((0, 3))
