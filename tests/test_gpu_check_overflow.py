@@ -7,9 +7,11 @@ FP32 screen rejects included) and the call fails when a histogram does not sum
 to its pair total.  Here: the counted overflow equals the oracle's on the
 small octant workload (both precisions, fused and separate launches), on
 ragged sizes across the kernel shapes, on patches and in 3-D; the 200k + 200k
-screen equals the all-binary64 kernel with counted overflow; and a test hook
-that checks against the pair total plus one makes the call fail while the
-context stays usable.
+screen equals the all-binary64 kernel with counted overflow; at 1M + 1M (every
+phase of the launch's draw order) and through the job server's steps the
+checked calls succeed with the usual histograms; and a test hook that checks
+against the pair total plus one makes the call fail while the context stays
+usable.
 """
 import os
 
@@ -136,3 +138,32 @@ def test_a_histogram_that_does_not_add_up_fails_the_call(T):
     with T.Context(flags=T.TPCF_F_CHECK_OVERFLOW) as ctx:
         d, b = ctx.catalog(w.data), ctx.bins(w.edges)
         np.testing.assert_array_equal(ctx.count_auto(d, b), oracle.count_auto(w.data, w.edges, THREADS))
+
+
+def test_counted_overflow_at_1m_covers_every_draw_phase(T):
+    # 1.9e6 items against 64 x 2432 late items: the walk-order middle of the range runs too, so
+    # an item the draw order dropped or counted twice would make the checked call fail
+    w = synth.octant_precision(seed=0, n=1_000_000)
+    with T.Context() as ctx:
+        d, r, b = ctx.catalog(w.data), ctx.catalog(w.rand), ctx.bins(w.edges)
+        derived = ctx.count_all(d, r, b)
+    with T.Context(flags=T.TPCF_F_CHECK_OVERFLOW) as ctx:
+        d, r, b = ctx.catalog(w.data), ctx.catalog(w.rand), ctx.bins(w.edges)
+        counted, st = ctx.count_all(d, r, b, stats=True)
+    for a, c in zip(counted, derived):
+        np.testing.assert_array_equal(a, c)
+    assert st["device_error"] == 0 and st["pairs"] == w.pairs
+
+
+def test_counted_overflow_through_the_job_server(T):
+    # small jobs share the multi-job kernel's steps, the largest runs in slices of the one-job kernel
+    specs = synth.serving_jobs(24, seed=5)
+    jobs = [synth.materialise_job(s) for s in specs]
+    with T.Context() as lone:
+        want = [lone.correlate(j.data, j.rand, j.edges) for j in jobs]
+    with T.Context(flags=T.TPCF_F_CHECK_OVERFLOW) as ctx:
+        ids = [ctx.submit(j.data, j.rand, j.edges) for j in jobs]
+        got = [ctx.poll(i, len(j.edges)) for i, j in zip(ids, jobs)]
+    for g, w_ in zip(got, want):
+        for k, name in enumerate(("dd", "dr", "rr")):
+            np.testing.assert_array_equal(g[name], w_[k])
