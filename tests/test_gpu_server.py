@@ -3,7 +3,9 @@
 Every job's histograms must equal the oracle's (small jobs) or a lone
 tpcf_correlate call (larger jobs), whatever else runs beside it; the
 device-memory budget must serialize jobs that do not fit together and refuse
-a job that alone exceeds it; cancel and poll follow their documented states.
+a job that alone exceeds it; cancel and poll follow their documented states; a
+step whose bounded waits expire fails its jobs with TPCF_ETIMEOUT and leaves the
+device usable; a job whose bins do not fit the multi-job kernel runs alone.
 """
 import os
 
@@ -198,3 +200,41 @@ def test_mixed_sizes_and_bin_sets(T):
             res = ctx.poll(jid, len(w.edges))
             for name, want in zip(("dd", "dr", "rr", "w"), alone[k]):
                 np.testing.assert_array_equal(res[name], want, err_msg=f"job {k} {name}")
+
+
+def test_a_step_that_times_out_fails_its_jobs_and_the_device_stays_usable(T):
+    """With the test hook that leaves each warp's first tile copy unissued, every
+    step's bounded waits expire: its jobs finish with TPCF_ETIMEOUT (multi-job
+    steps and one-job slices alike), and a fresh server then counts correctly."""
+    fp = synth.Footprint("octant")
+    small = [octant_job(300 + 50 * k, 600 + 70 * k, 40 + k) for k in range(3)]
+    edges = synth.linear_edges(0.0, 10.0, 20)
+    with T.Context(flags=T.TPCF_F_TEST_WAIT_TIMEOUT, wait_timeout_us=200_000) as ctx:
+        ids = [ctx.submit(d, r, edges) for d, r in small]
+        for jid in ids:
+            res = ctx.poll(jid, len(edges), raise_on_error=False)
+            assert res["status"] == T.TPCF_ETIMEOUT
+    d, r = synth.clustered(2000, 8, 0.5, fp, 7), synth.randoms(3000, fp, 8)
+    with T.Context() as ctx:
+        res = ctx.poll(ctx.submit(d, r, edges), len(edges))
+    np.testing.assert_array_equal(res["dd"], oracle.count_auto(d, edges, THREADS))
+    np.testing.assert_array_equal(res["dr"], oracle.count_cross(d, r, edges, THREADS))
+    np.testing.assert_array_equal(res["rr"], oracle.count_auto(r, edges, THREADS))
+
+
+def test_a_job_with_too_many_edges_for_the_step_kernel_runs_alone(T):
+    """300 bins do not fit the multi-job kernel's shared-memory histograms: that
+    job is counted alone by its preparation worker while the others share steps;
+    all equal their lone calls."""
+    edges_wide = synth.linear_edges(0.0, 3.0, 300)
+    edges = synth.linear_edges(0.0, 3.0, 40)
+    jobs = [octant_job(4000 + 500 * k, 6000 + 300 * k, 60 + k) for k in range(4)]
+    sets = [edges_wide if k == 1 else edges for k in range(len(jobs))]
+    with T.Context() as lone:
+        want = [lone.correlate(d, r, e) for (d, r), e in zip(jobs, sets)]
+    with T.Context() as ctx:
+        ids = [ctx.submit(d, r, e) for (d, r), e in zip(jobs, sets)]
+        got = [ctx.poll(i, len(e)) for i, e in zip(ids, sets)]
+    for k, (g, w_) in enumerate(zip(got, want)):
+        for name, a in zip(("dd", "dr", "rr", "w"), w_):
+            np.testing.assert_array_equal(g[name], a, err_msg=f"job {k} {name}")
