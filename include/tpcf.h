@@ -381,13 +381,15 @@ int tpcf_correlate(tpcf_ctx *ctx, const double *d_xyz, uint64_t nd, const double
  * and bins are prepared on the device (preparation workers, their own
  * streams) and stay resident until it completes.
  * Continuous batching: the counting work of all admitted jobs runs as a
- * sequence of steps, each one launch of a multi-job kernel over slices of
- * many jobs' work items (each job with its own bins and histograms; a step
- * that holds a single job launches the one-job kernel); a step gives every
- * job with little work left all of it and fills the rest of its pair budget
- * in admission order, and a job admitted while steps run joins the next
- * step.  Two steps are in flight, on two streams, so that the blocks of one
- * start on the SMs the other's blocks leave.  Each job's histograms equal those of a lone tpcf_correlate
+ * sequence of steps, two in flight on two streams, so that the blocks of one
+ * start on the SMs the other's blocks leave.  Small jobs (at most 2e10 pairs)
+ * share steps: one launch of a multi-job kernel over all of their work items,
+ * each job with its own bins and histograms.  A large job runs in
+ * preemptible steps of the one-job kernel over all of its remaining work; a
+ * small job that becomes ready makes the running large step stop drawing new
+ * items (its warps finish the items they hold), runs, and the large job
+ * continues where it stopped.  A job admitted while steps run joins the next
+ * step.  Each job's histograms equal those of a lone tpcf_correlate
  * call (every pair is counted once, whatever step it lands in).  Jobs with
  * more edges than the multi-job kernel's shared memory holds are counted
  * alone by their preparation worker.  Job buffers are allocated and freed in

@@ -352,19 +352,23 @@ __device__ __noinline__ bool heavy_item(const WorkDesc& wd, const SubProblem& sp
 //   [L, n)                     items 0 .. n - L - 1, all,
 //   [n, n + L - tail)          light items of the last L but the last `tail`,
 //   then kTailParts parts of each light item of the last `tail`.
-// L = kLateRounds and tail = kTailRounds items per warp of the launch (at most n).
-constexpr uint32_t kLateRounds = 64, kTailRounds = 8, kTailParts = 4;
+// L = kLateRounds and tail = kTailRounds items per warp of the launch (at most
+// n; the constants and the order's length, draw_positions, are in plan.h).
 
 // The warp's next item (or part) with countable tiles, drawing again past
 // empty and skipped ones; called by every lane of the warp (lane 0 draws a
-// position from `counter`, the position is broadcast).
+// position from `counter`, the position is broadcast).  A preemptible launch
+// draws from pos_lo on and stops drawing once its yield word is set (the
+// positions it took are the counter's value).
 __device__ void draw_next(const WorkDesc& wd, Cursor& c, unsigned long long* counter) {
-    const uint64_t n = wd.item_hi - wd.item_lo, warps = (uint64_t)gridDim.x * (blockDim.x / 32u);
+    const uint64_t n = wd.item_hi - wd.item_lo;
+    const uint64_t warps = wd.draw_warps;
     const uint64_t L = umin64(n, warps * kLateRounds), tail = umin64(L, warps * kTailRounds);
     const uint64_t parts_at = n + L - tail, end = parts_at + tail * kTailParts;
     while (true) {
-        unsigned long long p = 0;
-        if ((threadIdx.x & 31) == 0) p = atomicAdd(counter, 1ull);
+        unsigned long long p = ~0ull;  // (a yield: no position taken)
+        if ((threadIdx.x & 31) == 0 && *reinterpret_cast<volatile unsigned long long*>(wd.stats + kStatYield) == 0ull)
+            p = wd.pos_lo + atomicAdd(counter, 1ull);
         p = __shfl_sync(0xffffffffu, p, 0);
         if (p >= end) {
             c.valid = false;
@@ -1402,6 +1406,8 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
                 bw.item_lo = sl.q_begin;
                 bw.item_hi = (uint64_t)sl.q_begin + n;
                 bw.item_counter = wd.slice_ctr + si;
+                bw.pos_lo = 0;
+                bw.draw_warps = gridDim.x * (uint32_t)W;
             }
             __syncthreads();
             run_items(bw);
@@ -1529,6 +1535,9 @@ static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t
     // the 16-bit counters' merge interval is bounded in the kernel, per tile
     wd.flush_limit = 0xffffu;
     if (L.total > sh.smem || wd.I != 32u * (uint32_t)R) return cudaErrorInvalidValue;
+    // the draw order is laid out for this launch's warps unless the caller fixed it
+    // (continuations of a preempted launch keep the order of the first)
+    if (wd.draw_warps == 0) wd.draw_warps = (uint32_t)sh.blocks * (uint32_t)(T / 32);
     count_kernel<T, R, MODE, MULTI><<<sh.blocks, T, sh.smem, stream>>>(wd);
     return cudaGetLastError();
 }

@@ -141,6 +141,8 @@ int serving_job_desc(tpcf_ctx* ctx, const tpcf_catalog* d, const tpcf_catalog* r
 int serving_launch(tpcf_ctx* ctx, const Shape& sh, int nedges_max, const StepSlice* slices, int nslices,
                    unsigned long long* slice_ctr, uint32_t positions, unsigned long long* stats, cudaStream_t st);
 int serving_launch_one(tpcf_ctx* ctx, const Shape& sh, const WorkDesc& job, uint32_t q_begin, uint32_t n,
-                       unsigned long long* stats, cudaStream_t st);
+                       uint64_t pos_lo, uint32_t draw_warps, unsigned long long* stats, cudaStream_t st);
+// Positions of the one-job kernel's draw order over n items for `warps` warps.
+uint64_t serving_positions(uint64_t n, uint32_t warps);
 
 }  // namespace tpcf

@@ -102,6 +102,17 @@ __host__ __device__ inline uint64_t item_pairs(const ItemGeom& g, uint32_t na, u
     return span_pairs(g.i0, I, g.j0, (uint64_t)g.j0 + Jc, na, nb, auto_mode);
 }
 
+// The counting kernel's draw order over a launch's n items (count.cu): the
+// heavy items among the last L = kLateRounds x warps first, the rest in walk
+// order, then the light items of the last L, of which the last kTailRounds x
+// warps are handed out as kTailParts tile-range parts each.  Its length in
+// draw positions:
+constexpr uint32_t kLateRounds = 64, kTailRounds = 8, kTailParts = 4;
+__host__ __device__ inline uint64_t draw_positions(uint64_t n, uint64_t warps) {
+    const uint64_t L = umin64(n, warps * kLateRounds), tail = umin64(L, warps * kTailRounds);
+    return n + L - tail + tail * kTailParts;
+}
+
 // Walk order of one sub-problem's items: position k (0 <= k < n) visits item
 // (k * m) mod n, with m an odd number near 0.618 n coprime with n.  Items that
 // are neighbours in the triangle or rectangle (and cost alike: near-diagonal

@@ -1415,15 +1415,19 @@ int tpcf::serving_launch(tpcf_ctx* ctx, const Shape& sh, int nedges_max, const S
     return TPCF_OK;
 }
 
-// One serving step that holds the items [q_begin, q_begin + n) of a single
-// job (job: its work description from serving_job_desc): the one-job kernel,
-// which reads the description from its parameter; stats: kStatWords device
-// words zeroed by the caller (its item counter included).
+// One serving step that holds a single job (job: its work description from
+// serving_job_desc): the one-job kernel, which reads the description from its
+// parameter, over the items [q_begin, q_begin + n), drawing their order's
+// positions from pos_lo on (the order laid out for draw_warps warps; 0: this
+// launch's) until it ends or stats[kStatYield] is set; stats: kStatWords
+// device words zeroed by the caller (its item counter included).
 int tpcf::serving_launch_one(tpcf_ctx* ctx, const Shape& sh, const WorkDesc& job, uint32_t q_begin, uint32_t n,
-                             unsigned long long* stats, cudaStream_t st) {
+                             uint64_t pos_lo, uint32_t draw_warps, unsigned long long* stats, cudaStream_t st) {
     WorkDesc wd = job;
     wd.item_lo = q_begin;
     wd.item_hi = (uint64_t)q_begin + n;
+    wd.pos_lo = pos_lo;
+    wd.draw_warps = draw_warps;
     wd.stats = stats;
     wd.item_counter = stats + kStatNextItem;
     wd.slices = nullptr;
@@ -1438,6 +1442,8 @@ int tpcf::serving_launch_one(tpcf_ctx* ctx, const Shape& sh, const WorkDesc& job
     ctx->launches.fetch_add(1);
     return TPCF_OK;
 }
+
+uint64_t tpcf::serving_positions(uint64_t n, uint32_t warps) { return draw_positions(n, warps); }
 
 // ====================================================================== counting ABI
 extern "C" int tpcf_count_auto(tpcf_ctx* ctx, const tpcf_catalog* cat, const tpcf_bins* bins,

@@ -47,13 +47,11 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
-// Jobs with at most kSmallJobPairs pairs left run whole, together, in steps
-// of up to kStepPairs pairs; larger jobs in slices of kSlicePairs pairs (each
-// launch ends with a drain of its last items: about a millisecond, or 1-2 %
-// of a slice of this size, 100 ms on a GB300).
+// Jobs of at most kSmallJobPairs pairs run whole, together, in steps of up to
+// kStepPairs pairs; larger jobs run in preemptible steps over all of their
+// remaining work, which stop drawing when small jobs are ready.
 constexpr double kSmallJobPairs = 2e10;
 constexpr double kStepPairs = 1.5e11;
-constexpr double kSlicePairs = 6e11;
 constexpr int kStepsInFlight = 2;
 constexpr int kDefaultSlots = 32;
 constexpr int kPrepWorkers = 4;
@@ -88,6 +86,14 @@ struct Job {
     double pairs_per_item = 0;
     int inflight = 0;                     // steps with slices of the job that have not finished
     bool solo = false;                    // counted alone (outside the steps)
+    // a large job runs in preemptible one-job steps: one draw order over all of its
+    // items, laid out for draw_warps warps, positions [0, pos_end) of which pos_next
+    // are taken; its finalize follows in a step of its own
+    bool big = false;
+    uint32_t draw_warps = 0;
+    uint64_t pos_next = 0, pos_end = 0;
+    bool finalized = false;               // the step holding its finalize has been launched
+    bool work_left() const { return big ? pos_next < pos_end : next < n_items; }
 };
 
 // One step on the device: its slices, the jobs it holds, those it completes.
@@ -96,6 +102,9 @@ struct Step {
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaEvent_t kdone = nullptr;          // its counting launch has finished
     std::vector<std::shared_ptr<Job>> jobs, finals;
+    std::shared_ptr<Job> big;             // a preemptible step of this large job (or none)
+    uint64_t pos_lo = 0;                  // ... from this draw position
+    bool yielded = false;                 // its yield word has been set
 };
 
 class JobServer {
@@ -112,6 +121,13 @@ class JobServer {
         // step that used the memory finish, and an allocation that reuses it (a new job's,
         // on a preparation stream) then waits for no running step
         ok_ = ok_ && cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking) == cudaSuccess;
+        // yields of large jobs' steps: a one-word copy on a stream of its own (it runs while
+        // the step's kernel does), and per step buffer the event of the last such copy
+        ok_ = ok_ && cudaStreamCreateWithFlags(&yield_stream_, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaHostAlloc((void**)&h_one_, 8, cudaHostAllocDefault) == cudaSuccess;
+        if (ok_) *h_one_ = 1ull;
+        for (int k = 0; k < kStepsInFlight; ++k)
+            ok_ = ok_ && cudaEventCreateWithFlags(&yield_ev_[k], cudaEventDisableTiming) == cudaSuccess;
         // pinned result buffers (one per slot: 3 histograms of up to TPCF_MAX_EDGES + 1 words) and
         // per-step-buffer slices and statistics words
         const size_t res_words = 3 * (size_t)(TPCF_MAX_EDGES + 1);
@@ -156,6 +172,10 @@ class JobServer {
         for (int k = 0; k < kStepsInFlight; ++k)
             if (streams_[k]) cudaStreamSynchronize(streams_[k]);
         if (stream_) cudaStreamSynchronize(stream_);
+        if (yield_stream_) cudaStreamSynchronize(yield_stream_);
+        for (int k = 0; k < kStepsInFlight; ++k)
+            if (yield_ev_[k]) cudaEventDestroy(yield_ev_[k]);
+        if (h_one_) cudaFreeHost(h_one_);
         for (int k = 0; k < kStepsInFlight; ++k) {
             if (d_slices_[k]) cudaFree(d_slices_[k]);
             if (d_stats_[k]) cudaFree(d_stats_[k]);
@@ -167,6 +187,7 @@ class JobServer {
         for (int k = 0; k < kStepsInFlight; ++k)
             if (streams_[k]) cudaStreamDestroy(streams_[k]);
         if (stream_) cudaStreamDestroy(stream_);
+        if (yield_stream_) cudaStreamDestroy(yield_stream_);
     }
 
     bool ok() const { return ok_; }
@@ -352,6 +373,8 @@ class JobServer {
             } else {
                 j->state = Job::kActive;
                 active_.push_back(j);
+                // a small job does not wait for a large job's step: that step stops drawing
+                if (!j->big && j->work_left()) yield_big_step();
                 cv_sched_.notify_all();
             }
         }
@@ -388,6 +411,12 @@ class JobServer {
                 return TPCF_ECUDA;
             j.pairs = totals[0] + totals[1] + totals[2];
             j.pairs_per_item = j.n_items ? (double)j.pairs / (double)j.n_items : 0.0;
+            // a large job: one draw order over all of its items, laid out for a full grid
+            j.big = (double)j.pairs > kSmallJobPairs;
+            if (j.big) {
+                j.draw_warps = (uint32_t)sh.blocks * (uint32_t)(sh.threads / 32);
+                j.pos_end = serving_positions(j.n_items, j.draw_warps);
+            }
             // a job without items (every histogram empty) needs no step
             if (j.n_items == 0) {
                 uint64_t* h = res_buf(j);
@@ -410,89 +439,111 @@ class JobServer {
     }
 
     // ---------------------------------------------------------------- steps
-    // Builds and launches the next step (mu_ held); false when no admitted job
-    // has work left to schedule.
+    // Builds and launches the next step (mu_ held); false when nothing can be
+    // launched now.  In order of preference:
+    //  1. the finalize of large jobs whose draw positions are all taken (a step
+    //     without a counting launch);
+    //  2. the small jobs with work left, all of it, in admission order, up to
+    //     kStepPairs pairs and the slots: the multi-job kernel (the one-job kernel
+    //     for a single job); a large job's step in flight is told to yield, so
+    //     that this step's blocks get the SMs;
+    //  3. when no large job's step is in flight: a preemptible step of the oldest
+    //     large job over all of its remaining draw positions (the one-job kernel,
+    //     whose job description is its parameter).
     bool launch_step() {
+        Step step;
         std::vector<std::shared_ptr<Job>> pick;
         std::vector<uint64_t> take;
-        // A step holds either the jobs with little work left (all of it, in
-        // admission order, up to kStepPairs pairs and the slots: the multi-job
-        // kernel) or a slice of kSlicePairs pairs of the oldest job with more (the
-        // one-job kernel, whose job description is its parameter).  With two
-        // steps in flight on two streams, a short step of small jobs runs beside
-        // the slices of a large one.
-        double used = 0;
-        for (auto& j : active_) {
-            if (j->cancel || j->next >= j->n_items) continue;
-            const uint64_t left = j->n_items - j->next;
-            const double left_pairs = (double)left * j->pairs_per_item;
-            if (left_pairs > kSmallJobPairs) continue;
-            if (!pick.empty() && used + left_pairs > kStepPairs) break;
-            pick.push_back(j);
-            take.push_back(left);
-            used += left_pairs;
-            if ((int)pick.size() >= slots_) break;
-        }
-        if (pick.empty()) {
+        for (auto& j : active_)
+            if (j->big && !j->finalized && !j->cancel && j->status == TPCF_OK && !j->work_left() && j->inflight == 0)
+                step.finals.push_back(j);
+        bool small = false;
+        if (step.finals.empty()) {
+            double used = 0;
             for (auto& j : active_) {
-                if (j->cancel || j->next >= j->n_items) continue;
+                if (j->big || j->cancel || !j->work_left()) continue;
                 const uint64_t left = j->n_items - j->next;
-                uint64_t n = j->pairs_per_item > 0 ? (uint64_t)std::ceil(kSlicePairs / j->pairs_per_item) : left;
-                n = std::max<uint64_t>(1, std::min(n, left));
+                const double left_pairs = (double)left * j->pairs_per_item;
+                if (!pick.empty() && used + left_pairs > kStepPairs) break;
                 pick.push_back(j);
-                take.push_back(n);
-                break;
+                take.push_back(left);
+                used += left_pairs;
+                if ((int)pick.size() >= slots_) break;
             }
+            small = !pick.empty();
+            if (!small && !big_in_flight()) {
+                for (auto& j : active_) {
+                    if (!j->big || j->cancel || !j->work_left() || j->inflight > 0) continue;
+                    pick.push_back(j);
+                    step.big = j;
+                    step.pos_lo = j->pos_next;
+                    break;
+                }
+            }
+            if (pick.empty()) return false;
         }
-        if (pick.empty()) return false;
 
-        Step step;
         step.buf = step_seq_++ % kStepsInFlight;
-        StepSlice* hs = h_slices_[step.buf];
-        uint32_t pos = 0;
-        int ne_max = 2;
-        for (size_t k = 0; k < pick.size(); ++k) {
-            Job& j = *pick[k];
-            hs[k].job = j.dwd;
-            hs[k].q_begin = (uint32_t)j.next;
-            hs[k].pos_begin = pos;
-            pos += (uint32_t)take[k];
-            hs[k].pos_end = pos;
-            hs[k].pad = 0;
-            j.next += take[k];
-            ++j.inflight;
-            ne_max = std::max(ne_max, (int)j.edges.size());
-            step.jobs.push_back(pick[k]);
-            if (j.next == j.n_items) step.finals.push_back(pick[k]);
-        }
-        Shape sh;
-        int rc = serving_shape(ctx_, ne_max, &sh) ? TPCF_OK : TPCF_EINVAL;
         cudaStream_t ss = streams_[step.buf];
         cudaEventCreate(&step.t0);
         cudaEventCreate(&step.t1);
         cudaEventCreateWithFlags(&step.kdone, cudaEventDisableTiming);
         cudaEventRecord(step.t0, ss);
-        if (rc == TPCF_OK &&
-            (cudaMemcpyAsync(d_slices_[step.buf], hs, pick.size() * sizeof(StepSlice), cudaMemcpyHostToDevice,
-                             ss) != cudaSuccess ||
-             cudaMemsetAsync(d_stats_[step.buf], 0, (kStatWords + pick.size()) * 8, ss) != cudaSuccess))
+        int rc = TPCF_OK;
+        // (a yield copy into this buffer's words lands before they are cleared)
+        if (cudaStreamWaitEvent(ss, yield_ev_[step.buf], 0) != cudaSuccess ||
+            cudaMemsetAsync(d_stats_[step.buf], 0, (kStatWords + pick.size()) * 8, ss) != cudaSuccess)
             rc = TPCF_ECUDA;
-        // a step of one job runs the one-job kernel (its description in the
-        // kernel parameter), a step of several the step kernel
-        if (rc == TPCF_OK && pick.size() == 1)
-            rc = serving_launch_one(ctx_, pick[0]->sh, pick[0]->hwd, hs[0].q_begin, pos, d_stats_[step.buf], ss);
-        else if (rc == TPCF_OK)
-            rc = serving_launch(ctx_, sh, ne_max, d_slices_[step.buf], (int)pick.size(),
-                                d_stats_[step.buf] + kStatWords, pos, d_stats_[step.buf], ss);
+        if (small) {
+            StepSlice* hs = h_slices_[step.buf];
+            uint32_t pos = 0;
+            int ne_max = 2;
+            for (size_t k = 0; k < pick.size(); ++k) {
+                Job& j = *pick[k];
+                hs[k].job = j.dwd;
+                hs[k].q_begin = (uint32_t)j.next;
+                hs[k].pos_begin = pos;
+                pos += (uint32_t)take[k];
+                hs[k].pos_end = pos;
+                hs[k].pad = 0;
+                j.next += take[k];
+                ++j.inflight;
+                ne_max = std::max(ne_max, (int)j.edges.size());
+                step.jobs.push_back(pick[k]);
+                step.finals.push_back(pick[k]);  // all of a small job's work is in its step
+            }
+            Shape sh;
+            if (rc == TPCF_OK && !serving_shape(ctx_, ne_max, &sh)) rc = TPCF_EINVAL;
+            if (rc == TPCF_OK && pick.size() == 1) {
+                rc = serving_launch_one(ctx_, pick[0]->sh, pick[0]->hwd, hs[0].q_begin, pos, 0, 0, d_stats_[step.buf],
+                                        ss);
+            } else if (rc == TPCF_OK) {
+                if (cudaMemcpyAsync(d_slices_[step.buf], hs, pick.size() * sizeof(StepSlice), cudaMemcpyHostToDevice,
+                                    ss) != cudaSuccess)
+                    rc = TPCF_ECUDA;
+                else
+                    rc = serving_launch(ctx_, sh, ne_max, d_slices_[step.buf], (int)pick.size(),
+                                        d_stats_[step.buf] + kStatWords, pos, d_stats_[step.buf], ss);
+            }
+            yield_big_step();
+        } else if (step.big) {
+            Job& j = *step.big;
+            ++j.inflight;
+            step.jobs.push_back(step.big);
+            if (rc == TPCF_OK)
+                rc = serving_launch_one(ctx_, j.sh, j.hwd, 0, (uint32_t)j.n_items, j.pos_next, j.draw_warps,
+                                        d_stats_[step.buf], ss);
+        } else {
+            for (auto& jp : step.finals) {  // finalize-only step of large jobs
+                ++jp->inflight;
+                step.jobs.push_back(jp);
+            }
+        }
         cudaEventRecord(step.kdone, ss);
-        // the jobs this step completes: overflow from the pair totals, histograms to the host,
-        // once the previous step (on the other stream, possibly with slices of the same jobs)
-        // has counted too
-        if (rc == TPCF_OK && !step.finals.empty() && !steps_.empty() &&
-            cudaStreamWaitEvent(ss, steps_.back().kdone, 0) != cudaSuccess)
-            rc = TPCF_ECUDA;
+        // the jobs this step completes: overflow from the pair totals, histograms to the host
         for (auto& jp : step.finals) {
             Job& j = *jp;
+            j.finalized = true;
             const int ne = (int)j.edges.size();
             if (rc == TPCF_OK &&
                 (launch_finalize_batch(j.acc, ne + 1, ne, j.acc, ne + 1, j.dtot, 3,
@@ -511,6 +562,24 @@ class JobServer {
         return true;
     }
 
+    bool big_in_flight() const {
+        for (const Step& st : steps_)
+            if (st.big) return true;
+        return false;
+    }
+
+    // Tells the large job's step in flight (if any) to stop drawing positions
+    // (mu_ held): its yield word is set by a copy on the yield stream; the step's
+    // warps finish the items they hold and its blocks leave the SMs.
+    void yield_big_step() {
+        for (Step& st : steps_) {
+            if (!st.big || st.yielded) continue;
+            st.yielded = true;
+            cudaMemcpyAsync(d_stats_[st.buf] + kStatYield, h_one_, 8, cudaMemcpyHostToDevice, yield_stream_);
+            cudaEventRecord(yield_ev_[st.buf], yield_stream_);
+        }
+    }
+
     // The oldest step has finished (mu_ held): job bookkeeping, completions.
     void complete_step() {
         Step step = std::move(steps_.front());
@@ -522,6 +591,12 @@ class JobServer {
         const unsigned long long err = h_stats_[step.buf][kStatError];
         if (rc == TPCF_OK && (err & kErrWaitTimeout)) rc = TPCF_ETIMEOUT;
         else if (rc == TPCF_OK && err) rc = TPCF_ECUDA;
+        // a large job's step: the positions it took (a yielded step stops early;
+        // warps that found the order exhausted drew past its end)
+        if (step.big && rc == TPCF_OK) {
+            Job& j = *step.big;
+            j.pos_next = std::min<uint64_t>(j.pos_end, step.pos_lo + h_stats_[step.buf][kStatNextItem]);
+        }
         for (auto& jp : step.jobs) {
             Job& j = *jp;
             --j.inflight;
@@ -529,14 +604,15 @@ class JobServer {
             if (rc != TPCF_OK) {
                 j.status = rc;
                 j.next = j.n_items;  // nothing more is scheduled for it
+                j.pos_next = j.pos_end;
             }
         }
         for (auto& jp : step.jobs) {
             Job& j = *jp;
             if (j.state == Job::kDone || j.inflight > 0) continue;
-            if (j.next >= j.n_items || j.cancel) {
+            if (j.finalized || j.cancel || j.status != TPCF_OK) {
                 active_.erase(std::remove(active_.begin(), active_.end(), jp), active_.end());
-                finish(j, j.status != TPCF_OK ? j.status : TPCF_OK);
+                finish(j, j.status);
             }
         }
         cudaEventDestroy(step.t0);
@@ -544,12 +620,11 @@ class JobServer {
         cudaEventDestroy(step.kdone);
     }
 
-    // Jobs without items and cancelled jobs that hold no step (mu_ held).
+    // Jobs without items, cancelled jobs and failed jobs that hold no step (mu_ held).
     void settle_idle_jobs() {
         for (auto it = active_.begin(); it != active_.end();) {
             Job& j = **it;
-            if (j.inflight == 0 && (j.n_items == 0 || (j.cancel && j.next < j.n_items) ||
-                                    (j.next >= j.n_items && j.status != TPCF_OK))) {
+            if (j.inflight == 0 && (j.n_items == 0 || (j.cancel && !j.finalized) || j.status != TPCF_OK)) {
                 std::shared_ptr<Job> keep = *it;
                 it = active_.erase(it);
                 finish(j, j.status);
@@ -608,6 +683,9 @@ class JobServer {
     std::vector<cudaStream_t> prep_streams_;
     cudaStream_t streams_[kStepsInFlight] = {nullptr, nullptr};
     cudaStream_t stream_ = nullptr;       // frees of finished jobs' memory
+    cudaStream_t yield_stream_ = nullptr;  // yields of large jobs' steps
+    unsigned long long* h_one_ = nullptr;  // pinned: the yield word's value
+    cudaEvent_t yield_ev_[kStepsInFlight] = {nullptr, nullptr};
     uint64_t* h_res_ = nullptr;
     StepSlice* h_slices_[kStepsInFlight] = {nullptr, nullptr};
     StepSlice* d_slices_[kStepsInFlight] = {nullptr, nullptr};

@@ -100,6 +100,7 @@ constexpr int kMaxInlineSub = 3;
 // Device statistics words (per call, in the scratch slot after the histograms).
 enum StatWord { kStatPairs = 0, kStatBand = 1, kStatMismatch = 2, kStatError = 3, kStatPruned = 4,
                 kStatNextItem = 5,  // counting kernel: items drawn from the launch's dynamic pool
+                kStatYield = 6,     // counting kernel: nonzero stops further draws (preemptible steps)
                 kStatWords = 8 };
 
 // Device error word bits.
@@ -124,6 +125,13 @@ struct WorkDesc {
     uint64_t item_lo, item_hi;       // walk positions of this launch (shards)
     unsigned long long* stats;       // kStatWords words
     unsigned long long* item_counter;  // the counter items are drawn with (stats + kStatNextItem)
+    // Draw order: the launch draws the positions of [item_lo, item_hi)'s draw
+    // order from pos_lo on, the order laid out for draw_warps warps (set by the
+    // launcher), and stops drawing once stats[kStatYield] is nonzero (the job
+    // server's preemptible steps); the item counter then says how many
+    // positions it took.
+    uint64_t pos_lo;
+    uint32_t draw_warps;
     // serving steps (the multi-job kernel): the step's slices, sorted by position,
     // and one item counter per slice (zeroed before the launch)
     const StepSlice* slices;
