@@ -358,8 +358,9 @@ __device__ __noinline__ bool heavy_item(const WorkDesc& wd, const SubProblem& sp
 // The warp's next item (or part) with countable tiles, drawing again past
 // empty and skipped ones; called by every lane of the warp (lane 0 draws a
 // position from `counter`, the position is broadcast).  A preemptible launch
-// draws from pos_lo on and stops drawing once its yield word is set (the
-// positions it took are the counter's value).
+// (PREEMPT) draws from pos_lo on and stops drawing once its yield word is set
+// (the positions it took are the counter's value).
+template <bool PREEMPT>
 __device__ void draw_next(const WorkDesc& wd, Cursor& c, unsigned long long* counter) {
     const uint64_t n = wd.item_hi - wd.item_lo;
     const uint64_t warps = wd.draw_warps;
@@ -367,8 +368,14 @@ __device__ void draw_next(const WorkDesc& wd, Cursor& c, unsigned long long* cou
     const uint64_t parts_at = n + L - tail, end = parts_at + tail * kTailParts;
     while (true) {
         unsigned long long p = ~0ull;  // (a yield: no position taken)
-        if ((threadIdx.x & 31) == 0 && *reinterpret_cast<volatile unsigned long long*>(wd.stats + kStatYield) == 0ull)
-            p = wd.pos_lo + atomicAdd(counter, 1ull);
+        if ((threadIdx.x & 31) == 0) {
+            if constexpr (PREEMPT) {
+                if (*reinterpret_cast<volatile unsigned long long*>(wd.stats + kStatYield) == 0ull)
+                    p = wd.pos_lo + atomicAdd(counter, 1ull);
+            } else {
+                p = atomicAdd(counter, 1ull);
+            }
+        }
         p = __shfl_sync(0xffffffffu, p, 0);
         if (p >= end) {
             c.valid = false;
@@ -404,10 +411,11 @@ __device__ void draw_next(const WorkDesc& wd, Cursor& c, unsigned long long* cou
     }
 }
 
+template <bool PREEMPT>
 __device__ __forceinline__ void advance(const WorkDesc& wd, Cursor& c, unsigned long long* counter) {
     if (!c.valid) return;
     if (++c.t < c.g.t_end) return;
-    draw_next(wd, c, counter);
+    draw_next<PREEMPT>(wd, c, counter);
 }
 
 // ============================================================== block helpers
@@ -1042,7 +1050,7 @@ __device__ __forceinline__ bool prune_chunk(const WorkDesc& wd, uint32_t jg0, ui
 // slice's counter, shared by all blocks.  When a block moves to another job,
 // its warps merge their counters into the previous job's histograms and the
 // block loads the new job's bins and LUT.
-template <int T, int R, int MODE, bool MULTI>
+template <int T, int R, int MODE, bool MULTI, bool PREEMPT>
 __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ WorkDesc wd) {
     constexpr bool PLAIN = MODE == kModePlain;
     constexpr bool EUCLID = MODE == kModeEuclid;
@@ -1116,10 +1124,10 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
     if (aborted || ctl[kCtlAbort]) return;
     // (single launches draw from the launch's statistics word: no pointer held in registers)
     Cursor prod;
-    draw_next(wd, prod, MULTI ? wd.item_counter : wd.stats + kStatNextItem);
+    draw_next<PREEMPT>(wd, prod, MULTI ? wd.item_counter : wd.stats + kStatNextItem);
     for (; issued < seq + S && prod.valid; ++issued) {
         issue(wd, issued, prod);
-        advance(wd, prod, MULTI ? wd.item_counter : wd.stats + kStatNextItem);
+        advance<PREEMPT>(wd, prod, MULTI ? wd.item_counter : wd.stats + kStatNextItem);
     }
     for (; seq < issued; ++seq) {
         // ---- wait for tile seq
@@ -1339,7 +1347,7 @@ __global__ void __launch_bounds__(T, 1) count_kernel(const __grid_constant__ Wor
         if (prod.valid && !ctl[kCtlAbort]) {
             issue(wd, seq + S, prod);
             ++issued;
-            advance(wd, prod, MULTI ? wd.item_counter : wd.stats + kStatNextItem);
+            advance<PREEMPT>(wd, prod, MULTI ? wd.item_counter : wd.stats + kStatNextItem);
         }
     }
     };
@@ -1511,7 +1519,7 @@ cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long l
 // ============================================================== launchers
 // Fills the block constants of the work description (shared-memory offsets of
 // the shape, merge interval) and launches.
-template <int T, int R, int MODE, bool MULTI = false>
+template <int T, int R, int MODE, bool MULTI = false, bool PREEMPT = false>
 static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t stream) {
     WorkDesc wd = wd_in;
     const SmemLayout L = smem_layout(MODE, T, (int)wd.J, (int)wd.stages, wd.nedges_max);
@@ -1538,21 +1546,22 @@ static cudaError_t launch_t(const WorkDesc& wd_in, const Shape& sh, cudaStream_t
     // the draw order is laid out for this launch's warps unless the caller fixed it
     // (continuations of a preempted launch keep the order of the first)
     if (wd.draw_warps == 0) wd.draw_warps = (uint32_t)sh.blocks * (uint32_t)(T / 32);
-    count_kernel<T, R, MODE, MULTI><<<sh.blocks, T, sh.smem, stream>>>(wd);
+    count_kernel<T, R, MODE, MULTI, PREEMPT><<<sh.blocks, T, sh.smem, stream>>>(wd);
     return cudaGetLastError();
 }
 
 // The limit is raised to the device's opt-in maximum rather than to `bytes`:
 // the attribute belongs to the kernel, not to a launch, so a smaller value set
 // by one host thread could otherwise undercut a concurrent launch of another.
-template <int T, int R, int MODE, bool MULTI = false>
+template <int T, int R, int MODE, bool MULTI = false, bool PREEMPT = false>
 static cudaError_t set_smem_t(size_t bytes) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if (bytes > (size_t)optin) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(count_kernel<T, R, MODE, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    return cudaFuncSetAttribute(count_kernel<T, R, MODE, MULTI, PREEMPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin);
 }
 
 cudaError_t launch_count_step(const WorkDesc& wd, const Shape& sh, cudaStream_t stream) {
@@ -1561,6 +1570,17 @@ cudaError_t launch_count_step(const WorkDesc& wd, const Shape& sh, cudaStream_t 
 }
 
 cudaError_t count_step_set_smem_limit(size_t bytes) { return set_smem_t<512, 8, kModeScreen, true>(bytes); }
+
+// The job server's one-job steps: the 512 x 8 screen kernel with preemptible
+// draws (a start position and the yield word).
+cudaError_t launch_count_preemptible(const WorkDesc& wd, const Shape& sh, cudaStream_t stream) {
+    if (sh.threads != 512 || sh.ipt != 8) return cudaErrorInvalidConfiguration;
+    return launch_t<512, 8, kModeScreen, false, true>(wd, sh, stream);
+}
+
+cudaError_t count_preemptible_set_smem_limit(size_t bytes) {
+    return set_smem_t<512, 8, kModeScreen, false, true>(bytes);
+}
 
 #define TPCF_SHAPES(X) X(128, 8) X(256, 8) X(512, 8) X(256, 16)
 

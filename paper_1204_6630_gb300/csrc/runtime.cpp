@@ -1437,8 +1437,8 @@ int tpcf::serving_launch_one(tpcf_ctx* ctx, const Shape& sh, const WorkDesc& job
     const uint64_t warps = (uint64_t)sh.threads / 32;
     const uint64_t need = ((uint64_t)n + warps - 1) / warps;
     if ((uint64_t)s2.blocks > need) s2.blocks = (int)std::max<uint64_t>(1, need);
-    if (count_set_smem_limit(kModeScreenScalar, sh.threads, sh.ipt, sh.smem) != cudaSuccess) return TPCF_ECUDA;
-    if (launch_count(wd, s2, kModeScreenScalar, wd.ne, st) != cudaSuccess) return TPCF_ECUDA;
+    if (count_preemptible_set_smem_limit(sh.smem) != cudaSuccess) return TPCF_ECUDA;
+    if (launch_count_preemptible(wd, s2, st) != cudaSuccess) return TPCF_ECUDA;
     ctx->launches.fetch_add(1);
     return TPCF_OK;
 }

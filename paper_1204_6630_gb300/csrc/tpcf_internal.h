@@ -183,13 +183,16 @@ struct Shape {
 // all-binary64 comparator, FP32 screen of distances (3-D variant).
 enum { kModeScreenScalar = 0, kModePlainFP64 = 1, kModeEuclidScreen = 3 };
 
-// Launchers (kernels.cu).  All are asynchronous in `stream` and return a
+// Launchers (count.cu, prep.cu).  All are asynchronous in `stream` and return a
 // cudaError_t from the launch.
 cudaError_t launch_count(const WorkDesc& wd, const Shape& sh, int mode, int nedges,
                          cudaStream_t stream);
 // One serving step (FP32 screen of angles, shape 512 x 8): wd holds the launch
 // layout, the statistics words and the step's slices.
 cudaError_t launch_count_step(const WorkDesc& wd, const Shape& sh, cudaStream_t stream);
+// One serving step of a single job (FP32 screen of angles, shape 512 x 8): the
+// one-job kernel with preemptible draws (wd.pos_lo, stats[kStatYield]).
+cudaError_t launch_count_preemptible(const WorkDesc& wd, const Shape& sh, cudaStream_t stream);
 // count_over = 1: the kernel counted the overflow row (TPCF_F_CHECK_OVERFLOW);
 // the finalize then checks that the histogram sums to the pair total.
 cudaError_t launch_finalize(unsigned long long* acc, int nedges, unsigned long long* out,
@@ -209,5 +212,6 @@ bool count_shape_supported(int threads, int ipt);
 bool derive_cos_thresholds(const double* edges, int nedges, double* cos_thr);
 cudaError_t count_set_smem_limit(int mode, int threads, int ipt, size_t bytes);
 cudaError_t count_step_set_smem_limit(size_t bytes);
+cudaError_t count_preemptible_set_smem_limit(size_t bytes);
 
 }  // namespace tpcf
