@@ -1,5 +1,5 @@
-// Internal types shared by the host runtime (runtime.cpp) and the kernels
-// (kernels.cu).  Not part of the public ABI.
+// Internal types shared by the host runtime (runtime.cpp, server.cpp) and the
+// kernels (count.cu, prep.cu).  Not part of the public ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,7 +8,7 @@
 namespace tpcf {
 
 // Catalog padding: every device catalog holds a multiple of this many
-// points; points past n are zero vectors (never counted, see kernels.cu).
+// points; points past n are zero vectors (never counted, see count.cu).
 constexpr uint32_t kPad = 4096;
 
 // Segments of a segmented catalog start on multiples of this many points (one
@@ -27,7 +27,7 @@ constexpr double kCapScale3d = 5.421010862427522e-20;
 constexpr int kLutBits = 14;
 constexpr int kLutCells = (1 << kLutBits) + 1;
 
-// The chord refinement of unsettled pairs (kernels.cu, slow_j) is proven for
+// The chord refinement of unsettled pairs (count.cu, classify_unsettled) is proven for
 // catalogs whose points satisfy | |v|^2 - 1 | <= kChordEpsRef.
 constexpr double kChordEpsRef = 0x1p-40;
 
