@@ -90,6 +90,7 @@ struct Job {
     // items, laid out for draw_warps warps, positions [0, pos_end) of which pos_next
     // are taken; its finalize follows in a step of its own
     bool big = false;
+    bool small = false;                   // at most kSmallJobPairs pairs (known at submission)
     uint32_t draw_warps = 0;
     uint64_t pos_next = 0, pos_end = 0;
     bool finalized = false;               // the step holding its finalize has been launched
@@ -201,6 +202,10 @@ class JobServer {
         j->estimator = job->estimator;
         j->nd = job->nd;
         j->nr = job->nr;
+        {
+            const double nd = (double)job->nd, nr = (double)job->nr;
+            j->small = nd * (nd - 1) / 2 + nd * nr + nr * (nr - 1) / 2 <= kSmallJobPairs;
+        }
         const uint64_t nmax = job->nd > job->nr ? job->nd : job->nr;
         uint64_t n_pow2 = 2048;
         while (n_pow2 < nmax) n_pow2 <<= 1;
@@ -365,9 +370,16 @@ class JobServer {
                 if (prep_queue_.empty()) return;  // stopping
                 j = prep_queue_.front();
                 prep_queue_.pop_front();
+                // a small job's preparation kernels need SMs that a large job's step
+                // holds: that step stops drawing, and none resumes until it is ready
+                if (j->small) {
+                    ++small_preparing_;
+                    yield_big_step();
+                }
             }
             const int rc = prepare(*j, st);
             std::lock_guard<std::mutex> g(mu_);
+            if (j->small) --small_preparing_;
             if (rc != TPCF_OK || j->cancel || j->solo) {
                 finish(*j, rc);
             } else {
@@ -375,8 +387,8 @@ class JobServer {
                 active_.push_back(j);
                 // a small job does not wait for a large job's step: that step stops drawing
                 if (!j->big && j->work_left()) yield_big_step();
-                cv_sched_.notify_all();
             }
+            cv_sched_.notify_all();  // (also when large steps waited for this preparation)
         }
     }
 
@@ -471,7 +483,7 @@ class JobServer {
                 if ((int)pick.size() >= slots_) break;
             }
             small = !pick.empty();
-            if (!small && !big_in_flight()) {
+            if (!small && !big_in_flight() && small_preparing_ == 0) {
                 for (auto& j : active_) {
                     if (!j->big || j->cancel || !j->work_left() || j->inflight > 0) continue;
                     pick.push_back(j);
@@ -670,6 +682,7 @@ class JobServer {
     bool stop_ = false;
     uint64_t next_id_ = 1;
     uint64_t step_seq_ = 0;
+    int small_preparing_ = 0;             // small jobs in preparation (large steps wait for them)
     std::mutex mu_;
     std::condition_variable cv_prep_, cv_sched_, cv_done_;
     std::deque<std::shared_ptr<Job>> queue_, prep_queue_;

@@ -238,3 +238,25 @@ def test_a_job_with_too_many_edges_for_the_step_kernel_runs_alone(T):
     for k, (g, w_) in enumerate(zip(got, want)):
         for name, a in zip(("dd", "dr", "rr", "w"), w_):
             np.testing.assert_array_equal(g[name], a, err_msg=f"job {k} {name}")
+
+
+def test_a_small_job_preempts_a_running_large_job(T):
+    """A large job's step stops drawing when a small job is ready: the small job,
+    submitted while the large one counts, finishes first; both equal lone calls."""
+    import time
+    edges = synth.linear_edges(0.0, 2.0, 30)
+    big = octant_job(700_000, 1_400_000, seed=70)
+    small = octant_job(2000, 4000, seed=71)
+    with T.Context() as lone:
+        want_big = lone.correlate(*big, edges)
+        want_small = lone.correlate(*small, edges)
+    with T.Context() as ctx:
+        jb = ctx.submit(*big, edges)
+        time.sleep(0.15)  # the large job is prepared and counting
+        js = ctx.submit(*small, edges)
+        rs = ctx.poll(js, len(edges))
+        rb = ctx.poll(jb, len(edges))
+    assert rs["submit_ms"] + rs["latency_ms"] < rb["submit_ms"] + rb["latency_ms"]
+    for res, want in ((rb, want_big), (rs, want_small)):
+        for name, a in zip(("dd", "dr", "rr", "w"), want):
+            np.testing.assert_array_equal(res[name], a)
