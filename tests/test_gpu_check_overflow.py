@@ -156,7 +156,7 @@ def test_counted_overflow_at_1m_covers_every_draw_phase(T):
 
 
 def test_counted_overflow_through_the_job_server(T):
-    # small jobs share the multi-job kernel's steps, the largest runs in slices of the one-job kernel
+    # small jobs share the multi-job kernel's steps, the largest runs in preemptible one-job steps
     specs = synth.serving_jobs(24, seed=5)
     jobs = [synth.materialise_job(s) for s in specs]
     with T.Context() as lone:
